@@ -1,0 +1,538 @@
+"""Pins of the CPU oracle to things other than itself: closed forms the paper
+states, hand-derived values, invariants of the continuum and of the
+discretisation, finite differences of its own energy, and library routines
+for special cases.  No GPU.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1911_07045_b300 import synth
+
+A, B, C = synth.A_5CB, synth.B_5CB, synth.C_5CB
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def s0_poly(A_, B_, C_):
+    # Eq. (S0def), written independently of the oracle
+    return (-B_ + math.sqrt(B_ * B_ - 24 * A_ * C_)) / (6 * C_)
+
+
+def f_of_S(S, A_=A, B_=B, C_=C):
+    # Eq. (fphaseS): the uniaxial reduction of the bulk energy
+    return 0.75 * A_ * S ** 2 + 0.25 * B_ * S ** 3 + 9.0 / 16.0 * C_ * S ** 4
+
+
+def df_dS(S, A_=A, B_=B, C_=C):
+    return 1.5 * A_ * S + 0.75 * B_ * S ** 2 + 2.25 * C_ * S ** 3
+
+
+def rand_q(N, seed, scale=0.3):
+    return np.random.default_rng(seed).normal(scale=scale, size=(5, N))
+
+
+def full_Q(q):
+    """(N,3,3) tensors from (5,N) components."""
+    N = q.shape[1]
+    Q = np.zeros((N, 3, 3))
+    Q[:, 0, 0], Q[:, 0, 1], Q[:, 0, 2] = q[0], q[1], q[2]
+    Q[:, 1, 0], Q[:, 1, 1], Q[:, 1, 2] = q[1], q[3], q[4]
+    Q[:, 2, 0], Q[:, 2, 1], Q[:, 2, 2] = q[2], q[4], -q[0] - q[3]
+    return Q
+
+
+def comps(Q):
+    return np.stack([Q[:, 0, 0], Q[:, 0, 1], Q[:, 0, 2], Q[:, 1, 1], Q[:, 1, 2]])
+
+
+# ---- paper's printed numbers ------------------------------------------------
+
+def test_paper_5cb_numbers(oracle_mod):
+    g = json.load(open(os.path.join(GOLD, "paper_5cb.json")))
+    S0 = oracle_mod.uniaxial_s0(g["A"], g["B"], g["C"])
+    assert abs(S0 - g["S0_printed"]) < g["S0_printed_digits"]
+    # K = L1 9 S0^2 / 2  and  dx^2 = L1 / (L1~ |A|)
+    L1 = 2 * g["K_newton"] / (9 * S0 ** 2)
+    dx_nm = math.sqrt(L1 / (g["L1_tilde"] * abs(g["A"]))) * 1e9
+    assert abs(dx_nm - g["dx_nm_printed"]) < g["dx_nm_printed_digits"]
+    # lattice-unit constants have the same S0 (S0 depends on ratios only)
+    assert abs(oracle_mod.uniaxial_s0(A, B, C) - S0) < 1e-14
+
+
+def test_rapini_papoular_identity(oracle_mod):
+    """Uniaxial Q at S0 at angle theta to the preferred axis: Nobili-Durand
+    energy = 9/2 S0^2 W sin^2(theta), i.e. the Rapini-Papoular form with
+    W_RP = 9 S0^2 W_ND up to a constant."""
+    g = json.load(open(os.path.join(GOLD, "paper_5cb.json")))
+    W = 1.7
+    for theta in (0.0, 0.3, 1.0, math.pi / 2):
+        nu = np.array([0.0, 0.0, 1.0])
+        o = oracle_mod.Oracle((3, 3, 3), A, B, C, 1.0, objects=[dict(
+            type="anchored", xyz=[[1, 1, 1]], kinds=[oracle_mod.ND_ORIENTED], W=[W],
+            dirs=[nu])])
+        S0 = o.S0
+        n = np.array([math.sin(theta), 0.0, math.cos(theta)])
+        q = np.repeat(synth.uniaxial_q(n[:, None], S0), 27, axis=1)
+        _, parts = o.energy(q)
+        rp = -0.5 * g["W_RP_over_W_ND_over_S0sq"] * S0 ** 2 * W * math.cos(theta) ** 2
+        assert abs(parts[2] - (4.5 * S0 ** 2 * W + rp)) < 1e-13
+        assert abs(parts[2] - 4.5 * S0 ** 2 * W * math.sin(theta) ** 2) < 1e-13
+
+
+def test_fournier_galatola_values(oracle_mod):
+    """Planar-degenerate form: 0 for any in-plane director at S0, and
+    9/4 S0^2 W cos^2 t (1 + sin^2 t) for a director tilted by t from nu."""
+    W = 0.8
+    nu = np.array([1.0, 2.0, 2.0]) / 3.0
+    t1 = np.cross(nu, [0, 0, 1.0]); t1 /= np.linalg.norm(t1)
+    t2 = np.cross(nu, t1)
+    o = oracle_mod.Oracle((3, 3, 3), A, B, C, 1.0, objects=[dict(
+        type="anchored", xyz=[[0, 2, 1]], kinds=[oracle_mod.FG_PLANAR], W=[W], dirs=[nu])])
+    S0 = o.S0
+    for phi in (0.0, 0.7, 2.0):
+        n = math.cos(phi) * t1 + math.sin(phi) * t2
+        q = np.repeat(synth.uniaxial_q(n[:, None], S0), 27, axis=1)
+        assert abs(o.energy(q)[1][2]) < 1e-14
+    for t in (0.2, 0.9, 1.3):
+        n = math.cos(t) * nu + math.sin(t) * t1
+        q = np.repeat(synth.uniaxial_q(n[:, None], S0), 27, axis=1)
+        want = 2.25 * S0 ** 2 * W * math.cos(t) ** 2 * (1 + math.sin(t) ** 2)
+        assert abs(o.energy(q)[1][2] - want) < 1e-13
+
+
+# ---- bulk --------------------------------------------------------------------
+
+@pytest.mark.parametrize("mat", [(A, B, C), (-1.0, -12.3256, 10.0581)])
+def test_uniform_s0_is_stationary(oracle_mod, mat):
+    A_, B_, C_ = mat
+    S0 = s0_poly(A_, B_, C_)
+    assert abs(df_dS(S0, A_, B_, C_)) < 1e-13
+    shape = (3, 4, 2)
+    N = 24
+    n = synth.random_directors(1, 11)
+    q = np.repeat(synth.uniaxial_q(n, S0), N, axis=1)
+    o = oracle_mod.Oracle(shape, A_, B_, C_, 2.32, 0.5, 0.3)
+    E, parts = o.energy(q)
+    assert abs(E - N * f_of_S(S0, A_, B_, C_)) < 1e-13 * N
+    assert parts[1] == 0.0
+    assert np.abs(o.force(q)).max() < 1e-14
+
+
+@pytest.mark.parametrize("S", [0.1, 0.3, 0.75, -0.2])
+def test_uniform_uniaxial_force_is_polynomial_derivative(oracle_mod, S):
+    n = synth.random_directors(1, 7)
+    q = np.repeat(synth.uniaxial_q(n, S), 8, axis=1)
+    o = oracle_mod.Oracle((2, 2, 2), A, B, C, 2.32)
+    E, _ = o.energy(q)
+    assert abs(E - 8 * f_of_S(S)) < 1e-14
+    F = o.force(q)
+    # -F . dq/dS = df/dS along the uniaxial family q(S) = S q(1)
+    proj = -(F[:, 0] * q[:, 0] / S).sum()
+    assert abs(proj - df_dS(S)) < 1e-13
+
+
+def test_bulk_gradient_biaxial_fd(oracle_mod):
+    """Uniform biaxial Q: the force on one site of a 1^3 lattice equals a
+    central difference of Eq. (fphase) written out with numpy traces."""
+    def f_bulk(q5):
+        Q = full_Q(q5[:, None])[0]
+        t2 = np.trace(Q @ Q)
+        return A / 2 * t2 + B / 3 * np.trace(Q @ Q @ Q) + C / 4 * t2 * t2
+    q = np.array([0.21, -0.13, 0.07, -0.05, 0.19])
+    o = oracle_mod.Oracle((1, 1, 1), A, B, C, 2.32)
+    F = o.force(q[:, None])[:, 0]
+    h = 1e-5
+    for c in range(5):
+        e = np.zeros(5); e[c] = h
+        fd = -(f_bulk(q + e) - f_bulk(q - e)) / (2 * h)
+        assert abs(fd - F[c]) < 1e-9
+
+
+# ---- hand-derived chain ---------------------------------------------------------
+
+@pytest.mark.parametrize("Ls", [(2.32, 0.0, 0.0), (1.3, 0.5, 0.3)])
+@pytest.mark.parametrize("periodic_yz", [0, 1])
+def test_chain3_hand_values(oracle_mod, Ls, periodic_yz):
+    g = json.load(open(os.path.join(GOLD, "chain3_hand.json")))
+    L1, L2, L3 = Ls
+    o = oracle_mod.Oracle((3, 1, 1), A, B, C, L1, L2, L3,
+                          periodic=(0, periodic_yz, periodic_yz))
+    q = np.zeros((5, 3))
+    q[1] = g["a"]
+    E, parts = o.energy(q)
+    e = g["energy"]
+    want = e["A"] * A + e["C"] * C + e["L1"] * L1 + e["L2"] * L2 + e["L3"] * L3
+    assert abs(E - want) < 1e-12
+    F = o.force(q)
+    for s in range(3):
+        f = g["force_q1"][s]
+        want = f["L1"] * L1 + f["L23"] * (L2 + L3) + f["A"] * A + f["C"] * C
+        assert abs(F[1, s] - want) < 1e-12
+    for s in range(3):
+        assert abs(F[0, s] - g["force_q0_q3_B"][s] * B) < 1e-12
+        assert abs(F[3, s] - g["force_q0_q3_B"][s] * B) < 1e-12
+    assert np.abs(F[[2, 4]]).max() < 1e-14
+
+
+# ---- force = -gradient ------------------------------------------------------------
+
+HOM = lambda W: (0, W, (0.0, 0.0, 1.0))
+GEOMS = {
+    "bulk_1c": dict(shape=(4, 3, 5), L=(2.32, 0, 0), periodic=(1, 1, 1), objects=[]),
+    "wall_nd_3c": dict(shape=(5, 4, 5), L=(2.32, 0.5, 0.3), periodic=(1, 1, 1),
+                       objects=[dict(type="wall", axis=2, plane=0, anchor=HOM(2.0))]),
+    "sphere_nd_3c": dict(shape=(6, 6, 6), L=(1.1, 0.9, -0.4), periodic=(1, 1, 1),
+                         objects=[dict(type="sphere", c=(3, 3, 3), R=1.5, anchor=HOM(5.3))]),
+    "fg_walls_open_y": dict(shape=(4, 5, 6), L=(2.32, 0.5, 0.3), periodic=(1, 0, 1),
+                            objects=[dict(type="wall", axis=2, plane=0, anchor=(2, 1.0, (0, 0, 1))),
+                                     dict(type="wall", axis=2, plane=4, anchor=(2, 1.5, (0, 0, 1)))]),
+    "custom_open_x": dict(shape=(5, 4, 4), L=(1.0, 0.7, 0.2), periodic=(0, 1, 1),
+                          objects=[dict(type="sites", xyz=[[2, 1, 1], [2, 2, 1], [3, 2, 1]],
+                                        anchor=(1, 3.0, (0.6, 0.0, 0.8))),
+                                   dict(type="anchored", xyz=[[0, 0, 0], [4, 3, 3], [1, 1, 1]],
+                                        kinds=[2, 1, 0], W=[1.0, 2.0, 0.5],
+                                        dirs=[[0, 1, 0], [1, 1, 0], [0, 0, 1]])]),
+    "tiny_2cube": dict(shape=(2, 2, 3), L=(1.5, 0.4, 0.6), periodic=(1, 1, 0), objects=[]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GEOMS))
+def test_force_is_minus_gradient(oracle_mod, name):
+    gdef = GEOMS[name]
+    o = oracle_mod.Oracle(gdef["shape"], A, B, C, *gdef["L"], periodic=gdef["periodic"],
+                          objects=gdef["objects"])
+    q = rand_q(o.N, 5)
+    F = o.force(q)
+    sim = o.simulated()
+    assert np.all(F[:, ~sim] == 0)
+    rng = np.random.default_rng(3)
+    h = 1e-5
+    for _ in range(25):
+        i = int(rng.choice(np.nonzero(sim)[0]))
+        c = int(rng.integers(5))
+        vals = []
+        for s in (+1, -1, +2, -2):
+            qq = q.copy()
+            qq[c, i] += s * h
+            vals.append(o.energy(qq)[0])
+        # 4th-order central difference
+        fd = -(8 * (vals[0] - vals[1]) - (vals[2] - vals[3])) / (12 * h)
+        assert abs(fd - F[c, i]) < 1e-7 * max(1.0, abs(F[c, i])), (i, c, fd, F[c, i])
+
+
+# ---- distortion pins ------------------------------------------------------------------
+
+def test_uniform_field_zero_distortion_with_objects(oracle_mod):
+    for gname in ("wall_nd_3c", "sphere_nd_3c", "custom_open_x", "fg_walls_open_y"):
+        gdef = GEOMS[gname]
+        o = oracle_mod.Oracle(gdef["shape"], A, B, C, *gdef["L"], periodic=gdef["periodic"],
+                              objects=gdef["objects"])
+        n = np.array([0.3, -0.5, 0.8]); n /= np.linalg.norm(n)
+        q = np.repeat(synth.uniaxial_q(n[:, None], o.S0), o.N, axis=1)
+        _, parts = o.energy(q)
+        assert parts[1] == 0.0
+        o0 = oracle_mod.Oracle(gdef["shape"], A, B, C, 0.0, periodic=gdef["periodic"],
+                               objects=gdef["objects"])
+        # the force is the bulk + anchoring force alone
+        assert np.abs(o.force(q) - o0.force(q)).max() < 1e-14
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+def test_twist_texture_energy(oracle_mod, m):
+    shape = (3, 2, 12)
+    L1 = 2.32
+    o = oracle_mod.Oracle(shape, A, B, C, L1, 0.5, 0.3)
+    q = synth.texture_q(shape, "twist", m)
+    E, parts = o.energy(q)
+    N = o.N
+    k = math.pi * m / shape[2]
+    S0 = o.S0
+    assert abs(parts[1] / N - 2.25 * S0 ** 2 * L1 * math.sin(k) ** 2) < 1e-13
+    assert abs(parts[0] / N - f_of_S(S0)) < 1e-13
+
+
+@pytest.mark.parametrize("m", [1, 2])
+def test_splay_bend_texture_energy(oracle_mod, m):
+    shape = (2, 3, 10)
+    L1, L2, L3 = 2.32, 0.5, 0.3
+    o = oracle_mod.Oracle(shape, A, B, C, L1, L2, L3)
+    q = synth.texture_q(shape, "splaybend", m)
+    _, parts = o.energy(q)
+    k = math.pi * m / shape[2]
+    S0 = o.S0
+    want = 2.25 * S0 ** 2 * math.sin(k) ** 2 * (L1 + (L2 + L3) / 2)
+    assert abs(parts[1] / o.N - want) < 1e-13
+
+
+def test_plane_wave_discrete_laplacian(oracle_mod):
+    """A small Q_xy wave eps cos(2 pi m x / L) about Q = 0: the force on
+    Q_xy is -(2A + 2 L1 lambda_m) q with lambda_m = 2 (1 - cos(2 pi m / L)),
+    the eigenvalue of the periodic second difference; the factor 2 is the
+    symmetric pair Q_xy = Q_yx."""
+    L, L1, eps = 8, 2.32, 1e-6
+    o = oracle_mod.Oracle((L, 3, 2), A, B, C, L1)
+    x = np.tile(np.arange(L), 6).astype(float)
+    for m in (1, 2, 3):
+        q = np.zeros((5, o.N))
+        q[1] = eps * np.cos(2 * math.pi * m * x / L)
+        F = o.force(q)
+        lam = 2 * (1 - math.cos(2 * math.pi * m / L))
+        want = -(2 * A + 2 * L1 * lam) * q[1]
+        assert np.abs(F[1] - want).max() < 1e-9 * eps
+        # only the second-order B Q.Q term reaches the other components
+        assert np.abs(F[[0, 3]]).max() <= abs(B) * eps ** 2 * (1 + 1e-9)
+        assert np.abs(F[[2, 4]]).max() < 1e-30
+
+
+def test_l2_l3_summation_by_parts_identity(oracle_mod):
+    """On a fully periodic lattice without objects the averaged L2 and L3
+    terms are equal for every Q (centred differences commute and sum by
+    parts), so energies and forces with (L2, L3) = (1, 0) and (0, 1) agree."""
+    shape = (4, 5, 3)
+    o2 = oracle_mod.Oracle(shape, A, B, C, 0.0, 1.0, 0.0)
+    o3 = oracle_mod.Oracle(shape, A, B, C, 0.0, 0.0, 1.0)
+    o1 = oracle_mod.Oracle(shape, A, B, C, 1.0, 0.0, 0.0)
+    q = rand_q(o2.N, 9)
+    e2, e3, e1 = o2.energy(q)[1][1], o3.energy(q)[1][1], o1.energy(q)[1][1]
+    assert abs(e2 - e3) < 1e-12 * abs(e2)
+    assert abs(e2 - e1) > 1e-3 * abs(e1)  # and they are not the L1 term
+    assert np.abs(o2.force(q) - o3.force(q)).max() < 1e-12
+
+
+def test_l2_l3_differ_on_a_ramp_in_a_closed_box(oracle_mod):
+    """Q_xx = a x, Q_zz = -a x, Q_xy = b y in a box closed along x and y:
+    every difference is uniform, so each site's average is the continuum
+    value: L1 (a^2+b^2) + (L2+L3)(a^2+b^2)/2 + L2 a b (the L3 cross term
+    dQ_iy/dx dQ_ix/dy vanishes, the L2 cross term dQ_xx/dx dQ_xy/dy does not)."""
+    shape = (4, 5, 3)
+    a, b = 0.07, -0.11
+    for L1, L2, L3 in ((0.0, 1.0, 0.0), (0.0, 0.0, 1.0), (2.32, 0.5, 0.3)):
+        o = oracle_mod.Oracle(shape, A, B, C, L1, L2, L3, periodic=(0, 0, 1))
+        N = o.N
+        x = np.tile(np.arange(4), 15).astype(float)
+        y = np.tile(np.repeat(np.arange(5), 4), 3).astype(float)
+        q = np.zeros((5, N))
+        q[0] = a * x
+        q[1] = b * y
+        want = L1 * (a * a + b * b) + (L2 + L3) * (a * a + b * b) / 2 + L2 * a * b
+        assert abs(o.energy(q)[1][1] / N - want) < 1e-14
+
+
+def _rot_q(q, R):
+    Q = full_Q(q)
+    return comps(np.einsum("ab,nbc,dc->nad", R, Q, R))
+
+
+def test_global_rotation_invariance_bulk_l1(oracle_mod):
+    gdef = GEOMS["sphere_nd_3c"]
+    o = oracle_mod.Oracle(gdef["shape"], A, B, C, 2.32, objects=[
+        dict(type="sphere", c=(3, 3, 3), R=1.5, anchor=HOM(0.0))])
+    q = rand_q(o.N, 21)
+    rng = np.random.default_rng(4)
+    R, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    if np.linalg.det(R) < 0:
+        R[:, 0] *= -1
+    E, parts = o.energy(q)
+    E2, parts2 = o.energy(_rot_q(q, R))
+    assert abs(E - E2) < 1e-12 * abs(E)
+
+
+def _lattice_rotation(shape_L, R, q, objects):
+    """Rotate field and geometry by a cubic lattice rotation R (integer
+    matrix) about the origin, wrapping coordinates into [0, L)."""
+    L = shape_L
+    N = L ** 3
+    idx = np.arange(N)
+    xyz = np.stack([idx % L, (idx // L) % L, idx // (L * L)])
+    new = (R @ xyz) % L
+    j = new[0] + L * (new[1] + L * new[2])
+    qr = np.zeros_like(q)
+    qr[:, j] = _rot_q(q, R)
+    objs = []
+    for ob in objects:
+        ob = dict(ob)
+        if ob["type"] == "sphere":
+            ob["c"] = tuple(float(v) for v in (R @ np.array(ob["c"])) % L)
+        elif ob["type"] == "wall":
+            ax = int(np.nonzero(R[:, ob["axis"]])[0][0])
+            ob["plane"] = int((R[ax, ob["axis"]] * ob["plane"]) % L)
+            ob["axis"] = ax
+        elif ob["type"] in ("sites", "anchored"):
+            ob["xyz"] = ((R @ np.array(ob["xyz"]).T) % L).T
+            if "dirs" in ob:
+                ob["dirs"] = (R @ np.array(ob["dirs"], float).T).T
+        if "anchor" in ob:
+            k, W, d = ob["anchor"]
+            ob["anchor"] = (k, W, tuple(R @ np.array(d, float)))
+        objs.append(ob)
+    return qr, objs
+
+
+@pytest.mark.parametrize("rot", ["z90", "x90", "y180"])
+def test_cubic_lattice_rotation_invariance(oracle_mod, rot):
+    R = {"z90": np.array([[0, -1, 0], [1, 0, 0], [0, 0, 1]]),
+         "x90": np.array([[1, 0, 0], [0, 0, -1], [0, 1, 0]]),
+         "y180": np.array([[-1, 0, 0], [0, 1, 0], [0, 0, -1]])}[rot]
+    L = 6
+    objects = [dict(type="wall", axis=2, plane=0, anchor=(2, 1.0, (0, 0, 1))),
+               dict(type="sphere", c=(3.0, 2.0, 3.0), R=1.2, anchor=HOM(5.3)),
+               dict(type="anchored", xyz=[[1, 4, 4], [5, 5, 2]], kinds=[1, 2], W=[2.0, 1.0],
+                    dirs=[[1.0, 2.0, 0.5], [0.0, 0.6, 0.8]])]
+    o = oracle_mod.Oracle((L, L, L), A, B, C, 2.32, 0.5, 0.3, objects=objects)
+    q = rand_q(o.N, 8)
+    qr, objr = _lattice_rotation(L, R, q, objects)
+    orr = oracle_mod.Oracle((L, L, L), A, B, C, 2.32, 0.5, 0.3, objects=objr)
+    E, parts = o.energy(q)
+    Er, partsr = orr.energy(qr)
+    assert np.allclose(parts, partsr, rtol=1e-12, atol=1e-12)
+    # forces: the 3x3 derivative rotates as a tensor
+    F, Fr = o.force(q), orr.force(qr)
+    idx = np.arange(o.N)
+    xyz = np.stack([idx % L, (idx // L) % L, idx // (L * L)])
+    new = (R @ xyz) % L
+    j = new[0] + L * (new[1] + L * new[2])
+    # the force pairs with a perturbation: F.dq invariant for dq rotated alike
+    dq = rand_q(o.N, 77, 1.0)
+    dqr = np.zeros_like(dq)
+    dqr[:, j] = _rot_q(dq, R)
+    assert abs((F * dq).sum() - (Fr * dqr).sum()) < 1e-10 * np.abs(F * dq).sum()
+
+
+def test_symmetric_traceless_structure(oracle_mod):
+    q = rand_q(10, 3)
+    Q = full_Q(q)
+    assert np.abs(Q - Q.transpose(0, 2, 1)).max() == 0
+    assert np.abs(np.trace(Q, axis1=1, axis2=2)).max() < 1e-15
+
+
+# ---- eigen readback ---------------------------------------------------------------------
+
+def test_eigen_uniaxial_and_biaxial(oracle_mod):
+    rng = np.random.default_rng(12)
+    for _ in range(20):
+        Rm, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        n, m_, l = Rm[:, 0], Rm[:, 1], Rm[:, 2]
+        S, SB = rng.uniform(0.1, 0.8), rng.uniform(0.0, 0.1)
+        Q = 1.5 * S * (np.outer(n, n) - np.eye(3) / 3) + 0.5 * SB * (np.outer(m_, m_) - np.outer(l, l))
+        ev, vec = oracle_mod.eig_sym3(comps(Q[None])[:, 0])
+        want = sorted([S, (-S + SB) / 2, (-S - SB) / 2], reverse=True)
+        assert np.allclose(ev, want, atol=1e-14)
+        assert abs(abs(vec[0] @ n) - 1) < 1e-10
+    for _ in range(20):
+        q = rng.normal(size=5)
+        ev, _ = oracle_mod.eig_sym3(q)
+        assert np.allclose(ev, np.linalg.eigvalsh(full_Q(q[:, None])[0])[::-1], atol=1e-14)
+
+
+# ---- geometry ---------------------------------------------------------------------------
+
+def test_geometry_sphere_and_walls(oracle_mod):
+    L = 12
+    c, R = (5.0, 6.0, 6.0), 3.4
+    o = oracle_mod.Oracle((L, L, L), A, B, C, 1.0, objects=[
+        dict(type="wall", axis=2, plane=0, anchor=HOM(1.0)),
+        dict(type="sphere", c=c, R=R, anchor=HOM(2.0))])
+    sim = o.simulated().reshape(L, L, L)   # [z, y, x]
+    zz, yy, xx = np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij")
+    inside = (xx - c[0]) ** 2 + (yy - c[1]) ** 2 + (zz - c[2]) ** 2 <= R * R
+    assert np.array_equal(~sim, inside | (zz == 0))
+    sites, kind, W, q0, nu = o.records()
+    S0 = o.S0
+    for s, k, w, qq in zip(sites, kind, W, q0):
+        x, y, z = s % L, (s // L) % L, s // (L * L)
+        assert k == 1
+        if z in (1, L - 1):
+            assert w == 1.0
+            assert np.allclose(qq, synth.uniaxial_q(np.array([[0.0], [0], [1]]), S0)[:, 0])
+        else:
+            assert w == 2.0
+            d = np.array([x - c[0], y - c[1], z - c[2]])
+            assert np.allclose(qq, synth.uniaxial_q((d / np.linalg.norm(d))[:, None], S0)[:, 0])
+    # every simulated face neighbour of an object site has a record
+    touched = np.zeros_like(sim)
+    obj = ~sim
+    for ax in range(3):
+        for sh in (1, -1):
+            touched |= np.roll(obj, sh, axis=ax)
+    assert np.array_equal(np.sort(sites), np.nonzero((touched & sim).ravel())[0])
+
+
+# ---- FIRE ---------------------------------------------------------------------------------
+
+FP = dict(dt0=0.1, dt_max=0.25, alpha0=0.2, f_alpha=0.5, f_inc=2.0, f_dec=0.5, n_min=2,
+          max_iter=100, force_tol=0.0)
+
+
+def test_fire_scalar_machine_scripted(oracle_mod):
+    st = dict(dt=0.1, alpha=0.2, npos=0, iter=0, initialized=1, status=0)
+    expect = [  # (P, a, b/(nv/nF), dt, alpha, npos) by hand from Algorithm 1
+        (+1.0, 0.8, 0.2, 0.1, 0.2, 1),
+        (+1.0, 0.8, 0.2, 0.1, 0.2, 2),
+        (+1.0, 0.8, 0.2, 0.2, 0.1, 3),
+        (+1.0, 0.9, 0.1, 0.25, 0.05, 4),
+        (-1.0, 0.0, 0.0, 0.125, 0.2, 0),
+        (0.0, 0.0, 0.0, 0.0625, 0.2, 0),
+        (+2.0, 0.8, 0.2, 0.0625, 0.2, 1),
+    ]
+    nF, nv = 2.0, 3.0
+    for P, a_w, b_w, dt_w, al_w, np_w in expect:
+        a, b, st = oracle_mod.fire_scalars(FP, st, P, nF, nv)
+        assert abs(a - a_w) < 1e-15 and abs(b - b_w * nv / nF) < 1e-15
+        assert abs(st["dt"] - dt_w) < 1e-15 and abs(st["alpha"] - al_w) < 1e-15
+        assert st["npos"] == np_w
+    a, b, st = oracle_mod.fire_scalars(FP, st, 1.0, 0.0, 3.0)
+    assert (a, b) == (1.0, 0.0)
+
+
+def test_fire_single_site_reaches_uniaxial_s0(oracle_mod):
+    o = oracle_mod.Oracle((1, 1, 1), A, B, C, 2.32, 0.5, 0.3)
+    q0 = np.array([[0.30], [0.05], [-0.02], [-0.12], [0.04]])
+    params = dict(synth.FIRE_DEFAULTS, max_iter=200000, force_tol=1e-12)
+    q, v, F, st = o.fire(q0, params, 200000)
+    assert st["status"] == oracle_mod.CONVERGED
+    ev, _ = oracle_mod.eig_sym3(q[:, 0])
+    S0 = o.S0
+    assert np.allclose(ev, [S0, -S0 / 2, -S0 / 2], atol=1e-10)
+    assert abs(o.energy(q)[0] - f_of_S(S0)) < 1e-14
+
+
+def test_fire_fixed_point_and_descent(oracle_mod):
+    o = oracle_mod.Oracle((4, 4, 4), A, B, C, 2.32)
+    n = synth.random_directors(1, 5)
+    q = np.repeat(synth.uniaxial_q(n, o.S0), o.N, axis=1)
+    params = dict(synth.FIRE_DEFAULTS, max_iter=100, force_tol=1e-12)
+    q2, v, F, st = o.fire(q, params, 10)
+    assert st["status"] == oracle_mod.CONVERGED and st["iter"] == 0
+    assert np.array_equal(q2, q)
+    # from random directors the energy stays above N f0 and goes down
+    q = synth.random_uniaxial_q((4, 4, 4), 3)
+    E0 = o.energy(q)[0]
+    params = dict(synth.FIRE_DEFAULTS, max_iter=10 ** 6, force_tol=1e-9)
+    q2, v, F, st = o.fire(q, params, 400)
+    E1 = o.energy(q2)[0]
+    assert E1 < E0
+    assert E1 >= o.N * f_of_S(o.S0) - 1e-12
+
+
+def test_fire_reduces_to_velocity_verlet_on_a_harmonic_well(oracle_mod):
+    """With alpha0 = 0 (no mixing) and an unreachable N_min, and while P > 0,
+    FIRE is plain velocity Verlet.  For f = A/2 tr Q^2 with only Q_xy set,
+    f = A q1^2 and F = -omega^2 q1 with omega^2 = 2A; one Verlet step of size
+    h is the linear map [q, v] -> [q (1 - h^2 w2/2) + h v,
+    v (1 - h^2 w2/2) - h w2 q (1 - h^2 w2/4)] (textbook form)."""
+    Ah, h = 0.5, 0.1
+    w2 = 2 * Ah
+    o = oracle_mod.Oracle((1, 1, 1), Ah, 0.0, 0.0, 1.0)
+    q = np.zeros((5, 1)); q[1, 0] = 1.0
+    params = dict(dt0=h, dt_max=1.0, alpha0=0.0, f_alpha=1.0, f_inc=1.0, f_dec=0.5,
+                  n_min=10 ** 6, max_iter=10 ** 6, force_tol=0.0)
+    M = np.array([[1 - h * h * w2 / 2, h], [-h * w2 * (1 - h * h * w2 / 4), 1 - h * h * w2 / 2]])
+    for k in (1, 5, 12):
+        qk, vk, Fk, st = o.fire(q, params, k)
+        want = np.linalg.matrix_power(M, k) @ np.array([1.0, 0.0])
+        assert st["iter"] == k
+        assert abs(qk[1, 0] - want[0]) < 1e-14 and abs(vk[1, 0] - want[1]) < 1e-14
+        assert abs(Fk[1, 0] + w2 * qk[1, 0]) < 1e-15
