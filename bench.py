@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Benchmark: FIRE site-updates/s of the fused force + FIRE step on the 512^3
+lattice (four homeotropic colloids, planar-degenerate walls, three-constant
+elasticity), in the FP32-bulk / FP64-reduction form (``value``) and the FP64
+form, with the HBM roofline of the step kernel.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
+
+One JSON line on stdout (rank 0).  Under torchrun (N > 1) every rank runs an
+independent replica of the lattice on its own GPU (the path is single-GPU;
+replicas only) and the value is the sum over ranks divided by the slowest
+rank's time.  ``--impl reference`` times the CPU oracle on a bounded sample
+of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1911_07045_b300 import synth  # noqa: E402
+
+METRIC = "FIRE site-updates/s at 512^3 (FP32 vs FP64), % HBM peak; served p50/p99 latency"
+UNIT = "site-updates/s"
+# algorithmic bytes per site-update: the FIRE state that must persist, q and
+# v (5 components each), read and written, plus the 1-byte site mask
+ALG_BYTES = {"fp32": 4 * 5 * 4 + 1, "fp64": 4 * 5 * 8 + 1}
+# bytes the stored-force design moves: q, v, F read and written + mask
+DESIGN_BYTES = {"fp32": 6 * 5 * 4 + 1, "fp64": 6 * 5 * 8 + 1}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6400.0), "measured"
+    return 6400.0, "fallback"
+
+
+# ---- distributed plumbing ------------------------------------------------------
+
+class Dist:
+    def __init__(self, backend=None):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            if backend is None:
+                import torch
+                backend = "nccl" if torch.cuda.is_available() else "gloo"
+            dist.init_process_group(backend)
+            self.pg = dist
+            self.backend = backend
+
+    def barrier(self):
+        if self.pg:
+            if self.backend == "nccl":
+                import torch
+                self.pg.barrier(device_ids=[self.local])
+            else:
+                self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        dev = f"cuda:{self.local}" if self.backend == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        dev = f"cuda:{self.local}" if self.backend == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def aggregate(dist: Dist, units: float, seconds: float):
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    tmax = dist.max(seconds)
+    total = dist.sum(units)
+    return total / tmax, tmax
+
+
+# ---- clocks during the timed region ---------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---- our arm ------------------------------------------------------------------------
+
+def run_form(precision: str, L: int, steps: int, warmup: int, dist: Dist, sampler_gpu: int):
+    import torch
+    from paper_1911_07045_b300 import lqmin
+    cfg = synth.config_large(L)
+    stream = torch.cuda.Stream()
+    prec = lqmin.LQ_FP32_BULK_FP64_RED if precision == "fp32" else lqmin.LQ_FP64
+    s = lqmin.solver_for(cfg, precision=prec, stream=stream.cuda_stream)
+    nsim, nrec = s.geometry_info()
+    s.init_random_uniaxial(cfg["seed"])
+    # fixed-step run: a tolerance of 0 never converges, so every step is done
+    p = lqmin.fire_params(**dict(synth.FIRE_DEFAULTS, max_iter=10 ** 12, force_tol=0.0))
+    r = s.step(p, warmup)
+    assert r.fire_status == lqmin.FIRE_RUNNING, r.as_dict()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(sampler_gpu) as clk:
+        e0.record(stream)
+        r = s.step(p, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    ok = r.fire_status == lqmin.FIRE_RUNNING and r.iterations == warmup + steps
+    N = L ** 3
+    value, tmax = aggregate(dist, N * steps, sec)
+    per_launch = sec / steps
+    out = dict(value=value, ms_per_step=tmax / steps * 1e3, per_launch_s=per_launch, ok=ok,
+               clocks=clk.summary(), nsim=nsim, nanchored=nrec, N=N,
+               max_force=r.max_force, launches=steps)
+    # end to end through the C interface with host buffers: upload q0 from
+    # pinned memory, read the FIRE residual back after every step, download q
+    q_host = torch.empty((5, N), dtype=torch.float64, pin_memory=True).numpy()
+    s.init_random_uniaxial(cfg["seed"])
+    s._ck(s.lib.lq_get_q(s.h, lqmin._ptr(q_host)))   # the start state, in pinned memory
+    k_e2e = max(3, min(steps, 20))
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.set_q(q_host)
+    for _ in range(k_e2e):
+        r = s.step(p, 1)        # returns the residual (max |F|) to the host
+    s._ck(s.lib.lq_get_q(s.h, lqmin._ptr(q_host)))
+    t1 = time.perf_counter()
+    dist.barrier()
+    e2e_val, _ = aggregate(dist, N * k_e2e, t1 - t0)
+    out["e2e"] = dict(value=e2e_val, unit=UNIT, steps=k_e2e,
+                      h2d_bytes_per_step=int(5 * N * 8 / k_e2e),
+                      d2h_bytes_per_step=int((5 * N * 8) / k_e2e + 160))
+    s.close()
+    return out
+
+
+def cpu_baseline(L_sample=128, steps=6):
+    """The oracle as it stands, on the host cores: FIRE iterations on a
+    L_sample^3 lattice with the same structure (colloids scaled by L/512,
+    planar walls, three constants)."""
+    import oracle
+    oracle.build()
+    cfg = synth.config_large(L_sample)
+    o = oracle.Oracle(cfg["shape"], synth.A_5CB, synth.B_5CB, synth.C_5CB, cfg["L1"], cfg["L2"],
+                      cfg["L3"], objects=cfg["objects"])
+    q = synth.random_uniaxial_q(cfg["shape"], cfg["seed"])
+    params = dict(synth.FIRE_DEFAULTS, max_iter=10 ** 9, force_tol=0.0)
+    q, v, F, st = o.fire(q, params, 0)           # initial force, not timed
+    t0 = time.perf_counter()
+    q, v, F, st = o.fire(q, params, steps, state=st, v=v, F=F)
+    dt = time.perf_counter() - t0
+    return {"value": o.N * steps / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{steps} FIRE iterations of the FP64 oracle on a {L_sample}^3 lattice with the "
+                      f"same structure (4 colloids scaled by {L_sample}/512, planar walls, 3 constants)",
+            "seconds": dt}
+
+
+def main_ours(args, dist: Dist):
+    import torch
+    torch.cuda.set_device(dist.local)
+    peak, peak_kind = measured_peaks()
+    forms = {}
+    for prec in args.precision.split(","):
+        forms[prec] = run_form(prec, args.size, args.steps, args.warmup, dist, dist.local)
+    head = "fp32" if "fp32" in forms else next(iter(forms))
+    h = forms[head]
+    # roofline of the step kernel: algorithmic bytes per launch over the
+    # device time per launch (CUDA events around the timed launches)
+    rl = {}
+    for k, f in forms.items():
+        ach = ALG_BYTES[k] * f["N"] / f["per_launch_s"] / 1e9
+        rl[k] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                 "frac": round(ach / peak, 4), "traffic": None,
+                 "design_bytes_per_site": DESIGN_BYTES[k], "alg_bytes_per_site": ALG_BYTES[k],
+                 "peak_kind": peak_kind}
+    line = {
+        "metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": dist.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": h["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if head == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": f"{args.size}^3 lattice, 4 homeotropic colloids (W=5.3), planar "
+                               f"walls z=0,{args.size - 1} (W=1), L1/L2/L3=2.32/0.5/0.3, random "
+                               f"uniaxial start (seed 3)",
+                   "form": head, "sites_per_gpu": h["N"], "simulated_sites": h["nsim"],
+                   "anchored_sites": h["nanchored"],
+                   "parallelism": f"replicas x{dist.world}" if dist.world > 1 else "1 GPU",
+                   "l2": "inputs larger than L2 (state > 126 MB)"},
+        "roofline": rl[head],
+        "forms": {k: {"value": f["value"], "ms_per_step": f["ms_per_step"], "roofline": rl[k],
+                      "clocks": f["clocks"], "valid": f["ok"]} for k, f in forms.items()},
+        "e2e": h["e2e"],
+        "gpu_launches": sum(f["launches"] for f in forms.values()),
+        "clocks": h["clocks"],
+    }
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if not all(f["ok"] for f in forms.values()):
+        line["invalid"] = "FIRE stopped before all timed steps ran"
+    return line
+
+
+def main_reference(args, dist: Dist):
+    """CPU oracle as the reference arm: each step is one FIRE iteration of
+    the oracle on a bounded 96^3 sample of the workload."""
+    if dist.rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    Ls = 96
+    cfg = synth.config_large(Ls)
+    o = oracle.Oracle(cfg["shape"], synth.A_5CB, synth.B_5CB, synth.C_5CB, cfg["L1"], cfg["L2"],
+                      cfg["L3"], objects=cfg["objects"])
+    q = synth.random_uniaxial_q(cfg["shape"], cfg["seed"])
+    params = dict(synth.FIRE_DEFAULTS, max_iter=10 ** 9, force_tol=0.0)
+    q, v, F, st = o.fire(q, params, 0)
+    q, v, F, st = o.fire(q, params, args.warmup, state=st, v=v, F=F)
+    t0 = time.perf_counter()
+    q, v, F, st = o.fire(q, params, args.steps, state=st, v=v, F=F)
+    sec = time.perf_counter() - t0
+    val = o.N * args.steps / sec
+    sample = (f"each step = 1 FIRE iteration of the FP64 oracle on a {Ls}^3 lattice with the same "
+              f"structure (colloids scaled by {Ls}/512, planar walls, 3 constants)")
+    return {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": dist.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.size}^3 lattice workload, sampled at {Ls}^3",
+                       "form": "fp64 oracle"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=512)
+    ap.add_argument("--precision", default="fp32,fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    dist = Dist(backend="gloo" if args.impl == "reference" else None)
+    try:
+        line = main_reference(args, dist) if args.impl == "reference" else main_ours(args, dist)
+        if dist.rank == 0 and line is not None:
+            print(json.dumps(line), flush=True)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

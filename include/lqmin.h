@@ -1,0 +1,227 @@
+/*
+ * lqmin.h -- C interface of the B300 (sm_103a) lattice Landau-de Gennes
+ * minimiser: force on the five-component Q-tensor lattice (bulk, averaged
+ * one-sided-difference distortion, anchoring) fused with FIRE steps.
+ *
+ * Paper: D. M. Sussman and D. A. Beller, "Fast, scalable, and interactive
+ * software for Landau-de Gennes numerical modeling of nematic topological
+ * defects" (arXiv:1911.07045).  Each call names the passage that defines the
+ * operation it performs.
+ *
+ * Conventions shared by every call
+ *   * Lattice sites (x, y, z), 0 <= x < nx etc.; linear index
+ *     i = (z*ny + y)*nx + x.  Spacing is 1 lattice unit (section III.B).
+ *   * A Q field is five arrays of N = nx*ny*nz doubles, structure of arrays:
+ *     q[c*N + i] for c = 0..4 = (Qxx, Qxy, Qxz, Qyy, Qyz); Qzz = -Qxx - Qyy
+ *     (section III.B: five independent degrees of freedom per site).
+ *   * Forces are -dF/dq over those five variables (section III.B, gradient
+ *     by explicit differentiation of the discrete energy), 0 at object sites.
+ *   * Host pointers are owned by the caller and only read or written during
+ *     the call.  Device state is owned by the solver until lq_destroy.
+ *   * Every call returns an lq_status; on failure lq_last_error() gives a
+ *     message.  No call aborts or exits.  Calls on one solver must not
+ *     overlap (the solver is not thread-safe); distinct solvers may be used
+ *     from different threads.
+ *   * All device work is issued on the CUDA stream given to lq_create; the
+ *     calls that return host data synchronise that stream.
+ */
+#ifndef LQMIN_H
+#define LQMIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lq_solver lq_solver;
+
+typedef enum {
+    LQ_OK = 0,
+    LQ_EINVAL = 1,          /* bad argument or state; nothing changed */
+    LQ_ENOMEM = 2,          /* device or host allocation failed */
+    LQ_ECUDA = 3,           /* a CUDA call failed; message has the CUDA error */
+    LQ_ENOTCONVERGED = 4,   /* max_iter reached before the force tolerance */
+    LQ_ETIMEOUT = 5,        /* wall-clock limit reached */
+    LQ_EDIVERGED = 6,       /* a FIRE reduction became NaN or infinite */
+    LQ_EBUSY = 7            /* work still running (server polling) */
+} lq_status;
+
+typedef enum {
+    LQ_FP64 = 0,                 /* state, stencil and reductions in FP64 */
+    LQ_FP32_BULK_FP64_RED = 1    /* state and stencil/bulk arithmetic in FP32,
+                                    FIRE reductions, residual and energy in FP64 */
+} lq_precision;
+
+/* Lattice, section III.B.  spacing must be 1 (lattice units).
+   periodic[k] != 0 wraps axis k; otherwise the lattice edge ends the
+   one-sided differences along k (no neighbour beyond it). */
+typedef struct {
+    int nx, ny, nz;
+    double spacing;
+    int periodic[3];
+} lq_lattice;
+
+/* Material constants in lattice units.  Bulk A, B, C: Eq. (fphase).
+   Distortion L1, L2, L3: Eq. (fdistortionFull); L4 and L6 must be 0.
+   n_constants = 1 uses the one-constant form Eq. (fd1) (L2 = L3 = 0
+   required), 3 the L1/L2/L3 form.  S0 <= 0 selects Eq. (S0def) from A, B, C;
+   it sets the preferred order of the anchoring terms. */
+typedef struct {
+    double A, B, C;
+    double L1, L2, L3, L4, L6;
+    int n_constants;
+    double S0;
+} lq_material;
+
+/* Anchoring of a surface, section II (boundary free energy):
+   ND_HOMEOTROPIC  Nobili-Durand W tr((Q - Q0)^2), Q0 = 3/2 S0 (nu nu - I/3)
+                   with nu the surface normal;
+   ND_ORIENTED     the same with the preferred director dir instead of nu;
+   FG_PLANAR       Fournier-Galatola planar-degenerate W |Qt - P Qt P|^2,
+                   Qt = Q + S0 I/2, P = I - nu nu.
+   For objects without a geometric normal (site lists) dir is used as nu. */
+typedef enum {
+    LQ_ANCHOR_ND_HOMEOTROPIC = 0,
+    LQ_ANCHOR_ND_ORIENTED = 1,
+    LQ_ANCHOR_FG_PLANAR = 2
+} lq_anchor_kind;
+
+typedef struct {
+    int kind;       /* lq_anchor_kind */
+    double W;       /* anchoring strength (lattice units) */
+    double dir[3];  /* preferred director or normal, see above; need not be unit */
+} lq_anchoring;
+
+/* FIRE parameters, Algorithm 1 (after Bitzek et al. 2006).  Velocity Verlet
+   steps of size dt; alpha mixes v toward |v| F/|F|; after more than n_min
+   consecutive steps with P = F.v > 0, dt <- min(dt f_inc, dt_max) and
+   alpha <- alpha f_alpha; when P <= 0, dt <- dt f_dec, alpha <- alpha0,
+   v <- 0.  Converged when max over sites of the five-component force norm
+   is below force_tol.  wall_timeout_s <= 0 disables the wall-clock limit. */
+typedef struct {
+    double dt0, dt_max, alpha0, f_alpha, f_inc, f_dec;
+    int n_min;
+    int64_t max_iter;
+    double force_tol;
+    double wall_timeout_s;
+} lq_fire_params;
+
+typedef enum { LQ_FIRE_RUNNING = 0, LQ_FIRE_CONVERGED = 1, LQ_FIRE_MAXITER = 2,
+               LQ_FIRE_DIVERGED = 3 } lq_fire_status;
+
+/* State after the last completed FIRE iteration.  max_force is the largest
+   site force norm, rms_force = |F| / sqrt(N simulated sites), power = F.v
+   (section III.B, Fig. 2 measures); energy is filled by lq_minimize only. */
+typedef struct {
+    int64_t iterations;
+    double max_force, rms_force, norm_force, norm_velocity, power;
+    double dt, alpha;
+    int64_t npos;
+    double energy;
+    int fire_status;        /* lq_fire_status */
+    double seconds;         /* wall time of the call */
+} lq_result;
+
+/* ---- lifetime ------------------------------------------------------------- */
+
+/* Create a solver for one lattice (section III.B).  cuda_stream is a
+   cudaStream_t (NULL = the default stream); precision is an lq_precision.
+   Allocates the device state: 2 x (q, v, F) buffers, 1-byte site masks and
+   the FIRE reduction scratch.  LQ_EINVAL for non-positive sizes, spacing
+   != 1, L4/L6 != 0, or n_constants not 1 or 3. */
+lq_status lq_create(const lq_lattice *lattice, const lq_material *material,
+                    int precision, void *cuda_stream, lq_solver **out);
+/* Free all device and host memory of the solver (NULL is accepted). */
+void lq_destroy(lq_solver *s);
+/* Message of the last failed call on this solver (never NULL). */
+const char *lq_last_error(const lq_solver *s);
+/* Message of the last failed lq_create in this thread. */
+const char *lq_create_error(void);
+
+/* ---- geometry: objects and boundary sites (section III.B "type" per site;
+        section V simple objects and custom boundary files) ----------------- */
+
+/* Wall: every site with coord[axis] == plane becomes an object site; its
+   simulated face neighbours are boundary sites with normal e_axis. */
+lq_status lq_add_wall(lq_solver *s, int axis, int plane, const lq_anchoring *a);
+/* Sphere: sites with |x - c|^2 <= R^2 (minimum image along periodic axes)
+   are object sites; boundary normal (x - c)/|x - c|. */
+lq_status lq_add_sphere(lq_solver *s, const double c[3], double radius,
+                        const lq_anchoring *a);
+/* Custom object: the n listed sites (xyz[3*t..3*t+2]) become object sites;
+   their simulated face neighbours take anchoring a (dir used as normal).
+   Sites outside the lattice are ignored. */
+lq_status lq_add_object_sites(lq_solver *s, int64_t n, const int32_t *xyz,
+                              const lq_anchoring *a);
+/* Custom boundary records: each listed simulated site gets its own
+   anchoring per_site[t] (dir is the preferred director or normal).
+   When several objects claim a boundary site, the first one added wins. */
+lq_status lq_add_anchored_sites(lq_solver *s, int64_t n, const int32_t *xyz,
+                                const lq_anchoring *per_site);
+/* Number of simulated sites and of sites carrying an anchoring record
+   (builds the geometry if it changed). */
+lq_status lq_geometry_info(lq_solver *s, int64_t *n_simulated, int64_t *n_anchored);
+/* Per-site mask byte: bit0 simulated, bit1 anchored, bits 2..7 neighbour
+   simulated along +x, -x, +y, -y, +z, -z.  out holds N bytes. */
+lq_status lq_get_mask(lq_solver *s, uint8_t *out);
+
+/* ---- state in and out ------------------------------------------------------ */
+
+/* Set Q from a host array (5*N doubles, layout above).  Resets FIRE. */
+lq_status lq_set_q(lq_solver *s, const double *q_host);
+/* Set Q from a device array of 5*N elements, dtype 0 = double, 1 = float;
+   the copy runs on the solver stream.  Resets FIRE. */
+lq_status lq_set_q_device(lq_solver *s, const void *dptr, int dtype);
+/* Random uniaxial start (section V: random initial Q, reproducible): site i
+   gets 3/2 S (n n - I/3) with n uniform on the sphere from SplitMix64
+   outputs 2i+1 (z = 2u-1) and 2i+2 (phi = 2 pi u) of the stream seed.
+   S <= 0 selects S0.  Resets FIRE. */
+lq_status lq_init_random_uniaxial(lq_solver *s, uint64_t seed, double S);
+/* Copy the current Q / FIRE velocity / FIRE force to a host array (5*N). */
+lq_status lq_get_q(lq_solver *s, double *out);
+lq_status lq_get_velocity(lq_solver *s, double *out);
+lq_status lq_get_force(lq_solver *s, double *out);
+/* Evaluate F = -dF/dq at the current Q (section III.B) without touching the
+   FIRE state; out = 5*N doubles. */
+lq_status lq_force(lq_solver *s, double *out);
+/* Total free energy of the current Q, summed in FP64: total and parts
+   (bulk Eq. (fphase), distortion Eq. (fdistortionFull) averaged over allowed
+   differences, anchoring).  Either pointer may be NULL. */
+lq_status lq_energy(lq_solver *s, double *total, double parts[3]);
+/* Largest eigenvalue of Q per site (the director's order, section II;
+   defects are where it drops, section V); 0 at object sites.  N doubles. */
+lq_status lq_order_field(lq_solver *s, double *S_out);
+
+/* ---- FIRE (Algorithm 1) ------------------------------------------------------- */
+
+/* Start FIRE from the current Q: v = 0, F = F(q), dt = dt0, alpha = alpha0. */
+lq_status lq_fire_reset(lq_solver *s, const lq_fire_params *p);
+/* Run up to n more FIRE iterations (starting FIRE first if needed); stops
+   early at convergence, max_iter or divergence.  out may be NULL. */
+lq_status lq_step(lq_solver *s, const lq_fire_params *p, int64_t n, lq_result *out);
+/* Minimise from the current Q to force_tol (section V: until a force
+   tolerance or the maximum number of iterations).  Returns LQ_OK when
+   converged, LQ_ENOTCONVERGED at max_iter, LQ_EDIVERGED, LQ_ETIMEOUT. */
+lq_status lq_minimize(lq_solver *s, const lq_fire_params *p, lq_result *out);
+/* Read the FIRE counters without running anything. */
+lq_status lq_fire_result(lq_solver *s, lq_result *out);
+
+/* Checkpoint of Q, v, F and the FIRE scalars.  With buf == NULL, *bytes
+   receives the size needed.  Resuming from a checkpoint continues the run
+   bit-for-bit. */
+lq_status lq_get_state(lq_solver *s, void *buf, size_t *bytes);
+lq_status lq_set_state(lq_solver *s, const void *buf, size_t bytes);
+
+/* ---- tuning ---------------------------------------------------------------------- */
+
+/* Number of z planes one thread block marches through (0 = automatic). */
+lq_status lq_set_zchunk(lq_solver *s, int zchunk);
+/* Bytes of device memory held by the solver. */
+size_t lq_device_bytes(const lq_solver *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LQMIN_H */

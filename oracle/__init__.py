@@ -27,15 +27,37 @@ WALL, SPHERE, SITES, ANCHORED = 0, 1, 2, 3
 RUNNING, CONVERGED, MAXITER, DIVERGED = 0, 1, 2, 3
 
 
+def _host_tag() -> str:
+    """CPU model and flags: -march=native code is only reused on the same CPU."""
+    model, flags = "", ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name") and not model:
+                model = line.split(":", 1)[1].strip()
+            if line.startswith("flags") and not flags:
+                flags = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import hashlib
+    return hashlib.sha1((model + "|" + flags).encode()).hexdigest()
+
+
 def build(force: bool = False) -> str:
-    """Compile ``liblqoracle.so`` with gcc + OpenMP (idempotent)."""
+    """Compile ``liblqoracle.so`` with gcc -O3 -march=native + OpenMP; rebuilt
+    when the sources change or the host CPU differs from the build host."""
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
+    tagfile = _LIB + ".host"
+    tag = _host_tag()
+    stale = (not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest
+             or not os.path.exists(tagfile) or open(tagfile).read().strip() != tag)
+    if force or stale:
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(
             ["gcc", "-O3", "-march=native", "-fopenmp", "-fPIC", "-shared", "-std=c99",
              "-Wall", _SRC, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
+        with open(tagfile, "w") as f:
+            f.write(tag + "\n")
     return _LIB
 
 

@@ -1,0 +1,91 @@
+// lq_common.cuh -- device data layout and small algebra shared by the kernels.
+//
+// Layout in HBM (one solver):
+//   q, v, F      structure of arrays, component c of site i at [c*N + i],
+//                two copies (ping-pong) because a FIRE step reads the
+//                neighbours' old state while it writes the new one;
+//   mask         one byte per site (bits below);
+//   anchoring    records of the anchored sites, sorted by site index, found
+//                through a per-(z, y)-row offset table and the x coordinate;
+//   FireDev      the FIRE scalars, the coefficients of the next step and the
+//                last reductions, written only by the last block of a step.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lq {
+
+// mask bits
+constexpr uint8_t M_SIM = 1u << 0;   // simulated (bulk or boundary) site
+constexpr uint8_t M_ANCH = 1u << 1;  // carries an anchoring record
+// neighbour simulated along +x, -x, +y, -y, +z, -z: bit 2 + 2k (+), 3 + 2k (-)
+__host__ __device__ constexpr uint8_t m_fwd(int k) { return (uint8_t)(1u << (2 + 2 * k)); }
+__host__ __device__ constexpr uint8_t m_bwd(int k) { return (uint8_t)(1u << (3 + 2 * k)); }
+
+enum : int { FIRE_RUNNING = 0, FIRE_CONVERGED = 1, FIRE_MAXITER = 2, FIRE_DIVERGED = 3 };
+
+// Anchoring record of one boundary site.  kind 1: Nobili-Durand, a = q0 (5
+// components of Q0); kind 2: Fournier-Galatola, a[0..2] = unit normal nu.
+template <typename T>
+struct AnchorRec {
+    T a[5];
+    T W;
+    int kind;
+    int pad;
+};
+
+struct FireDev {
+    // parameters
+    double dt0, dt_max, alpha0, f_alpha, f_inc, f_dec, tol;
+    long long n_min, max_iter;
+    // scalars of Algorithm 1
+    double dt, alpha;
+    long long npos, iter, kcount;
+    int status, cur;          // cur: which ping-pong buffer holds the state
+    // coefficients of the next step: v_mix = cv v + cF F, drift with dt_step
+    double cv, cF, dt_step;
+    // reductions of the last evaluated state
+    double P, F2, v2, r2;
+    long long nsim;
+    unsigned int counter;     // last-block-done ticket
+    unsigned int pad;
+};
+
+struct Geometry {
+    const uint8_t *mask;
+    const int *row_start;     // nz*ny + 1 offsets into the record arrays
+    const int *rec_x;         // x coordinate of each record
+    const void *recs;         // AnchorRec<T>
+};
+
+struct LatticeDev {
+    int nx, ny, nz;
+    int px, py, pz;           // periodic flags
+    long long N;
+};
+
+// ---- 5-component algebra --------------------------------------------------
+// A symmetric traceless 3x3 stored as q = (xx, xy, xz, yy, yz).
+
+template <typename T>
+__device__ __forceinline__ T sym(const T *q, int i, int j) {
+    // entry (i, j) of the full tensor
+    if (i > j) { int t = i; i = j; j = t; }
+    if (i == 0) return q[j];                 // xx, xy, xz
+    if (i == 1) return j == 1 ? q[3] : q[4]; // yy, yz
+    return -q[0] - q[3];                     // zz
+}
+
+// J^T of a symmetric traceless tensor: the derivative with respect to the
+// five components of <G, Q(q)> when G = that tensor.
+template <typename T>
+__device__ __forceinline__ void jt_sym(const T *d, T *out) {
+    out[0] = T(2) * d[0] + d[3];
+    out[1] = T(2) * d[1];
+    out[2] = T(2) * d[2];
+    out[3] = d[0] + T(2) * d[3];
+    out[4] = T(2) * d[4];
+}
+
+}  // namespace lq

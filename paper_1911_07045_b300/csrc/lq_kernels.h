@@ -1,0 +1,79 @@
+// lq_kernels.h -- host-side entry points of the kernels (internal to the library).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lq_common.cuh"
+
+namespace lq {
+
+struct StepLaunch {
+    void *q[2], *v[2], *F[2];
+    void *Fonly;
+    const void *qonly;
+    Geometry g;
+    LatticeDev L;
+    double A, B, C, L1, L2, L3, S0;
+    FireDev *st;
+    double *partials;
+    int zchunk, force_only, fp32, three;
+};
+
+dim3 step_grid(const LatticeDev &L, int zchunk, int tx, int ty);
+void step_tile(int fp32, int three, int *tx, int *ty);
+cudaError_t prepare_fire_step(int fp32, int three);
+cudaError_t launch_fire_step(const StepLaunch &sl, cudaStream_t stream);
+
+// geometry construction (device)
+struct AnchorSpecDev {
+    int kind;
+    double W;
+    double dir[3];
+};
+struct GeoObjDev {
+    int type;                 // 0 wall, 1 sphere, 2 object sites, 3 anchored sites
+    int axis, plane;
+    double c[3], R;
+    AnchorSpecDev spec;
+    const int32_t *xyz;       // device copy of a site list
+    long long n;
+    const AnchorSpecDev *per_site;
+};
+cudaError_t geo_owner(const LatticeDev &L, const GeoObjDev *objs_dev, int nobj, int *owner,
+                      cudaStream_t s);
+cudaError_t geo_scatter_sites(const LatticeDev &L, const int32_t *xyz, long long n, int id,
+                              int *owner, cudaStream_t s);
+cudaError_t geo_scatter_anchored(const LatticeDev &L, const int32_t *xyz, long long n, int id,
+                                 unsigned long long *xclaim, cudaStream_t s);
+cudaError_t geo_mask(const LatticeDev &L, const int *owner, const unsigned long long *xclaim,
+                     uint8_t *mask, cudaStream_t s);
+cudaError_t geo_row_count(const LatticeDev &L, const uint8_t *mask, int *counts, cudaStream_t s);
+cudaError_t geo_fill(const LatticeDev &L, const uint8_t *mask, const int *owner,
+                     const unsigned long long *xclaim, const GeoObjDev *objs_dev, double S0,
+                     const int *row_start, int *rec_x, void *recs, int fp32, cudaStream_t s);
+
+// state helpers
+cudaError_t zero_object_sites(const LatticeDev &L, const uint8_t *mask, void *const *arrays,
+                              int narrays, int fp32, cudaStream_t s);
+cudaError_t convert_f64_to_state(const double *src, void *dst, long long n, int fp32,
+                                 cudaStream_t s);
+cudaError_t convert_f32_to_state(const float *src, void *dst, long long n, int fp32,
+                                 cudaStream_t s);
+cudaError_t state_to_f64(const void *src, double *dst, long long n, int fp32, cudaStream_t s);
+// out = cv v + cF F (the velocity after the pending FIRE mixing), as doubles
+cudaError_t mixed_velocity(const void *v, const void *F, const FireDev *st, double *out,
+                           long long n, int fp32, cudaStream_t s);
+cudaError_t init_random_uniaxial(const LatticeDev &L, const uint8_t *mask, unsigned long long seed,
+                                 double S, void *q, int fp32, cudaStream_t s);
+cudaError_t count_simulated(const LatticeDev &L, const uint8_t *mask, unsigned long long *out,
+                            cudaStream_t s);
+
+// readback
+cudaError_t energy_parts(const LatticeDev &L, const Geometry &g, const void *q, int fp32,
+                         double A, double B, double C, double L1, double L2, double L3, double S0,
+                         double *partials, int max_blocks, double *out3, cudaStream_t s);
+cudaError_t order_field(const LatticeDev &L, const uint8_t *mask, const void *q, int fp32,
+                        double *S_out, cudaStream_t s);
+
+}  // namespace lq

@@ -1,0 +1,688 @@
+// step.cu -- one FIRE iteration as one kernel: velocity mixing of the
+// previous iteration, Verlet drift, the Landau-de Gennes force, the Verlet
+// kick, and the FIRE reductions with the scalar update done by the last block.
+//
+// Force (section III.B).  The discrete energy is the sum over simulated
+// sites of f_bulk (Eq. fphase) + the distortion density (Eq.
+// fdistortionFull) averaged over every allowed forward/backward difference
+// combination (Eq. onesidedderivatives) + the anchoring terms (section II).
+// The force is minus its derivative with respect to every q_i(x_j).
+//
+// Factorised form used here (exact rearrangement of that average).  For a
+// site i and axis k let n_k(i) be the number of allowed one-sided
+// differences, D_k^s the difference tensor for choice s, m_k = the mean of
+// the allowed D_k^s.  Since the choices along different axes are independent
+// and equally weighted, the combination average of Eq. (fdistortionFull) is
+//   sum_k [ L1/2 <|D_k|^2> + (L2+L3)/2 <|D_k[:,k]|^2> ]
+//   + L2/2 sum_{j!=k} m_j[:,j].m_k[:,k] + L3/2 sum_{j!=k} m_j[:,k].m_k[:,j].
+// Each link (i, i+e_k) carries one difference Delta; the energy derivative
+// with respect to it ("flux") is
+//   Phi = (w_f(i) + w_b(i+e_k)) [L1 Delta + (L2+L3) col_k(Delta[:,k])]
+//         + w_f(i) X_k(i) + w_b(i+e_k) X_k(i+e_k),   w = 1/n_k,
+// where X_k(i) holds the cross terms: column k = L2 (m_a[:,a] + m_b[:,b]),
+// column a = L3 m_a[:,k], column b = L3 m_b[:,k] ({a, b} = the other axes).
+// The distortion gradient at j is sum_k (Phi_k(j - e_k) - Phi_k(j)), mapped
+// to the five components by J^T.  One-constant: Phi = (w_f + w_b) L1 Delta.
+//
+// Schedule.  A block owns a TX x TY column of sites and marches along z
+// through zchunk planes.  Each plane of drifted Q (tile + 1-site ring incl.
+// corners) is staged once in shared memory (4-slot ring over z); the z-link
+// flux and the z cross terms are carried in registers from plane to plane.
+// Three-constant: the in-plane cross terms X_x, X_y of the tile and its ring
+// are computed once per plane into shared memory (two slots).
+//
+// FIRE (Algorithm 1).  Iteration n of the paper is: drift q += dt v +
+// dt^2/2 F, new force F', kick v += dt/2 (F + F'), reductions P = F.v, |F|,
+// |v|, then mixing v <- (1-alpha) v + alpha |v| F/|F| and the P test.  The
+// mixing needs the global reductions, so it is applied at the start of the
+// NEXT kernel: v_mix = cv v + cF F with (cv, cF, dt) written by the last
+// block of the previous kernel.  The first kernel after a reset (dt = 0,
+// cv = cF = 0) only evaluates F(q0).
+#include <cfloat>
+#include <cstdio>
+
+#include "lq_common.cuh"
+#include "lq_kernels.h"
+
+namespace lq {
+
+template <typename T>
+struct StepArgs {
+    T *q[2], *v[2], *F[2];
+    T *Fonly;                 // force-only output (5 N)
+    const T *qonly;           // force-only input (5 N)
+    Geometry g;
+    LatticeDev L;
+    T A, B, C, L1, L2, L3, S0;
+    FireDev *st;
+    double *partials;         // 4 doubles per block
+    int zchunk;
+    int force_only;
+};
+
+__device__ __forceinline__ int wrap_coord(int g, int n, int periodic) {
+    if (g >= 0 && g < n) return g;
+    if (periodic) {
+        if (g == -1) return n - 1;
+        if (g == n) return 0;
+    }
+    return -1;
+}
+
+template <typename T>
+__device__ __forceinline__ T inv_count(uint8_t m, int k) {
+    int n = ((m & m_fwd(k)) ? 1 : 0) + ((m & m_bwd(k)) ? 1 : 0);
+    return n == 2 ? T(0.5) : T(1);
+}
+
+// J^T of the matrix whose column k is Delta[:, k] (all else 0)
+template <int K, typename T>
+__device__ __forceinline__ void jt_col(const T *d, T *o) {
+    if (K == 0) { o[0] = d[0]; o[1] = d[1]; o[2] = d[2]; o[3] = T(0); o[4] = T(0); }
+    if (K == 1) { o[0] = T(0); o[1] = d[1]; o[2] = T(0); o[3] = d[3]; o[4] = d[4]; }
+    if (K == 2) { o[0] = d[0] + d[3]; o[1] = T(0); o[2] = d[2]; o[3] = d[0] + d[3]; o[4] = d[4]; }
+}
+
+// J^T X_k for the cross terms, from the means m_a, m_b of the other axes
+template <int K, typename T>
+__device__ __forceinline__ void jt_cross(const T *ma, const T *mb, T L2, T L3, T *o) {
+    constexpr int a = K == 0 ? 1 : 0;
+    constexpr int b = K == 2 ? 1 : 2;
+    T X[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        X[i][K] = L2 * (sym(ma, i, a) + sym(mb, i, b));
+        X[i][a] = L3 * sym(ma, i, K);
+        X[i][b] = L3 * sym(mb, i, K);
+    }
+    o[0] = X[0][0] - X[2][2];
+    o[1] = X[0][1] + X[1][0];
+    o[2] = X[0][2] + X[2][0];
+    o[3] = X[1][1] - X[2][2];
+    o[4] = X[1][2] + X[2][1];
+}
+
+template <typename T, int TX, int TY>
+struct Smem {
+    static constexpr int SX = TX + 2, SY = TY + 2, PL = SX * SY;
+    T *Q;        // [4][5][PL]
+    T *X;        // [2][2][5][PL]
+    uint8_t *M;  // [4][PL]
+    __device__ __forceinline__ T &q(int slot, int c, int lx, int ly) { return Q[(slot * 5 + c) * PL + ly * SX + lx]; }
+    __device__ __forceinline__ uint8_t &m(int slot, int lx, int ly) { return M[slot * PL + ly * SX + lx]; }
+    __device__ __forceinline__ T &x(int slot, int ax, int c, int lx, int ly) {
+        return X[((slot * 2 + ax) * 5 + c) * PL + ly * SX + lx];
+    }
+};
+
+// mean of the allowed one-sided differences along axis K at (lx, ly) of
+// plane slot sc; splus / sminus are the slots of the planes above / below
+template <int K, typename T, int TX, int TY>
+__device__ __forceinline__ void mean_diff(Smem<T, TX, TY> &S, int lx, int ly, int sc, int splus,
+                                          int sminus, T *out) {
+    uint8_t m = S.m(sc, lx, ly);
+    T f = (m & m_fwd(K)) ? T(1) : T(0);
+    T b = (m & m_bwd(K)) ? T(1) : T(0);
+    T w = (f + b == T(2)) ? T(0.5) : T(1);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        T q0 = S.q(sc, c, lx, ly), qf, qb;
+        if (K == 0) { qf = S.q(sc, c, lx + 1, ly); qb = S.q(sc, c, lx - 1, ly); }
+        if (K == 1) { qf = S.q(sc, c, lx, ly + 1); qb = S.q(sc, c, lx, ly - 1); }
+        if (K == 2) { qf = S.q(splus, c, lx, ly); qb = S.q(sminus, c, lx, ly); }
+        out[c] = w * (f * (qf - q0) + b * (q0 - qb));
+    }
+}
+
+// flux through the link (a, a + e_K); ma/mb masks, qa/qb drifted Q,
+// xa/xb the J^T X_K cross terms at both ends (three-constant only)
+template <int K, bool THREE, typename T>
+__device__ __forceinline__ void link_flux(uint8_t ma, uint8_t mb, const T *qa, const T *qb,
+                                          const T *xa, const T *xb, T L1, T L23, T *phi) {
+    if (!(ma & M_SIM) || !(ma & m_fwd(K))) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) phi[c] = T(0);
+        return;
+    }
+    T wa = inv_count<T>(ma, K), wb = inv_count<T>(mb, K);
+    T d[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) d[c] = qb[c] - qa[c];
+    if (!THREE) {
+        T w = wa + wb;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) phi[c] = w * d[c];
+    } else {
+        T j1[5], j2[5];
+        jt_sym(d, j1);
+        jt_col<K>(d, j2);
+        T w = wa + wb;
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+            phi[c] = w * (L1 * j1[c] + L23 * j2[c]) + wa * xa[c] + wb * xb[c];
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void bulk_force(const T *q, T A, T B, T C, T *out) {
+    T a = q[0], b = q[1], c = q[2], d = q[3], e = q[4], f = -a - d;
+    T s_xx = a * a + b * b + c * c;
+    T s_yy = b * b + d * d + e * e;
+    T s_zz = c * c + e * e + f * f;
+    T s_xy = a * b + b * d + c * e;
+    T s_xz = a * c + b * e + c * f;
+    T s_yz = b * c + d * e + e * f;
+    T tr2 = s_xx + s_yy + s_zz;
+    T g = A + C * tr2;
+    T jq[5];
+    jt_sym(q, jq);
+    out[0] = -(g * jq[0] + B * (s_xx - s_zz));
+    out[1] = -(g * jq[1] + B * T(2) * s_xy);
+    out[2] = -(g * jq[2] + B * T(2) * s_xz);
+    out[3] = -(g * jq[3] + B * (s_yy - s_zz));
+    out[4] = -(g * jq[4] + B * T(2) * s_yz);
+}
+
+// anchoring force of one record (Nobili-Durand or Fournier-Galatola)
+template <typename T>
+__device__ __forceinline__ void anchor_force(const T *q, const AnchorRec<T> &r, T S0, T *out) {
+    if (r.kind == 1) {
+        T d[5], j[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) d[c] = q[c] - r.a[c];
+        jt_sym(d, j);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) out[c] = -T(2) * r.W * j[c];
+    } else {
+        // G = 2 W R, R = Qt - P Qt P = nu w^T + w nu^T - (nu.w) nu nu^T, w = Qt nu
+        const T nx = r.a[0], ny = r.a[1], nz = r.a[2];
+        T hs = T(0.5) * S0;
+        T wx = q[0] * nx + q[1] * ny + q[2] * nz + hs * nx;
+        T wy = q[1] * nx + q[3] * ny + q[4] * nz + hs * ny;
+        T wz = q[2] * nx + q[4] * ny + (-q[0] - q[3]) * nz + hs * nz;
+        T nw = nx * wx + ny * wy + nz * wz;
+        T Rxx = T(2) * nx * wx - nw * nx * nx;
+        T Ryy = T(2) * ny * wy - nw * ny * ny;
+        T Rzz = T(2) * nz * wz - nw * nz * nz;
+        T Rxy = nx * wy + wx * ny - nw * nx * ny;
+        T Rxz = nx * wz + wx * nz - nw * nx * nz;
+        T Ryz = ny * wz + wy * nz - nw * ny * nz;
+        T w2 = T(2) * r.W;
+        out[0] = -w2 * (Rxx - Rzz);
+        out[1] = -w2 * T(2) * Rxy;
+        out[2] = -w2 * T(2) * Rxz;
+        out[3] = -w2 * (Ryy - Rzz);
+        out[4] = -w2 * T(2) * Ryz;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ const AnchorRec<T> *find_record(const Geometry &g, const LatticeDev &L,
+                                                           int x, int y, int z) {
+    long long row = (long long)z * L.ny + y;
+    int lo = g.row_start[row], hi = g.row_start[row + 1] - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) >> 1;
+        int xm = g.rec_x[mid];
+        if (xm == x) return reinterpret_cast<const AnchorRec<T> *>(g.recs) + mid;
+        if (xm < x) lo = mid + 1; else hi = mid - 1;
+    }
+    return nullptr;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// block-wide fixed-order reduction of 4 values into thread 0
+template <int NT>
+__device__ __forceinline__ void block_reduce4(double &p, double &f, double &w, double &r,
+                                              double *red) {
+    constexpr int NW = NT / 32;
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    p = warp_sum(p); f = warp_sum(f); w = warp_sum(w); r = warp_max(r);
+    if (lane == 0) { red[wid] = p; red[NW + wid] = f; red[2 * NW + wid] = w; red[3 * NW + wid] = r; }
+    __syncthreads();
+    if (wid == 0) {
+        p = lane < NW ? red[lane] : 0.0;
+        f = lane < NW ? red[NW + lane] : 0.0;
+        w = lane < NW ? red[2 * NW + lane] : 0.0;
+        r = lane < NW ? red[3 * NW + lane] : 0.0;
+        p = warp_sum(p); f = warp_sum(f); w = warp_sum(w); r = warp_max(r);
+    }
+    __syncthreads();
+}
+
+// FIRE scalar machine (Algorithm 1), run by one thread after the reductions
+__device__ void fire_update(FireDev *st, double P, double F2, double v2, double r2) {
+    st->P = P; st->F2 = F2; st->v2 = v2; st->r2 = r2;
+    st->cur ^= 1;
+    st->kcount += 1;
+    bool bad = !isfinite(P) || !isfinite(F2) || !isfinite(v2);
+    double rmax = sqrt(r2);
+    st->cv = 1.0; st->cF = 0.0;
+    if (st->kcount == 1) {           // the evaluation of F(q0)
+        if (bad) st->status = FIRE_DIVERGED;
+        else if (rmax < st->tol) st->status = FIRE_CONVERGED;
+        st->dt_step = st->dt;
+        return;
+    }
+    st->iter += 1;
+    if (bad) { st->status = FIRE_DIVERGED; return; }
+    if (rmax < st->tol) { st->status = FIRE_CONVERGED; return; }
+    if (st->iter >= st->max_iter) { st->status = FIRE_MAXITER; return; }
+    double a = 1.0, b = 0.0;
+    double nF = sqrt(F2), nv = sqrt(v2);
+    if (nF > 0.0) { a = 1.0 - st->alpha; b = st->alpha * nv / nF; }
+    if (P > 0.0) {
+        st->npos += 1;
+        if (st->npos > st->n_min) {
+            st->dt = fmin(st->dt * st->f_inc, st->dt_max);
+            st->alpha *= st->f_alpha;
+        }
+    } else {
+        st->npos = 0;
+        st->dt *= st->f_dec;
+        st->alpha = st->alpha0;
+        a = 0.0; b = 0.0;
+    }
+    st->cv = a; st->cF = b; st->dt_step = st->dt;
+}
+
+template <typename T, bool THREE, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY)
+fire_step_kernel(StepArgs<T> args) {
+    constexpr int NT = TX * TY;
+    using SM = Smem<T, TX, TY>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SM S;
+    S.Q = reinterpret_cast<T *>(smem_raw);
+    S.X = S.Q + 4 * 5 * SM::PL;
+    S.M = reinterpret_cast<uint8_t *>(S.X + (THREE ? 2 * 2 * 5 * SM::PL : 0));
+    __shared__ double red[4 * (NT / 32)];
+    __shared__ int am_last;
+
+    const LatticeDev L = args.L;
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * args.zchunk;
+    const int z1 = min(z0 + args.zchunk, L.nz);
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool valid = gx < L.nx && gy < L.ny;
+    const int lx = tx + 1, ly = ty + 1;
+    const long long N = L.N;
+
+    // FIRE coefficients for this step
+    int cur = 0;
+    T cv = T(0), cF = T(0), dt = T(0);
+    const T *qin, *vin, *Fin;
+    T *qout = nullptr, *vout = nullptr, *Fout;
+    if (args.force_only) {
+        qin = args.qonly; vin = args.qonly; Fin = args.qonly;
+        Fout = args.Fonly;
+    } else {
+        if (args.st->status != FIRE_RUNNING) return;
+        cur = args.st->cur;
+        cv = T(args.st->cv); cF = T(args.st->cF); dt = T(args.st->dt_step);
+        qin = args.q[cur]; vin = args.v[cur]; Fin = args.F[cur];
+        qout = args.q[cur ^ 1]; vout = args.v[cur ^ 1]; Fout = args.F[cur ^ 1];
+    }
+    const T hdt2 = T(0.5) * dt * dt;
+    const T hdt = T(0.5) * dt;
+
+    // ring sites of the staged plane: top row, bottom row, left/right columns
+    constexpr int NRING = 2 * SM::SX + 2 * TY;
+    int rx = -1, ry = -1;
+    if ((int)threadIdx.x < NRING) {
+        int r = threadIdx.x;
+        if (r < SM::SX) { rx = r; ry = 0; }
+        else if (r < 2 * SM::SX) { rx = r - SM::SX; ry = SM::SY - 1; }
+        else { r -= 2 * SM::SX; rx = (r & 1) ? SM::SX - 1 : 0; ry = 1 + (r >> 1); }
+    }
+
+    // drift and stage one site of plane z; returns v_mix and F_old
+    auto stage = [&](int slot, int sx, int sy, int z, T *vm, T *fo) {
+        int X = wrap_coord(x0 + sx - 1, L.nx, L.px);
+        int Y = wrap_coord(y0 + sy - 1, L.ny, L.py);
+        int Z = wrap_coord(z, L.nz, L.pz);
+        uint8_t m = 0;
+        T qh[5] = {T(0), T(0), T(0), T(0), T(0)};
+        if (X >= 0 && Y >= 0 && Z >= 0) {
+            long long i = ((long long)Z * L.ny + Y) * L.nx + X;
+            m = args.g.mask[i];
+            if (m & M_SIM) {
+                if (args.force_only) {
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) qh[c] = qin[c * N + i];
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) {
+                        T q = qin[c * N + i], v = vin[c * N + i], f = Fin[c * N + i];
+                        T vx = cv * v + cF * f;
+                        qh[c] = q + dt * vx + hdt2 * f;
+                        vm[c] = vx;
+                        fo[c] = f;
+                    }
+                }
+            }
+        }
+        S.m(slot, sx, sy) = m;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) S.q(slot, c, sx, sy) = qh[c];
+    };
+
+    T vm_cur[5], fo_cur[5], vm_nxt[5], fo_nxt[5];
+    T dummy_v[5], dummy_f[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) { vm_cur[c] = fo_cur[c] = vm_nxt[c] = fo_nxt[c] = T(0); }
+
+    // prologue: planes z0 - 1 and z0
+    stage((z0 - 1) & 3, lx, ly, z0 - 1, dummy_v, dummy_f);
+    if (rx >= 0) stage((z0 - 1) & 3, rx, ry, z0 - 1, dummy_v, dummy_f);
+    stage(z0 & 3, lx, ly, z0, vm_cur, fo_cur);
+    if (rx >= 0) stage(z0 & 3, rx, ry, z0, dummy_v, dummy_f);
+    __syncthreads();
+
+    const T L1 = args.L1, L23 = args.L2 + args.L3;
+    T phi_zm[5];      // flux of the link (z-1, z) at the own column
+    T xz_cur[5];      // J^T X_z at (own, z)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) { phi_zm[c] = T(0); xz_cur[c] = T(0); }
+    {
+        // link (z0-1, z0): needs X_z at both planes (three-constant)
+        T xz_m[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) xz_m[c] = T(0);
+        if (THREE) {
+            T mx[5], my[5];
+            int sm = (z0 - 1) & 3, sc = z0 & 3;
+            mean_diff<0>(S, lx, ly, sm, 0, 0, mx);
+            mean_diff<1>(S, lx, ly, sm, 0, 0, my);
+            jt_cross<2>(mx, my, args.L2, args.L3, xz_m);
+            mean_diff<0>(S, lx, ly, sc, 0, 0, mx);
+            mean_diff<1>(S, lx, ly, sc, 0, 0, my);
+            jt_cross<2>(mx, my, args.L2, args.L3, xz_cur);
+        }
+        T qa[5], qb[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) { qa[c] = S.q((z0 - 1) & 3, c, lx, ly); qb[c] = S.q(z0 & 3, c, lx, ly); }
+        link_flux<2, THREE>(S.m((z0 - 1) & 3, lx, ly), S.m(z0 & 3, lx, ly), qa, qb, xz_m, xz_cur,
+                            L1, L23, phi_zm);
+    }
+
+    double accP = 0.0, accF = 0.0, accV = 0.0, accR = 0.0;
+
+    for (int z = z0; z < z1; ++z) {
+        const int sc = z & 3, sp = (z + 1) & 3, sm = (z - 1) & 3;
+        // stage plane z + 1
+        stage(sp, lx, ly, z + 1, vm_nxt, fo_nxt);
+        if (rx >= 0) stage(sp, rx, ry, z + 1, dummy_v, dummy_f);
+        __syncthreads();
+
+        T xz_nxt[5];
+        if (THREE) {
+            const int xs = z & 1;
+            // cross terms of the tile at plane z
+            if (S.m(sc, lx, ly) & M_SIM) {
+                T mx[5], my[5], mz[5], o[5];
+                mean_diff<0>(S, lx, ly, sc, sp, sm, mx);
+                mean_diff<1>(S, lx, ly, sc, sp, sm, my);
+                mean_diff<2>(S, lx, ly, sc, sp, sm, mz);
+                jt_cross<0>(my, mz, args.L2, args.L3, o);
+#pragma unroll
+                for (int c = 0; c < 5; ++c) S.x(xs, 0, c, lx, ly) = o[c];
+                jt_cross<1>(mx, mz, args.L2, args.L3, o);
+#pragma unroll
+                for (int c = 0; c < 5; ++c) S.x(xs, 1, c, lx, ly) = o[c];
+            }
+            // ring: X_x on the left/right columns, X_y on the top/bottom rows
+            if ((int)threadIdx.x < 2 * TY) {
+                int sx = (threadIdx.x & 1) ? SM::SX - 1 : 0, sy = 1 + (threadIdx.x >> 1);
+                if (S.m(sc, sx, sy) & M_SIM) {
+                    T my[5], mz[5], o[5];
+                    mean_diff<1>(S, sx, sy, sc, sp, sm, my);
+                    mean_diff<2>(S, sx, sy, sc, sp, sm, mz);
+                    jt_cross<0>(my, mz, args.L2, args.L3, o);
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) S.x(xs, 0, c, sx, sy) = o[c];
+                }
+            } else if ((int)threadIdx.x < 2 * TY + 2 * TX) {
+                int r = threadIdx.x - 2 * TY;
+                int sx = 1 + (r >> 1), sy = (r & 1) ? SM::SY - 1 : 0;
+                if (S.m(sc, sx, sy) & M_SIM) {
+                    T mx[5], mz[5], o[5];
+                    mean_diff<0>(S, sx, sy, sc, sp, sm, mx);
+                    mean_diff<2>(S, sx, sy, sc, sp, sm, mz);
+                    jt_cross<1>(mx, mz, args.L2, args.L3, o);
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) S.x(xs, 1, c, sx, sy) = o[c];
+                }
+            }
+            // z cross term of the own column at plane z + 1
+            {
+                T mx[5], my[5];
+                mean_diff<0>(S, lx, ly, sp, 0, 0, mx);
+                mean_diff<1>(S, lx, ly, sp, 0, 0, my);
+                jt_cross<2>(mx, my, args.L2, args.L3, xz_nxt);
+            }
+            __syncthreads();
+        }
+
+        const uint8_t m0 = S.m(sc, lx, ly);
+        T q0[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) q0[c] = S.q(sc, c, lx, ly);
+
+        // z link (z, z+1) of the own column
+        T phi_zp[5];
+        {
+            T qb[5];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) qb[c] = S.q(sp, c, lx, ly);
+            link_flux<2, THREE>(m0, S.m(sp, lx, ly), q0, qb, xz_cur, THREE ? xz_nxt : xz_cur, L1,
+                                L23, phi_zp);
+        }
+
+        if (valid && (m0 & M_SIM)) {
+            T grad[5];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) grad[c] = phi_zm[c] - phi_zp[c];
+            // x and y links on both sides
+            {
+                const int xs = z & 1;
+                T qn[5], xa[5], xb[5], phi[5];
+                // (x-1, x)
+#pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    qn[c] = S.q(sc, c, lx - 1, ly);
+                    if (THREE) { xa[c] = S.x(xs, 0, c, lx - 1, ly); xb[c] = S.x(xs, 0, c, lx, ly); }
+                }
+                link_flux<0, THREE>(S.m(sc, lx - 1, ly), m0, qn, q0, xa, xb, L1, L23, phi);
+#pragma unroll
+                for (int c = 0; c < 5; ++c) grad[c] += phi[c];
+                // (x, x+1)
+#pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    qn[c] = S.q(sc, c, lx + 1, ly);
+                    if (THREE) { xa[c] = S.x(xs, 0, c, lx, ly); xb[c] = S.x(xs, 0, c, lx + 1, ly); }
+                }
+                link_flux<0, THREE>(m0, S.m(sc, lx + 1, ly), q0, qn, xa, xb, L1, L23, phi);
+#pragma unroll
+                for (int c = 0; c < 5; ++c) grad[c] -= phi[c];
+                // (y-1, y)
+#pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    qn[c] = S.q(sc, c, lx, ly - 1);
+                    if (THREE) { xa[c] = S.x(xs, 1, c, lx, ly - 1); xb[c] = S.x(xs, 1, c, lx, ly); }
+                }
+                link_flux<1, THREE>(S.m(sc, lx, ly - 1), m0, qn, q0, xa, xb, L1, L23, phi);
+#pragma unroll
+                for (int c = 0; c < 5; ++c) grad[c] += phi[c];
+                // (y, y+1)
+#pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    qn[c] = S.q(sc, c, lx, ly + 1);
+                    if (THREE) { xa[c] = S.x(xs, 1, c, lx, ly); xb[c] = S.x(xs, 1, c, lx, ly + 1); }
+                }
+                link_flux<1, THREE>(m0, S.m(sc, lx, ly + 1), q0, qn, xa, xb, L1, L23, phi);
+#pragma unroll
+                for (int c = 0; c < 5; ++c) grad[c] -= phi[c];
+            }
+            T Fn[5];
+            if (!THREE) {
+                T j[5];
+                jt_sym(grad, j);
+#pragma unroll
+                for (int c = 0; c < 5; ++c) Fn[c] = -L1 * j[c];
+            } else {
+#pragma unroll
+                for (int c = 0; c < 5; ++c) Fn[c] = -grad[c];
+            }
+            T fb[5];
+            bulk_force(q0, args.A, args.B, args.C, fb);
+#pragma unroll
+            for (int c = 0; c < 5; ++c) Fn[c] += fb[c];
+            if (m0 & M_ANCH) {
+                const AnchorRec<T> *r = find_record<T>(args.g, L, gx, gy, z);
+                if (r) {
+                    T fa[5];
+                    anchor_force(q0, *r, args.S0, fa);
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) Fn[c] += fa[c];
+                }
+            }
+            const long long i = ((long long)z * L.ny + gy) * L.nx + gx;
+            if (args.force_only) {
+#pragma unroll
+                for (int c = 0; c < 5; ++c) Fout[c * N + i] = Fn[c];
+            } else {
+                double sf = 0.0;
+#pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    T vn = vm_cur[c] + hdt * (fo_cur[c] + Fn[c]);
+                    qout[c * N + i] = q0[c];
+                    vout[c * N + i] = vn;
+                    Fout[c * N + i] = Fn[c];
+                    double fd = (double)Fn[c], vd = (double)vn;
+                    accP += fd * vd;
+                    sf += fd * fd;
+                    accV += vd * vd;
+                }
+                accF += sf;
+                accR = fmax(accR, sf);
+            }
+        }
+
+        // advance the carried z quantities
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            phi_zm[c] = phi_zp[c];
+            vm_cur[c] = vm_nxt[c];
+            fo_cur[c] = fo_nxt[c];
+            if (THREE) xz_cur[c] = xz_nxt[c];
+        }
+        // no barrier here: the next stage writes slot (z+2)&3, which no thread
+        // reads in this step, and the barrier after it orders everything else
+    }
+
+    if (args.force_only) return;
+
+    // block reduction, then the last block reduces the partials in order
+    block_reduce4<NT>(accP, accF, accV, accR, red);
+    const int nblocks = gridDim.x * gridDim.y * gridDim.z;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (threadIdx.x == 0) {
+        double *p = args.partials + 4 * (long long)bid;
+        p[0] = accP; p[1] = accF; p[2] = accV; p[3] = accR;
+        __threadfence();
+        unsigned int t = atomicAdd(&args.st->counter, 1u);
+        am_last = (t == (unsigned)(nblocks - 1));
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double P = 0.0, F2 = 0.0, V2 = 0.0, R2 = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += NT) {
+        const double *p = args.partials + 4 * (long long)b;
+        P += __ldcg(p); F2 += __ldcg(p + 1); V2 += __ldcg(p + 2); R2 = fmax(R2, __ldcg(p + 3));
+    }
+    block_reduce4<NT>(P, F2, V2, R2, red);
+    if (threadIdx.x == 0) {
+        fire_update(args.st, P, F2, V2, R2);
+        args.st->counter = 0;
+    }
+}
+
+// ---- host launchers ---------------------------------------------------------
+
+template <typename T, bool THREE, int TX, int TY>
+static size_t step_smem_bytes() {
+    constexpr int PL = (TX + 2) * (TY + 2);
+    size_t b = sizeof(T) * (4 * 5 * PL + (THREE ? 2 * 2 * 5 * PL : 0)) + 4 * PL;
+    return (b + 15) & ~size_t(15);
+}
+
+template <typename T, bool THREE, int TX, int TY>
+static cudaError_t launch_impl(const StepLaunch &sl, cudaStream_t stream) {
+    StepArgs<T> a;
+    for (int b = 0; b < 2; ++b) {
+        a.q[b] = static_cast<T *>(sl.q[b]);
+        a.v[b] = static_cast<T *>(sl.v[b]);
+        a.F[b] = static_cast<T *>(sl.F[b]);
+    }
+    a.Fonly = static_cast<T *>(sl.Fonly);
+    a.qonly = static_cast<const T *>(sl.qonly);
+    a.g = sl.g;
+    a.L = sl.L;
+    a.A = T(sl.A); a.B = T(sl.B); a.C = T(sl.C);
+    a.L1 = T(sl.L1); a.L2 = T(sl.L2); a.L3 = T(sl.L3); a.S0 = T(sl.S0);
+    a.st = sl.st;
+    a.partials = sl.partials;
+    a.zchunk = sl.zchunk;
+    a.force_only = sl.force_only;
+    size_t smem = step_smem_bytes<T, THREE, TX, TY>();
+    auto kern = fire_step_kernel<T, THREE, TX, TY>;
+    dim3 grid = step_grid(sl.L, sl.zchunk, TX, TY);
+    kern<<<grid, TX * TY, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+dim3 step_grid(const LatticeDev &L, int zchunk, int tx, int ty) {
+    return dim3((L.nx + tx - 1) / tx, (L.ny + ty - 1) / ty, (L.nz + zchunk - 1) / zchunk);
+}
+
+void step_tile(int fp32, int three, int *tx, int *ty) {
+    (void)fp32; (void)three;
+    *tx = 32;
+    *ty = 8;
+}
+
+template <typename T, bool THREE, int TX, int TY>
+static cudaError_t prepare_impl() {
+    return cudaFuncSetAttribute(fire_step_kernel<T, THREE, TX, TY>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)step_smem_bytes<T, THREE, TX, TY>());
+}
+
+cudaError_t prepare_fire_step(int fp32, int three) {
+    if (fp32) return three ? prepare_impl<float, true, 32, 8>() : prepare_impl<float, false, 32, 8>();
+    return three ? prepare_impl<double, true, 32, 8>() : prepare_impl<double, false, 32, 8>();
+}
+
+cudaError_t launch_fire_step(const StepLaunch &sl, cudaStream_t stream) {
+    if (sl.fp32) {
+        if (sl.three) return launch_impl<float, true, 32, 8>(sl, stream);
+        return launch_impl<float, false, 32, 8>(sl, stream);
+    }
+    if (sl.three) return launch_impl<double, true, 32, 8>(sl, stream);
+    return launch_impl<double, false, 32, 8>(sl, stream);
+}
+
+}  // namespace lq

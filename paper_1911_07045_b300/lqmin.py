@@ -1,0 +1,319 @@
+"""Thin ctypes binding of the C interface in ``include/lqmin.h``.
+
+Only argument marshalling lives here: every step of the force + FIRE path
+runs in the CUDA kernels of ``liblqmin.so``.  There is no CPU fallback: if
+the library has not been built, or no CUDA device is present, the first call
+raises.
+
+The ``lq_*`` functions mirror the C calls one to one (same names, numpy
+arrays for host buffers, ints for device pointers and streams).  ``Solver``
+is a small convenience wrapper that owns one ``lq_solver`` handle.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblqmin.so")
+
+LQ_OK, LQ_EINVAL, LQ_ENOMEM, LQ_ECUDA, LQ_ENOTCONVERGED, LQ_ETIMEOUT, LQ_EDIVERGED, LQ_EBUSY = range(8)
+STATUS_NAMES = ["LQ_OK", "LQ_EINVAL", "LQ_ENOMEM", "LQ_ECUDA", "LQ_ENOTCONVERGED", "LQ_ETIMEOUT",
+                "LQ_EDIVERGED", "LQ_EBUSY"]
+LQ_FP64, LQ_FP32_BULK_FP64_RED = 0, 1
+ND_HOMEOTROPIC, ND_ORIENTED, FG_PLANAR = 0, 1, 2
+FIRE_RUNNING, FIRE_CONVERGED, FIRE_MAXITER, FIRE_DIVERGED = 0, 1, 2, 3
+
+# every symbol include/lqmin.h declares
+EXPORTS = [
+    "lq_create", "lq_destroy", "lq_last_error", "lq_create_error", "lq_add_wall", "lq_add_sphere",
+    "lq_add_object_sites", "lq_add_anchored_sites", "lq_geometry_info", "lq_get_mask", "lq_set_q",
+    "lq_set_q_device", "lq_init_random_uniaxial", "lq_get_q", "lq_get_velocity", "lq_get_force",
+    "lq_force", "lq_energy", "lq_order_field", "lq_fire_reset", "lq_step", "lq_minimize",
+    "lq_fire_result", "lq_get_state", "lq_set_state", "lq_set_zchunk", "lq_device_bytes",
+]
+
+
+class LqError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class Lattice(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("spacing", C.c_double),
+                ("periodic", C.c_int * 3)]
+
+
+class Material(C.Structure):
+    _fields_ = [("A", C.c_double), ("B", C.c_double), ("C", C.c_double), ("L1", C.c_double),
+                ("L2", C.c_double), ("L3", C.c_double), ("L4", C.c_double), ("L6", C.c_double),
+                ("n_constants", C.c_int), ("S0", C.c_double)]
+
+
+class Anchoring(C.Structure):
+    _fields_ = [("kind", C.c_int), ("W", C.c_double), ("dir", C.c_double * 3)]
+
+
+class FireParams(C.Structure):
+    _fields_ = [("dt0", C.c_double), ("dt_max", C.c_double), ("alpha0", C.c_double),
+                ("f_alpha", C.c_double), ("f_inc", C.c_double), ("f_dec", C.c_double),
+                ("n_min", C.c_int), ("max_iter", C.c_int64), ("force_tol", C.c_double),
+                ("wall_timeout_s", C.c_double)]
+
+
+class Result(C.Structure):
+    _fields_ = [("iterations", C.c_int64), ("max_force", C.c_double), ("rms_force", C.c_double),
+                ("norm_force", C.c_double), ("norm_velocity", C.c_double), ("power", C.c_double),
+                ("dt", C.c_double), ("alpha", C.c_double), ("npos", C.c_int64),
+                ("energy", C.c_double), ("fire_status", C.c_int), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load ``liblqmin.so``; raises if it is missing (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -m paper_1911_07045_b300.build` (nvcc, sm_103a)")
+    lib = C.CDLL(path)
+    p, i64, d = C.c_void_p, C.c_int64, C.c_double
+    S = p  # lq_solver*
+    sig = {
+        "lq_create": (C.c_int, [C.POINTER(Lattice), C.POINTER(Material), C.c_int, p, C.POINTER(p)]),
+        "lq_destroy": (None, [S]),
+        "lq_last_error": (C.c_char_p, [S]),
+        "lq_create_error": (C.c_char_p, []),
+        "lq_add_wall": (C.c_int, [S, C.c_int, C.c_int, C.POINTER(Anchoring)]),
+        "lq_add_sphere": (C.c_int, [S, C.POINTER(C.c_double), d, C.POINTER(Anchoring)]),
+        "lq_add_object_sites": (C.c_int, [S, i64, p, C.POINTER(Anchoring)]),
+        "lq_add_anchored_sites": (C.c_int, [S, i64, p, p]),
+        "lq_geometry_info": (C.c_int, [S, C.POINTER(i64), C.POINTER(i64)]),
+        "lq_get_mask": (C.c_int, [S, p]),
+        "lq_set_q": (C.c_int, [S, p]),
+        "lq_set_q_device": (C.c_int, [S, p, C.c_int]),
+        "lq_init_random_uniaxial": (C.c_int, [S, C.c_uint64, d]),
+        "lq_get_q": (C.c_int, [S, p]),
+        "lq_get_velocity": (C.c_int, [S, p]),
+        "lq_get_force": (C.c_int, [S, p]),
+        "lq_force": (C.c_int, [S, p]),
+        "lq_energy": (C.c_int, [S, C.POINTER(d), p]),
+        "lq_order_field": (C.c_int, [S, p]),
+        "lq_fire_reset": (C.c_int, [S, C.POINTER(FireParams)]),
+        "lq_step": (C.c_int, [S, C.POINTER(FireParams), i64, C.POINTER(Result)]),
+        "lq_minimize": (C.c_int, [S, C.POINTER(FireParams), C.POINTER(Result)]),
+        "lq_fire_result": (C.c_int, [S, C.POINTER(Result)]),
+        "lq_get_state": (C.c_int, [S, p, C.POINTER(C.c_size_t)]),
+        "lq_set_state": (C.c_int, [S, p, C.c_size_t]),
+        "lq_set_zchunk": (C.c_int, [S, C.c_int]),
+        "lq_device_bytes": (C.c_size_t, [S]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a: np.ndarray):
+    return C.c_void_p(a.ctypes.data)
+
+
+def fire_params(dt0=1e-3, dt_max=1e-2, alpha0=0.99, f_alpha=0.99, f_inc=1.1, f_dec=0.5, n_min=5,
+                max_iter=10 ** 9, force_tol=1e-9, wall_timeout_s=0.0) -> FireParams:
+    return FireParams(dt0, dt_max, alpha0, f_alpha, f_inc, f_dec, n_min, max_iter, force_tol,
+                      wall_timeout_s)
+
+
+def anchoring(kind, W, dir=(0.0, 0.0, 1.0)) -> Anchoring:
+    return Anchoring(int(kind), float(W), (C.c_double * 3)(*[float(v) for v in dir]))
+
+
+class Solver:
+    """One lattice on the current CUDA device (see ``lq_create``)."""
+
+    def __init__(self, shape, A, B, C_, L1, L2=0.0, L3=0.0, periodic=(1, 1, 1), precision=LQ_FP64,
+                 stream=None, n_constants=None, S0=0.0):
+        lib = load()
+        nx, ny, nz = (int(v) for v in shape)
+        self.shape = (nx, ny, nz)
+        self.N = nx * ny * nz
+        lat = Lattice(nx, ny, nz, 1.0, (C.c_int * 3)(*[int(bool(p)) for p in periodic]))
+        if n_constants is None:
+            n_constants = 1 if (L2 == 0.0 and L3 == 0.0) else 3
+        mat = Material(A, B, C_, L1, L2, L3, 0.0, 0.0, n_constants, S0)
+        h = C.c_void_p()
+        st = lib.lq_create(C.byref(lat), C.byref(mat), int(precision),
+                           C.c_void_p(stream) if stream else None, C.byref(h))
+        if st != LQ_OK:
+            raise LqError(st, lib.lq_create_error().decode())
+        self.h = h
+        self.lib = lib
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lq_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, st, ok=(LQ_OK,)):
+        if st not in ok:
+            raise LqError(st, self.lib.lq_last_error(self.h).decode())
+        return st
+
+    # ---- geometry --------------------------------------------------------
+    def add_wall(self, axis, plane, kind=ND_HOMEOTROPIC, W=0.0, dir=(0, 0, 1)):
+        a = anchoring(kind, W, dir)
+        self._ck(self.lib.lq_add_wall(self.h, int(axis), int(plane), C.byref(a)))
+
+    def add_sphere(self, c, R, kind=ND_HOMEOTROPIC, W=0.0, dir=(0, 0, 1)):
+        a = anchoring(kind, W, dir)
+        cc = (C.c_double * 3)(*[float(v) for v in c])
+        self._ck(self.lib.lq_add_sphere(self.h, cc, float(R), C.byref(a)))
+
+    def add_object_sites(self, xyz, kind=ND_HOMEOTROPIC, W=0.0, dir=(0, 0, 1)):
+        xyz = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
+        a = anchoring(kind, W, dir)
+        self._ck(self.lib.lq_add_object_sites(self.h, xyz.shape[0], _ptr(xyz), C.byref(a)))
+
+    def add_anchored_sites(self, xyz, kinds, W, dirs):
+        xyz = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
+        n = xyz.shape[0]
+        arr = (Anchoring * max(1, n))()
+        kinds = np.broadcast_to(np.asarray(kinds), (n,))
+        W = np.broadcast_to(np.asarray(W, dtype=float), (n,))
+        dirs = np.broadcast_to(np.asarray(dirs, dtype=float), (n, 3))
+        for t in range(n):
+            arr[t] = anchoring(kinds[t], W[t], dirs[t])
+        self._ck(self.lib.lq_add_anchored_sites(self.h, n, _ptr(xyz), C.cast(arr, C.c_void_p)))
+
+    def add_objects(self, objects):
+        """Objects in the dict format of ``synth`` (same as the oracle's)."""
+        for o in objects:
+            t = o["type"]
+            if t == "wall":
+                k, W, d = o.get("anchor", (ND_HOMEOTROPIC, 0.0, (0, 0, 1)))
+                self.add_wall(o["axis"], o["plane"], k, W, d)
+            elif t == "sphere":
+                k, W, d = o.get("anchor", (ND_HOMEOTROPIC, 0.0, (0, 0, 1)))
+                self.add_sphere(o["c"], o["R"], k, W, d)
+            elif t == "sites":
+                k, W, d = o.get("anchor", (ND_HOMEOTROPIC, 0.0, (0, 0, 1)))
+                self.add_object_sites(o["xyz"], k, W, d)
+            elif t == "anchored":
+                self.add_anchored_sites(o["xyz"], o["kinds"], o["W"], o["dirs"])
+            else:
+                raise ValueError(t)
+
+    def geometry_info(self):
+        a, b = C.c_int64(), C.c_int64()
+        self._ck(self.lib.lq_geometry_info(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def mask(self):
+        out = np.empty(self.N, dtype=np.uint8)
+        self._ck(self.lib.lq_get_mask(self.h, _ptr(out)))
+        return out
+
+    # ---- state -----------------------------------------------------------
+    def set_q(self, q):
+        q = np.ascontiguousarray(q, dtype=np.float64).reshape(5, self.N)
+        self._ck(self.lib.lq_set_q(self.h, _ptr(q)))
+
+    def set_q_device(self, ptr: int, dtype: int):
+        self._ck(self.lib.lq_set_q_device(self.h, C.c_void_p(ptr), int(dtype)))
+
+    def init_random_uniaxial(self, seed, S=0.0):
+        self._ck(self.lib.lq_init_random_uniaxial(self.h, C.c_uint64(seed), float(S)))
+
+    def _get5(self, fn):
+        out = np.empty((5, self.N))
+        self._ck(fn(self.h, _ptr(out)))
+        return out
+
+    def get_q(self):
+        return self._get5(self.lib.lq_get_q)
+
+    def get_velocity(self):
+        return self._get5(self.lib.lq_get_velocity)
+
+    def get_force(self):
+        return self._get5(self.lib.lq_get_force)
+
+    def force(self):
+        return self._get5(self.lib.lq_force)
+
+    def energy(self):
+        tot = C.c_double()
+        parts = np.zeros(3)
+        self._ck(self.lib.lq_energy(self.h, C.byref(tot), _ptr(parts)))
+        return tot.value, parts
+
+    def order_field(self):
+        out = np.empty(self.N)
+        self._ck(self.lib.lq_order_field(self.h, _ptr(out)))
+        return out
+
+    # ---- FIRE --------------------------------------------------------------
+    def fire_reset(self, params: FireParams):
+        self._ck(self.lib.lq_fire_reset(self.h, C.byref(params)))
+
+    def step(self, params: FireParams, n: int) -> Result:
+        r = Result()
+        self._ck(self.lib.lq_step(self.h, C.byref(params), int(n), C.byref(r)))
+        return r
+
+    def minimize(self, params: FireParams):
+        r = Result()
+        st = self._ck(self.lib.lq_minimize(self.h, C.byref(params), C.byref(r)),
+                      ok=(LQ_OK, LQ_ENOTCONVERGED, LQ_ETIMEOUT, LQ_EDIVERGED))
+        return st, r
+
+    def fire_result(self) -> Result:
+        r = Result()
+        self._ck(self.lib.lq_fire_result(self.h, C.byref(r)))
+        return r
+
+    def get_state(self) -> bytes:
+        n = C.c_size_t()
+        self._ck(self.lib.lq_get_state(self.h, None, C.byref(n)))
+        buf = np.empty(n.value, dtype=np.uint8)
+        self._ck(self.lib.lq_get_state(self.h, _ptr(buf), C.byref(n)))
+        return buf
+
+    def set_state(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._ck(self.lib.lq_set_state(self.h, _ptr(buf), buf.size))
+
+    def set_zchunk(self, z):
+        self._ck(self.lib.lq_set_zchunk(self.h, int(z)))
+
+    def device_bytes(self):
+        return self.lib.lq_device_bytes(self.h)
+
+
+def solver_for(cfg: dict, precision=LQ_FP64, stream=None, A=None, B=None, C_=None,
+               periodic=(1, 1, 1)) -> Solver:
+    """Solver for a ``synth`` workload dict (shape, L1/L2/L3, objects)."""
+    from . import synth
+    s = Solver(cfg["shape"], synth.A_5CB if A is None else A, synth.B_5CB if B is None else B,
+               synth.C_5CB if C_ is None else C_, cfg["L1"], cfg.get("L2", 0.0), cfg.get("L3", 0.0),
+               periodic=cfg.get("periodic", periodic), precision=precision, stream=stream)
+    s.add_objects(cfg.get("objects", []))
+    return s

@@ -109,31 +109,43 @@ def _rng_stream(seed: int):
 
 
 def place_spheres(L: int, count: int, r_lo: float, r_hi: float, seed: int,
-                  wall_axis_z: bool = True, gap: int = 3, r_clamp=None):
+                  walls: bool = True, gap: int = 3, r_clamp=None):
     """Non-overlapping spheres with radius uniform in [r_lo, r_hi] (clamped to
-    r_clamp), centres on lattice sites, at least ``gap`` sites from each other
-    and from the z = 0 and z = L-1 walls."""
+    r_clamp), centres on lattice sites.  Surfaces stay ``gap`` sites apart
+    (minimum-image distance: the box is periodic along x and y, and along z
+    too when ``walls`` is False); with ``walls`` the spheres also stay
+    ``gap`` sites clear of the z = 0 and z = L-1 wall planes.  A draw that
+    cannot be placed after many tries is redrawn with its radius scaled by
+    0.9 (only small boxes ever need this)."""
     u = _rng_stream(seed)
     out = []
+    shrink = 1.0
     tries = 0
     while len(out) < count:
         tries += 1
-        if tries > 100000:
+        if tries % 2000 == 0:
+            shrink *= 0.9
+        if tries > 200000:
             raise RuntimeError("could not place spheres")
-        R = r_lo + (r_hi - r_lo) * next(u)
+        R = (r_lo + (r_hi - r_lo) * next(u)) * shrink
         if r_clamp is not None:
             R = min(R, r_clamp)
-        lo = int(math.ceil(R)) + gap + 1
-        hi = L - 1 - lo
-        if hi < lo:
-            continue
-        c = [lo + int((hi - lo + 1) * next(u)) for _ in range(3)]
-        if not wall_axis_z:
-            c[0] = int(L * next(u)) % L
+        c = [int(L * next(u)) % L for _ in range(3)]
+        if walls:
+            lo = int(math.ceil(R)) + gap + 1
+            hi = L - 1 - lo
+            if hi < lo:
+                continue
+            c[2] = lo + int((hi - lo + 1) * next(u))
         ok = True
         for (c2, R2) in out:
-            d = math.sqrt(sum((a - b) ** 2 for a, b in zip(c, c2)))
-            if d < R + R2 + gap:
+            d2 = 0.0
+            for k in range(3):
+                dk = abs(c[k] - c2[k])
+                if k < 2 or not walls:
+                    dk = min(dk, L - dk)
+                d2 += dk * dk
+            if math.sqrt(d2) < R + R2 + gap:
                 ok = False
                 break
         if ok:
@@ -167,8 +179,8 @@ def config_large(L: int = 512, seed: int = 3):
     objs = [dict(type="wall", axis=2, plane=0, anchor=pla),
             dict(type="wall", axis=2, plane=L - 1, anchor=pla)]
     scale = L / 512.0
-    for c, R in place_spheres(L, 4, 12 * scale, 24 * scale, seed,
-                              r_clamp=max(2.0, 0.3 * L)):
+    for c, R in place_spheres(L, 4, 12 * scale, 24 * scale, seed, walls=True,
+                              r_clamp=max(2.0, 0.2 * L)):
         objs.append(dict(type="sphere", c=c, R=R, anchor=hom))
     return dict(shape=(L, L, L), L1=L1_5CB, L2=L2_3C, L3=L3_3C, objects=objs, seed=seed,
                 tol=1e-8)
@@ -185,9 +197,10 @@ def config_batch(seed: int = 4, count: int = 64):
         L = edges[min(4, int(5 * next(u)))]
         nsph = min(3, int(4 * next(u)))
         hom = (ND_HOMEOTROPIC, W_HOMEOTROPIC, (0.0, 0.0, 1.0))
+        # radii clamped to L/5 so that three colloids fit the smallest boxes
         objs = [dict(type="sphere", c=c, R=R, anchor=hom)
                 for c, R in place_spheres(L, nsph, 6.0, 16.0, seed * 1000 + b + 1,
-                                          r_clamp=max(2.0, 0.3 * L))]
+                                          walls=False, r_clamp=0.2 * L)]
         out.append(dict(shape=(L, L, L), L1=L1_5CB, L2=0.0, L3=0.0, objects=objs,
                         seed=seed * 1000 + 500 + b))
     return out
@@ -233,7 +246,7 @@ def serving_requests(seed: int = 5, count: int = 2000, rate: float = 20.0):
             nsph = 1 + int(2 * next(u)) % 2
             objs = [dict(type="sphere", c=c, R=R, anchor=hom)
                     for c, R in place_spheres(L, nsph, 12.0, 24.0, seed * 100000 + r + 1,
-                                              r_clamp=math.floor(0.3 * L))]
+                                              walls=False, r_clamp=math.floor(0.2 * L))]
             kind = "colloids"
         out.append(dict(t_arrival=t, shape=(L, L, L), L1=L1_5CB, L2=0.0, L3=0.0,
                         objects=objs, seed=seed * 100000 + 50000 + r, kind=kind, tol=1e-6))

@@ -1,0 +1,142 @@
+"""FIRE through the C interface against the oracle's Algorithm 1: one fused
+step, K steps, a full minimisation, checkpoint/resume, and the failure
+statuses (divergence, max_iter, wall-clock limit) -- all raised on the host
+from device flags, with nothing that faults the GPU."""
+import numpy as np
+import pytest
+
+from _helpers import HOM, PLANAR, make_pair, need_gpu, rand_q
+from paper_1911_07045_b300 import lqmin, synth
+
+pytestmark = pytest.mark.gpu
+
+FP = dict(synth.FIRE_DEFAULTS)
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+GEOMS = {
+    "bulk_1c": dict(shape=(24, 20, 18), L=(2.32, 0, 0), objects=[]),
+    "colloid_walls_3c": dict(shape=(30, 28, 26), L=(2.32, 0.5, 0.3),
+                             objects=[dict(type="wall", axis=2, plane=0, anchor=PLANAR()),
+                                      dict(type="wall", axis=2, plane=25, anchor=PLANAR()),
+                                      dict(type="sphere", c=(15.0, 14.0, 13.0), R=5.0,
+                                           anchor=HOM())]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GEOMS))
+def test_one_step_and_k_steps_match_oracle(oracle_mod, name):
+    g = GEOMS[name]
+    s, o = make_pair(oracle_mod, g["shape"], g["L"], g["objects"])
+    q0 = synth.random_uniaxial_q(g["shape"], 11)
+    s.set_q(q0)
+    params = dict(FP, max_iter=10 ** 6, force_tol=1e-12)
+    p = lqmin.fire_params(**params)
+    r = s.step(p, 1)
+    qo, vo, Fo, st = o.fire(q0, params, 1)
+    assert r.iterations == st["iter"] == 1
+    assert rel(s.get_q(), qo) < 1e-12
+    assert rel(s.get_velocity(), vo) < 1e-12
+    assert rel(s.get_force(), Fo) < 1e-12
+    assert (r.dt, r.alpha, r.npos) == (st["dt"], st["alpha"], st["npos"])
+    # 199 more steps: 200 in total
+    r = s.step(p, 199)
+    qo, vo, Fo, st = o.fire(qo, params, 199, state=st, v=vo, F=Fo)
+    assert r.iterations == st["iter"] == 200
+    assert np.abs(s.get_q() - qo).max() < 1e-9
+    assert r.npos == st["npos"]
+    assert abs(r.dt - st["dt"]) <= 1e-12 * st["dt"] and abs(r.alpha - st["alpha"]) <= 1e-12
+
+
+def test_small_periodic_full_minimisation_matches_oracle(oracle_mod):
+    """32^3 periodic one-constant bulk from random directors (seed 1) to
+    max|F| < 1e-9: both reach the uniform texture at S0 (energy N f0)."""
+    cfg = synth.config_small_periodic()
+    s, o = make_pair(oracle_mod, cfg["shape"], (cfg["L1"], 0, 0), [])
+    q0 = synth.random_uniaxial_q(cfg["shape"], cfg["seed"])
+    s.set_q(q0)
+    params = dict(FP, max_iter=100000, force_tol=cfg["tol"])
+    st_code, r = s.minimize(lqmin.fire_params(**params))
+    assert st_code == lqmin.LQ_OK and r.fire_status == lqmin.FIRE_CONVERGED
+    qo, vo, Fo, st = o.fire(q0, params, 100000)
+    assert st["status"] == oracle_mod.CONVERGED
+    Eo = o.energy(qo)[0]
+    assert abs(r.energy - Eo) <= 1e-10 * abs(Eo)
+    assert r.max_force < cfg["tol"]
+    # the same trajectory up to rounding: the iteration counts agree closely
+    assert abs(r.iterations - st["iter"]) <= max(5, st["iter"] // 50)
+
+
+def test_checkpoint_resume_is_bitwise(oracle_mod):
+    g = GEOMS["colloid_walls_3c"]
+    for prec in (0, 1):
+        s, _ = make_pair(oracle_mod, g["shape"], g["L"], g["objects"], precision=prec)
+        s.init_random_uniaxial(5)
+        p = lqmin.fire_params(**dict(FP, max_iter=10 ** 6, force_tol=1e-12))
+        s.step(p, 37)
+        ck = s.get_state()
+        s.step(p, 41)
+        qa, va, ra = s.get_q(), s.get_velocity(), s.fire_result()
+        s.set_state(ck)
+        s.step(p, 41)
+        qb, vb, rb = s.get_q(), s.get_velocity(), s.fire_result()
+        assert np.array_equal(qa, qb) and np.array_equal(va, vb)
+        assert ra.iterations == rb.iterations == 78 and ra.dt == rb.dt
+
+
+def test_statuses_without_faults(oracle_mod):
+    g = GEOMS["bulk_1c"]
+    s, _ = make_pair(oracle_mod, g["shape"], g["L"], g["objects"])
+    s.init_random_uniaxial(2)
+    # max_iter reached
+    code, r = s.minimize(lqmin.fire_params(**dict(FP, max_iter=7, force_tol=1e-14)))
+    assert code == lqmin.LQ_ENOTCONVERGED and r.iterations == 7
+    # a time step far beyond stability: the reductions overflow and FIRE
+    # reports divergence from the device flag
+    s.init_random_uniaxial(2)
+    code, r = s.minimize(lqmin.fire_params(**dict(FP, dt0=50.0, dt_max=50.0, max_iter=5000,
+                                                   force_tol=1e-14)))
+    assert code == lqmin.LQ_EDIVERGED and r.fire_status == lqmin.FIRE_DIVERGED
+    # wall-clock limit
+    s.init_random_uniaxial(2)
+    code, r = s.minimize(lqmin.fire_params(**dict(FP, max_iter=10 ** 9, force_tol=0.0,
+                                                   wall_timeout_s=0.05)))
+    assert code == lqmin.LQ_ETIMEOUT
+    # the solver stays usable afterwards
+    s.init_random_uniaxial(2)
+    r = s.step(lqmin.fire_params(**dict(FP, max_iter=10, force_tol=1e-14)), 3)
+    assert r.iterations == 3 and np.isfinite(r.max_force)
+
+
+def test_fp32_form_reaches_fp64_minimum(oracle_mod):
+    """FP32-bulk / FP64-reduction form: from a smooth start both precisions
+    settle in the same basin; final energy within 1e-6 relative and the
+    per-site order parameter within 1e-4 of the FP64 oracle."""
+    shape = (28, 28, 24)
+    objs = [dict(type="wall", axis=2, plane=0, anchor=HOM()),
+            dict(type="wall", axis=2, plane=23, anchor=HOM()),
+            dict(type="sphere", c=(14.0, 14.0, 12.0), R=5.0, anchor=HOM())]
+    L = (2.32, 0.5, 0.3)
+    s, o = make_pair(oracle_mod, shape, L, objs, precision=1)
+    # smooth start: uniform director along z, slightly tilted
+    n = np.array([0.1, 0.05, 1.0])
+    n /= np.linalg.norm(n)
+    q0 = np.repeat(synth.uniaxial_q(n[:, None], o.S0), o.N, axis=1)
+    params = dict(FP, max_iter=200000, force_tol=1e-6)
+    qo, vo, Fo, st = o.fire(q0, params, 200000)
+    assert st["status"] == oracle_mod.CONVERGED
+    s.set_q(q0)
+    code, r = s.minimize(lqmin.fire_params(**params))
+    assert code == lqmin.LQ_OK
+    Eo = o.energy(qo)[0]
+    assert abs(r.energy - Eo) <= 1e-6 * abs(Eo)
+    sim = o.simulated()
+    assert np.abs(s.order_field()[sim] - o.order_field(qo)[sim]).max() < 1e-4

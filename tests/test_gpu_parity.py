@@ -1,0 +1,127 @@
+"""CUDA path against the CPU oracle: geometry, force, energy, order field and
+the random start, through the C interface (FP64 and the FP32 form)."""
+import numpy as np
+import pytest
+
+from _helpers import CASES, HOM, PLANAR, force_rel_err, make_pair, need_gpu, rand_q
+from paper_1911_07045_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+FORCE_TOL_FP64 = 1e-10     # per-site relative, normalised as in force_rel_err
+ENERGY_TOL_FP64 = 1e-12    # relative total energy
+# FP32 form: stencil and bulk in single precision; unit roundoff 6e-8 times
+# the number of terms that cancel (O(10^2)) bounds the relative force error
+FORCE_TOL_FP32 = 5e-5
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def _mask_from_oracle(o, shape, periodic):
+    nx, ny, nz = shape
+    sim = o.simulated().reshape(nz, ny, nx)
+    m = sim.astype(np.uint8)
+    rec_sites = o.records()[0]
+    anch = np.zeros(nx * ny * nz, bool)
+    anch[rec_sites] = True
+    m |= (anch.reshape(nz, ny, nx).astype(np.uint8) << 1)
+    for k, ax in enumerate((2, 1, 0)):  # x, y, z in [z, y, x] order
+        n = shape[k]
+        for sgn, bit in ((+1, 2 + 2 * k), (-1, 3 + 2 * k)):
+            nb = np.roll(sim, -sgn, axis=ax)
+            if not periodic[k]:
+                idx = [slice(None)] * 3
+                idx[ax] = n - 1 if sgn > 0 else 0
+                nb = nb.copy()
+                nb[tuple(idx)] = False
+            m |= ((nb & sim).astype(np.uint8) << bit)
+    return m.ravel()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_geometry_masks_match_oracle(oracle_mod, name):
+    c = CASES[name]
+    per = c.get("periodic", (1, 1, 1))
+    s, o = make_pair(oracle_mod, c["shape"], c["L"], c["objects"], per)
+    want = _mask_from_oracle(o, c["shape"], per)
+    got = s.mask()
+    assert np.array_equal(got, want)
+    nsim, nrec = s.geometry_info()
+    assert nsim == int(o.simulated().sum()) and nrec == int(o.geom.nrec)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("zchunk", [0, 1, 3])
+def test_force_and_energy_fp64(oracle_mod, name, zchunk):
+    c = CASES[name]
+    per = c.get("periodic", (1, 1, 1))
+    s, o = make_pair(oracle_mod, c["shape"], c["L"], c["objects"], per, zchunk=zchunk)
+    q = rand_q(o.N, 17)
+    s.set_q(q)
+    Fo = o.force(q)
+    Fg = s.force()
+    sim = o.simulated()
+    assert force_rel_err(Fg, Fo, sim) < FORCE_TOL_FP64
+    assert np.all(Fg[:, ~sim] == 0)
+    Eo, po = o.energy(q)
+    Eg, pg = s.energy()
+    assert abs(Eg - Eo) <= ENERGY_TOL_FP64 * abs(Eo)
+    assert np.allclose(pg, po, rtol=1e-12, atol=1e-12 * abs(Eo))
+    # object sites read back as zero
+    qg = s.get_q()
+    assert np.array_equal(qg[:, sim], q[:, sim]) and np.all(qg[:, ~sim] == 0)
+
+
+@pytest.mark.parametrize("name", ["walls_nd_3c", "sphere_walls_fg_3c", "bulk1c_ragged",
+                                  "custom_open_x_3c"])
+def test_force_fp32_form(oracle_mod, name):
+    c = CASES[name]
+    per = c.get("periodic", (1, 1, 1))
+    s, o = make_pair(oracle_mod, c["shape"], c["L"], c["objects"], per, precision=1)
+    q = rand_q(o.N, 5).astype(np.float32).astype(np.float64)  # exactly representable
+    s.set_q(q)
+    Fo = o.force(q)
+    assert force_rel_err(s.force(), Fo, o.simulated()) < FORCE_TOL_FP32
+    Eo, _ = o.energy(q)
+    Eg, _ = s.energy()                # FP64 arithmetic on the FP32 state
+    assert abs(Eg - Eo) <= 1e-12 * abs(Eo)
+
+
+def test_colloid_slab_128_full_force(oracle_mod):
+    """The 128^3 homeotropic slab with a centred colloid (three constants)."""
+    cfg = synth.config_colloid_slab()
+    s, o = make_pair(oracle_mod, cfg["shape"], (cfg["L1"], cfg["L2"], cfg["L3"]), cfg["objects"])
+    q = synth.random_uniaxial_q(cfg["shape"], cfg["seed"])
+    s.set_q(q)
+    assert force_rel_err(s.force(), o.force(q), o.simulated()) < FORCE_TOL_FP64
+    Eo, _ = o.energy(q)
+    Eg, _ = s.energy()
+    assert abs(Eg - Eo) <= ENERGY_TOL_FP64 * abs(Eo)
+
+
+def test_order_field_and_random_start(oracle_mod):
+    shape = (20, 12, 9)
+    objs = [dict(type="sphere", c=(10.0, 6.0, 4.0), R=3.0, anchor=HOM())]
+    s, o = make_pair(oracle_mod, shape, (2.32, 0, 0), objs)
+    s.init_random_uniaxial(77, 0.0)
+    qg = s.get_q()
+    want = synth.random_uniaxial_q(shape, 77)
+    sim = o.simulated()
+    assert np.abs(qg[:, sim] - want[:, sim]).max() < 1e-15
+    assert np.all(qg[:, ~sim] == 0)
+    q = rand_q(o.N, 3)
+    s.set_q(q)
+    assert np.abs(s.order_field() - o.order_field(q)).max() < 1e-12
+
+
+def test_empty_lattice_all_object_sites(oracle_mod):
+    shape = (4, 3, 1)
+    objs = [dict(type="wall", axis=2, plane=0, anchor=HOM())]
+    s, o = make_pair(oracle_mod, shape, (2.32, 0.5, 0.3), objs)
+    assert s.geometry_info() == (0, 0)
+    s.set_q(rand_q(12, 1))
+    assert np.all(s.force() == 0)
+    assert s.energy()[0] == 0.0
