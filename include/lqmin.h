@@ -22,8 +22,12 @@
  *     message.  No call aborts or exits.  Calls on one solver must not
  *     overlap (the solver is not thread-safe); distinct solvers may be used
  *     from different threads.
- *   * All device work is issued on the CUDA stream given to lq_create; the
- *     calls that return host data synchronise that stream.
+ *   * All device work is issued on the CUDA stream given to lq_create (with
+ *     NULL the solver creates and owns a non-blocking stream, since CUDA
+ *     graphs cannot capture the legacy default stream); the calls that
+ *     return host data synchronise that stream.  Device inputs handed to
+ *     lq_set_q_device must be ready before the call (the caller orders its
+ *     own stream against the solver's).
  */
 #ifndef LQMIN_H
 #define LQMIN_H
@@ -127,7 +131,8 @@ typedef struct {
 /* ---- lifetime ------------------------------------------------------------- */
 
 /* Create a solver for one lattice (section III.B).  cuda_stream is a
-   cudaStream_t (NULL = the default stream); precision is an lq_precision.
+   cudaStream_t (NULL = a stream owned by the solver); precision is an
+   lq_precision.
    Allocates the device state: 2 x (q, v, F) buffers, 1-byte site masks and
    the FIRE reduction scratch.  LQ_EINVAL for non-positive sizes, spacing
    != 1, L4/L6 != 0, or n_constants not 1 or 3. */

@@ -176,7 +176,6 @@ __global__ void k_fill(LatticeDev L, const uint8_t *mask, const int *owner,
             }
             AnchorRec<T> rec;
             rec.W = T(sp.W);
-            rec.pad = 0;
             const double *n = (sp.kind == 1) ? sp.dir : nrm;
             double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
             double u[3] = {n[0] / len, n[1] / len, n[2] / len};
@@ -192,6 +191,14 @@ __global__ void k_fill(LatticeDev L, const uint8_t *mask, const int *owner,
                 rec.a[2] = T(1.5 * S0 * u[0] * u[2]);
                 rec.a[3] = T(1.5 * S0 * (u[1] * u[1] - 1.0 / 3.0));
                 rec.a[4] = T(1.5 * S0 * u[1] * u[2]);
+            }
+            // the FP32 form compares against the target on its fixed-point Q grid
+            for (int c = 0; c < 5; ++c) rec.qi[c] = 0;
+            if (rec.kind == 1) {
+                double q0[5] = {1.5 * S0 * (u[0] * u[0] - 1.0 / 3.0), 1.5 * S0 * u[0] * u[1],
+                                1.5 * S0 * u[0] * u[2], 1.5 * S0 * (u[1] * u[1] - 1.0 / 3.0),
+                                1.5 * S0 * u[1] * u[2]};
+                for (int c = 0; c < 5; ++c) rec.qi[c] = (int)llrint(q0[c] * QFIX_SCALE);
             }
             rec_x[out] = x;
             recs[out] = rec;
@@ -273,18 +280,49 @@ __global__ void k_convert(const S *src, D *dst, long long n) {
         dst[i] = D(src[i]);
 }
 
-cudaError_t convert_f64_to_state(const double *src, void *dst, long long n, int fp32,
-                                 cudaStream_t s) {
-    if (fp32) k_convert<double, float><<<blocks_for(n, 256), 256, 0, s>>>(src, (float *)dst, n);
-    else k_convert<double, double><<<blocks_for(n, 256), 256, 0, s>>>(src, (double *)dst, n);
+// Q into the fixed-point grid of the FP32 form; values with |q| >= 4 are
+// counted in *err and clamped
+template <typename S>
+__global__ void k_q_to_fixed(const S *src, int *dst, long long n, unsigned int *err) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double v = (double)src[i];
+        if (!(fabs(v) < QFIX_LIMIT)) {
+            atomicAdd(err, 1u);
+            v = 0.0;
+        }
+        dst[i] = (int)llrint(v * QFIX_SCALE);
+    }
+}
+
+__global__ void k_fixed_to_f64(const int *src, double *dst, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (double)src[i] * QFIX_INV;
+}
+
+cudaError_t q_import(const void *src, int src_f32, void *dst, long long n, int fp32,
+                     unsigned int *err, cudaStream_t s) {
+    int nb = blocks_for(n, 256);
+    if (fp32) {
+        cudaError_t e = cudaMemsetAsync(err, 0, sizeof(unsigned int), s);
+        if (e != cudaSuccess) return e;
+        if (src_f32) k_q_to_fixed<float><<<nb, 256, 0, s>>>((const float *)src, (int *)dst, n, err);
+        else k_q_to_fixed<double><<<nb, 256, 0, s>>>((const double *)src, (int *)dst, n, err);
+    } else {
+        if (src_f32) k_convert<float, double><<<nb, 256, 0, s>>>((const float *)src, (double *)dst, n);
+        else k_convert<double, double><<<nb, 256, 0, s>>>((const double *)src, (double *)dst, n);
+    }
     return cudaGetLastError();
 }
-cudaError_t convert_f32_to_state(const float *src, void *dst, long long n, int fp32,
-                                 cudaStream_t s) {
-    if (fp32) k_convert<float, float><<<blocks_for(n, 256), 256, 0, s>>>(src, (float *)dst, n);
-    else k_convert<float, double><<<blocks_for(n, 256), 256, 0, s>>>(src, (double *)dst, n);
+
+cudaError_t q_export(const void *src, double *dst, long long n, int fp32, cudaStream_t s) {
+    int nb = blocks_for(n, 256);
+    if (fp32) k_fixed_to_f64<<<nb, 256, 0, s>>>((const int *)src, dst, n);
+    else k_convert<double, double><<<nb, 256, 0, s>>>((const double *)src, dst, n);
     return cudaGetLastError();
 }
+
 cudaError_t state_to_f64(const void *src, double *dst, long long n, int fp32, cudaStream_t s) {
     if (fp32) k_convert<float, double><<<blocks_for(n, 256), 256, 0, s>>>((const float *)src, dst, n);
     else k_convert<double, double><<<blocks_for(n, 256), 256, 0, s>>>((const double *)src, dst, n);
@@ -320,6 +358,11 @@ __device__ __forceinline__ unsigned long long splitmix(unsigned long long seed,
     return z ^ (z >> 31);
 }
 
+__device__ __forceinline__ void store_q(double *q, long long i, double v) { q[i] = v; }
+__device__ __forceinline__ void store_q(int *q, long long i, double v) { q[i] = (int)llrint(v * QFIX_SCALE); }
+__device__ __forceinline__ double load_q(const double *q, long long i) { return q[i]; }
+__device__ __forceinline__ double load_q(const int *q, long long i) { return (double)q[i] * QFIX_INV; }
+
 template <typename T>
 __global__ void k_random_uniaxial(LatticeDev L, const uint8_t *mask, unsigned long long seed,
                                   double S, T *q) {
@@ -339,13 +382,13 @@ __global__ void k_random_uniaxial(LatticeDev L, const uint8_t *mask, unsigned lo
             qq[3] = 1.5 * S * (n1 * n1 - 1.0 / 3.0);
             qq[4] = 1.5 * S * n1 * n2;
         }
-        for (int c = 0; c < 5; ++c) q[c * L.N + i] = T(qq[c]);
+        for (int c = 0; c < 5; ++c) store_q(q, c * L.N + i, qq[c]);
     }
 }
 
 cudaError_t init_random_uniaxial(const LatticeDev &L, const uint8_t *mask, unsigned long long seed,
                                  double S, void *q, int fp32, cudaStream_t s) {
-    if (fp32) k_random_uniaxial<float><<<blocks_for(L.N, 256), 256, 0, s>>>(L, mask, seed, S, (float *)q);
+    if (fp32) k_random_uniaxial<int><<<blocks_for(L.N, 256), 256, 0, s>>>(L, mask, seed, S, (int *)q);
     else k_random_uniaxial<double><<<blocks_for(L.N, 256), 256, 0, s>>>(L, mask, seed, S, (double *)q);
     return cudaGetLastError();
 }
@@ -374,13 +417,14 @@ __device__ __forceinline__ double frob2(const double *d) {
     return d[0] * d[0] + d[3] * d[3] + zz * zz + 2.0 * (d[1] * d[1] + d[2] * d[2] + d[4] * d[4]);
 }
 
-template <typename T>
-__device__ __forceinline__ void load5(const T *q, long long N, long long i, double *o) {
-    for (int c = 0; c < 5; ++c) o[c] = (double)q[c * N + i];
+template <typename QS>
+__device__ __forceinline__ void load5(const QS *q, long long N, long long i, double *o) {
+    for (int c = 0; c < 5; ++c) o[c] = load_q(q, c * N + i);
 }
 
-template <typename T>
-__global__ void k_energy(LatticeDev L, Geometry g, const T *q, double A, double B, double C,
+// T: arithmetic type of the form (selects the record layout); QS: Q storage
+template <typename T, typename QS>
+__global__ void k_energy(LatticeDev L, Geometry g, const QS *q, double A, double B, double C,
                          double L1, double L2, double L3, double S0, double *partials) {
     double eb = 0.0, ed = 0.0, ea = 0.0;
     const long long N = L.N;
@@ -453,7 +497,8 @@ __global__ void k_energy(LatticeDev L, Geometry g, const T *q, double A, double 
                 double W = (double)rec->W;
                 if (rec->kind == 1) {
                     double d[5];
-                    for (int c = 0; c < 5; ++c) d[c] = q0[c] - (double)rec->a[c];
+                    for (int c = 0; c < 5; ++c)
+                        d[c] = q0[c] - (sizeof(T) == 4 ? (double)rec->qi[c] * QFIX_INV : (double)rec->a[c]);
                     ea += W * frob2(d);
                 } else {
                     double nu[3] = {(double)rec->a[0], (double)rec->a[1], (double)rec->a[2]};
@@ -509,9 +554,9 @@ cudaError_t energy_parts(const LatticeDev &L, const Geometry &g, const void *q, 
     int nb = blocks_for(L.N, 256);
     if (nb > max_blocks) nb = max_blocks;
     if (fp32)
-        k_energy<float><<<nb, 256, 0, s>>>(L, g, (const float *)q, A, B, C, L1, L2, L3, S0, partials);
+        k_energy<float, int><<<nb, 256, 0, s>>>(L, g, (const int *)q, A, B, C, L1, L2, L3, S0, partials);
     else
-        k_energy<double><<<nb, 256, 0, s>>>(L, g, (const double *)q, A, B, C, L1, L2, L3, S0, partials);
+        k_energy<double, double><<<nb, 256, 0, s>>>(L, g, (const double *)q, A, B, C, L1, L2, L3, S0, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_sum_partials3<<<1, 256, 0, s>>>(partials, nb, out3);
@@ -526,7 +571,8 @@ __global__ void k_order(LatticeDev L, const uint8_t *mask, const T *q, double *S
          i += (long long)gridDim.x * blockDim.x) {
         if (!(mask[i] & M_SIM)) { S[i] = 0.0; continue; }
         double a, b, c, d, e;
-        a = q[i]; b = q[L.N + i]; c = q[2 * L.N + i]; d = q[3 * L.N + i]; e = q[4 * L.N + i];
+        a = load_q(q, i); b = load_q(q, L.N + i); c = load_q(q, 2 * L.N + i);
+        d = load_q(q, 3 * L.N + i); e = load_q(q, 4 * L.N + i);
         double f = -a - d;
         double p2 = (a * a + d * d + f * f + 2.0 * (b * b + c * c + e * e)) / 6.0;
         if (p2 <= 0.0) { S[i] = 0.0; continue; }
@@ -541,7 +587,7 @@ __global__ void k_order(LatticeDev L, const uint8_t *mask, const T *q, double *S
 
 cudaError_t order_field(const LatticeDev &L, const uint8_t *mask, const void *q, int fp32,
                         double *S_out, cudaStream_t s) {
-    if (fp32) k_order<float><<<blocks_for(L.N, 256), 256, 0, s>>>(L, mask, (const float *)q, S_out);
+    if (fp32) k_order<int><<<blocks_for(L.N, 256), 256, 0, s>>>(L, mask, (const int *)q, S_out);
     else k_order<double><<<blocks_for(L.N, 256), 256, 0, s>>>(L, mask, (const double *)q, S_out);
     return cudaGetLastError();
 }

@@ -26,14 +26,24 @@ __host__ __device__ constexpr uint8_t m_bwd(int k) { return (uint8_t)(1u << (3 +
 enum : int { FIRE_RUNNING = 0, FIRE_CONVERGED = 1, FIRE_MAXITER = 2, FIRE_DIVERGED = 3 };
 
 // Anchoring record of one boundary site.  kind 1: Nobili-Durand, a = q0 (5
-// components of Q0); kind 2: Fournier-Galatola, a[0..2] = unit normal nu.
+// components of Q0), qi = the same in the fixed-point Q format of the FP32
+// form; kind 2: Fournier-Galatola, a[0..2] = unit normal nu.
 template <typename T>
 struct AnchorRec {
     T a[5];
     T W;
     int kind;
-    int pad;
+    int qi[5];
 };
+
+// FP32 form: Q is stored as 32-bit fixed point, q = n * 2^-28.  An FP32 Q
+// resolves only ~3e-8 at |Q| ~ 0.4, which is the size of the last FIRE
+// updates before max|F| < 1e-6, and the minimisation stalls there; the fixed
+// grid resolves 3.7e-9 everywhere in |Q| < 4 with the same 4 bytes, and the
+// differences of the stencil are exact integer subtractions.
+constexpr double QFIX_SCALE = 268435456.0;          // 2^28
+constexpr double QFIX_INV = 1.0 / 268435456.0;
+constexpr double QFIX_LIMIT = 4.0;                  // |q| must stay below
 
 struct FireDev {
     // parameters

@@ -56,10 +56,11 @@ cudaError_t geo_fill(const LatticeDev &L, const uint8_t *mask, const int *owner,
 // state helpers
 cudaError_t zero_object_sites(const LatticeDev &L, const uint8_t *mask, void *const *arrays,
                               int narrays, int fp32, cudaStream_t s);
-cudaError_t convert_f64_to_state(const double *src, void *dst, long long n, int fp32,
-                                 cudaStream_t s);
-cudaError_t convert_f32_to_state(const float *src, void *dst, long long n, int fp32,
-                                 cudaStream_t s);
+// Q into / out of the state format (FP32 form: fixed point, range errors
+// counted in *err); v and F out as doubles
+cudaError_t q_import(const void *src, int src_f32, void *dst, long long n, int fp32,
+                     unsigned int *err, cudaStream_t s);
+cudaError_t q_export(const void *src, double *dst, long long n, int fp32, cudaStream_t s);
 cudaError_t state_to_f64(const void *src, double *dst, long long n, int fp32, cudaStream_t s);
 // out = cv v + cF F (the velocity after the pending FIRE mixing), as doubles
 cudaError_t mixed_velocity(const void *v, const void *F, const FireDev *st, double *out,

@@ -34,6 +34,7 @@ struct HostObject {
 struct lq_solver {
     int device = 0;
     cudaStream_t stream = nullptr;
+    bool own_stream = false;        // created by lq_create when given NULL
     int fp32 = 0, three = 0;
     LatticeDev L{};
     lq_material mat{};
@@ -398,10 +399,11 @@ lq_status check_solver(lq_solver *s) {
     return LQ_OK;
 }
 
-lq_status copy_out_state(lq_solver *s, const void *src, double *out) {
+lq_status copy_out_state(lq_solver *s, const void *src, double *out, bool is_q = false) {
     size_t n = 5 * (size_t)s->L.N;
     if (s->fp32) {
-        CK(state_to_f64(src, s->xfer, (long long)n, 1, s->stream));
+        if (is_q) CK(q_export(src, s->xfer, (long long)n, 1, s->stream));
+        else CK(state_to_f64(src, s->xfer, (long long)n, 1, s->stream));
         CK(cudaMemcpyAsync(out, s->xfer, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     } else {
         CK(cudaMemcpyAsync(out, src, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
@@ -444,6 +446,16 @@ lq_status lq_create(const lq_lattice *lat, const lq_material *mat, int precision
     s = new lq_solver();
     cudaGetDevice(&s->device);
     s->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (!s->stream) {
+        // CUDA graphs cannot capture the legacy default stream: own a stream
+        cudaError_t es = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+        if (es != cudaSuccess) {
+            g_create_error = std::string("lq_create: ") + cudaGetErrorString(es);
+            delete s;
+            return LQ_ECUDA;
+        }
+        s->own_stream = true;
+    }
     s->fp32 = precision == LQ_FP32_BULK_FP64_RED;
     s->three = mat->n_constants == 3;
     s->esize = s->fp32 ? sizeof(float) : sizeof(double);
@@ -493,6 +505,7 @@ void lq_destroy(lq_solver *s) {
     cudaFree(s->mask); cudaFree(s->row_start); cudaFree(s->rec_x); cudaFree(s->recs);
     cudaFree(s->xfer); cudaFree(s->st); cudaFree(s->partials); cudaFree(s->out3);
     if (s->st_host) cudaFreeHost(s->st_host);
+    if (s->own_stream) cudaStreamDestroy(s->stream);
     delete s;
 }
 
@@ -565,7 +578,15 @@ lq_status lq_get_mask(lq_solver *s, uint8_t *out) {
     return LQ_OK;
 }
 
-static lq_status after_set_q(lq_solver *s) {
+static lq_status after_set_q(lq_solver *s, bool check_range) {
+    if (check_range) {
+        unsigned int bad = 0;
+        CK(cudaMemcpyAsync(&bad, s->out3, sizeof bad, cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        if (bad)
+            return fail(s, LQ_EINVAL, "%u Q components outside |q| < %g (FP32 form fixed-point range)",
+                        bad, QFIX_LIMIT);
+    }
     void *arrays[1] = {s->q[s->cur]};
     CK(zero_object_sites(s->L, s->mask, arrays, 1, s->fp32, s->stream));
     CK(cudaStreamSynchronize(s->stream));
@@ -580,13 +601,14 @@ lq_status lq_set_q(lq_solver *s, const double *qh) {
     if (r != LQ_OK) return r;
     if (s->fire_ready) { r = sync_state(s); if (r != LQ_OK) return r; }
     size_t n = 5 * (size_t)s->L.N;
+    unsigned int *err = reinterpret_cast<unsigned int *>(s->out3);
     if (s->fp32) {
         CK(cudaMemcpyAsync(s->xfer, qh, n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-        CK(convert_f64_to_state(s->xfer, s->q[s->cur], (long long)n, 1, s->stream));
+        CK(q_import(s->xfer, 0, s->q[s->cur], (long long)n, 1, err, s->stream));
     } else {
         CK(cudaMemcpyAsync(s->q[s->cur], qh, n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     }
-    return after_set_q(s);
+    return after_set_q(s, s->fp32 != 0);
 }
 
 lq_status lq_set_q_device(lq_solver *s, const void *dptr, int dtype) {
@@ -596,9 +618,9 @@ lq_status lq_set_q_device(lq_solver *s, const void *dptr, int dtype) {
     if (r != LQ_OK) return r;
     if (s->fire_ready) { r = sync_state(s); if (r != LQ_OK) return r; }
     long long n = 5 * s->L.N;
-    if (dtype == 0) CK(convert_f64_to_state(static_cast<const double *>(dptr), s->q[s->cur], n, s->fp32, s->stream));
-    else CK(convert_f32_to_state(static_cast<const float *>(dptr), s->q[s->cur], n, s->fp32, s->stream));
-    return after_set_q(s);
+    unsigned int *err = reinterpret_cast<unsigned int *>(s->out3);
+    CK(q_import(dptr, dtype, s->q[s->cur], n, s->fp32, err, s->stream));
+    return after_set_q(s, s->fp32 != 0);
 }
 
 lq_status lq_init_random_uniaxial(lq_solver *s, uint64_t seed, double S) {
@@ -606,8 +628,10 @@ lq_status lq_init_random_uniaxial(lq_solver *s, uint64_t seed, double S) {
     lq_status r = build_geometry(s);
     if (r != LQ_OK) return r;
     if (s->fire_ready) { r = sync_state(s); if (r != LQ_OK) return r; }
-    CK(init_random_uniaxial(s->L, s->mask, seed, S > 0 ? S : s->S0, s->q[s->cur], s->fp32, s->stream));
-    return after_set_q(s);
+    double Sv = S > 0 ? S : s->S0;
+    if (s->fp32 && !(1.5 * Sv < QFIX_LIMIT)) return fail(s, LQ_EINVAL, "S outside the FP32 form's range");
+    CK(init_random_uniaxial(s->L, s->mask, seed, Sv, s->q[s->cur], s->fp32, s->stream));
+    return after_set_q(s, false);
 }
 
 lq_status lq_get_q(lq_solver *s, double *out) {
@@ -616,7 +640,7 @@ lq_status lq_get_q(lq_solver *s, double *out) {
     lq_status r = build_geometry(s);
     if (r != LQ_OK) return r;
     if (s->fire_ready) { r = sync_state(s); if (r != LQ_OK) return r; }
-    return copy_out_state(s, s->q[s->cur], out);
+    return copy_out_state(s, s->q[s->cur], out, true);
 }
 
 lq_status lq_get_force(lq_solver *s, double *out) {

@@ -47,10 +47,14 @@
 namespace lq {
 
 template <typename T>
+struct Prec;
+
+template <typename T>
 struct StepArgs {
-    T *q[2], *v[2], *F[2];
+    typename Prec<T>::Q *q[2];
+    T *v[2], *F[2];
     T *Fonly;                 // force-only output (5 N)
-    const T *qonly;           // force-only input (5 N)
+    const typename Prec<T>::Q *qonly;  // force-only input (5 N)
     Geometry g;
     LatticeDev L;
     T A, B, C, L1, L2, L3, S0;
@@ -68,6 +72,62 @@ __device__ __forceinline__ int wrap_coord(int g, int n, int periodic) {
     }
     return -1;
 }
+
+// Storage and arithmetic of the two forms.  FP64: Q, v, F in double.  FP32
+// form: Q in 32-bit fixed point (exact integer differences), v and F in
+// float, every stencil and bulk operation in float.
+template <>
+struct Prec<double> {
+    using Q = double;
+    __device__ static __forceinline__ double val(double q) { return q; }
+    __device__ static __forceinline__ double diff(double a, double b) { return b - a; }
+    // q + dt v + dt^2/2 F; never out of range in FP64
+    __device__ static __forceinline__ double drift(double q, double dt, double vx, double hdt2,
+                                                   double f, bool &bad) {
+        return q + dt * vx + hdt2 * f;
+    }
+};
+template <>
+struct Prec<float> {
+    using Q = int;
+    __device__ static __forceinline__ float val(int q) { return __int2float_rn(q) * float(QFIX_INV); }
+    __device__ static __forceinline__ float diff(int a, int b) {
+        return __int2float_rn(b - a) * float(QFIX_INV);
+    }
+    __device__ static __forceinline__ int drift(int q, float dt, float vx, float hdt2, float f,
+                                                bool &bad) {
+        float u = (dt * vx + hdt2 * f) * float(QFIX_SCALE);
+        const float lim = float(QFIX_LIMIT * QFIX_SCALE);
+        if (!(fabsf(u) < lim)) { bad = true; return q; }
+        int qn = q + __float2int_rn(u);
+        if (qn >= int(lim) || qn <= -int(lim)) { bad = true; return q; }
+        return qn;
+    }
+};
+
+// per-thread accumulation of the FIRE sums: plain FP64 for the FP64 form;
+// compensated float-float (Knuth's two-sum) for the FP32 form, so that the
+// sums keep ~48 bits without FP64 work per site, and are FP64 from then on
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double get() const { return s; }
+};
+template <>
+struct Acc<float> {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        float t = __fadd_rn(hi, x);
+        float bp = __fsub_rn(t, hi);
+        float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+        hi = t;
+        lo = __fadd_rn(lo, e);
+    }
+    __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
+};
 
 template <typename T>
 __device__ __forceinline__ T inv_count(uint8_t m, int k) {
@@ -104,11 +164,12 @@ __device__ __forceinline__ void jt_cross(const T *ma, const T *mb, T L2, T L3, T
 
 template <typename T, int TX, int TY>
 struct Smem {
+    using QS = typename Prec<T>::Q;
     static constexpr int SX = TX + 2, SY = TY + 2, PL = SX * SY;
-    T *Q;        // [4][5][PL]
+    QS *Q;       // [4][5][PL] drifted Q in the storage format
     T *X;        // [2][2][5][PL]
     uint8_t *M;  // [4][PL]
-    __device__ __forceinline__ T &q(int slot, int c, int lx, int ly) { return Q[(slot * 5 + c) * PL + ly * SX + lx]; }
+    __device__ __forceinline__ QS &q(int slot, int c, int lx, int ly) { return Q[(slot * 5 + c) * PL + ly * SX + lx]; }
     __device__ __forceinline__ uint8_t &m(int slot, int lx, int ly) { return M[slot * PL + ly * SX + lx]; }
     __device__ __forceinline__ T &x(int slot, int ax, int c, int lx, int ly) {
         return X[((slot * 2 + ax) * 5 + c) * PL + ly * SX + lx];
@@ -124,21 +185,23 @@ __device__ __forceinline__ void mean_diff(Smem<T, TX, TY> &S, int lx, int ly, in
     T f = (m & m_fwd(K)) ? T(1) : T(0);
     T b = (m & m_bwd(K)) ? T(1) : T(0);
     T w = (f + b == T(2)) ? T(0.5) : T(1);
+    using P = Prec<T>;
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-        T q0 = S.q(sc, c, lx, ly), qf, qb;
+        typename P::Q q0 = S.q(sc, c, lx, ly), qf, qb;
         if (K == 0) { qf = S.q(sc, c, lx + 1, ly); qb = S.q(sc, c, lx - 1, ly); }
         if (K == 1) { qf = S.q(sc, c, lx, ly + 1); qb = S.q(sc, c, lx, ly - 1); }
         if (K == 2) { qf = S.q(splus, c, lx, ly); qb = S.q(sminus, c, lx, ly); }
-        out[c] = w * (f * (qf - q0) + b * (q0 - qb));
+        out[c] = w * (f * P::diff(q0, qf) + b * P::diff(qb, q0));
     }
 }
 
 // flux through the link (a, a + e_K); ma/mb masks, qa/qb drifted Q,
 // xa/xb the J^T X_K cross terms at both ends (three-constant only)
 template <int K, bool THREE, typename T>
-__device__ __forceinline__ void link_flux(uint8_t ma, uint8_t mb, const T *qa, const T *qb,
-                                          const T *xa, const T *xb, T L1, T L23, T *phi) {
+__device__ __forceinline__ void link_flux(uint8_t ma, uint8_t mb, const typename Prec<T>::Q *qa,
+                                          const typename Prec<T>::Q *qb, const T *xa, const T *xb,
+                                          T L1, T L23, T *phi) {
     if (!(ma & M_SIM) || !(ma & m_fwd(K))) {
 #pragma unroll
         for (int c = 0; c < 5; ++c) phi[c] = T(0);
@@ -147,7 +210,7 @@ __device__ __forceinline__ void link_flux(uint8_t ma, uint8_t mb, const T *qa, c
     T wa = inv_count<T>(ma, K), wb = inv_count<T>(mb, K);
     T d[5];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) d[c] = qb[c] - qa[c];
+    for (int c = 0; c < 5; ++c) d[c] = Prec<T>::diff(qa[c], qb[c]);
     if (!THREE) {
         T w = wa + wb;
 #pragma unroll
@@ -185,11 +248,23 @@ __device__ __forceinline__ void bulk_force(const T *q, T A, T B, T C, T *out) {
 
 // anchoring force of one record (Nobili-Durand or Fournier-Galatola)
 template <typename T>
-__device__ __forceinline__ void anchor_force(const T *q, const AnchorRec<T> &r, T S0, T *out) {
+__device__ __forceinline__ T nd_target_diff(const typename Prec<T>::Q q, const AnchorRec<T> &r, int c);
+template <>
+__device__ __forceinline__ double nd_target_diff<double>(double q, const AnchorRec<double> &r, int c) {
+    return q - r.a[c];
+}
+template <>
+__device__ __forceinline__ float nd_target_diff<float>(int q, const AnchorRec<float> &r, int c) {
+    return Prec<float>::diff(r.qi[c], q);   // exact fixed-point difference
+}
+
+template <typename T>
+__device__ __forceinline__ void anchor_force(const T *q, const typename Prec<T>::Q *qraw,
+                                             const AnchorRec<T> &r, T S0, T *out) {
     if (r.kind == 1) {
         T d[5], j[5];
 #pragma unroll
-        for (int c = 0; c < 5; ++c) d[c] = q[c] - r.a[c];
+        for (int c = 0; c < 5; ++c) d[c] = nd_target_diff<T>(qraw[c], r, c);
         jt_sym(d, j);
 #pragma unroll
         for (int c = 0; c < 5; ++c) out[c] = -T(2) * r.W * j[c];
@@ -265,7 +340,7 @@ __device__ void fire_update(FireDev *st, double P, double F2, double v2, double 
     st->P = P; st->F2 = F2; st->v2 = v2; st->r2 = r2;
     st->cur ^= 1;
     st->kcount += 1;
-    bool bad = !isfinite(P) || !isfinite(F2) || !isfinite(v2);
+    bool bad = !isfinite(P) || !isfinite(F2) || !isfinite(v2) || !isfinite(r2);
     double rmax = sqrt(r2);
     st->cv = 1.0; st->cF = 0.0;
     if (st->kcount == 1) {           // the evaluation of F(q0)
@@ -303,8 +378,10 @@ fire_step_kernel(StepArgs<T> args) {
     using SM = Smem<T, TX, TY>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SM S;
-    S.Q = reinterpret_cast<T *>(smem_raw);
-    S.X = S.Q + 4 * 5 * SM::PL;
+    using P = Prec<T>;
+    using QS = typename P::Q;
+    S.Q = reinterpret_cast<QS *>(smem_raw);
+    S.X = reinterpret_cast<T *>(S.Q + 4 * 5 * SM::PL);
     S.M = reinterpret_cast<uint8_t *>(S.X + (THREE ? 2 * 2 * 5 * SM::PL : 0));
     __shared__ double red[4 * (NT / 32)];
     __shared__ int am_last;
@@ -322,10 +399,12 @@ fire_step_kernel(StepArgs<T> args) {
     // FIRE coefficients for this step
     int cur = 0;
     T cv = T(0), cF = T(0), dt = T(0);
-    const T *qin, *vin, *Fin;
-    T *qout = nullptr, *vout = nullptr, *Fout;
+    const QS *qin;
+    const T *vin = nullptr, *Fin = nullptr;
+    QS *qout = nullptr;
+    T *vout = nullptr, *Fout;
     if (args.force_only) {
-        qin = args.qonly; vin = args.qonly; Fin = args.qonly;
+        qin = args.qonly;
         Fout = args.Fonly;
     } else {
         if (args.st->status != FIRE_RUNNING) return;
@@ -348,12 +427,13 @@ fire_step_kernel(StepArgs<T> args) {
     }
 
     // drift and stage one site of plane z; returns v_mix and F_old
+    bool bad = false;   // a drift left the fixed-point range (FP32 form)
     auto stage = [&](int slot, int sx, int sy, int z, T *vm, T *fo) {
         int X = wrap_coord(x0 + sx - 1, L.nx, L.px);
         int Y = wrap_coord(y0 + sy - 1, L.ny, L.py);
         int Z = wrap_coord(z, L.nz, L.pz);
         uint8_t m = 0;
-        T qh[5] = {T(0), T(0), T(0), T(0), T(0)};
+        QS qh[5] = {QS(0), QS(0), QS(0), QS(0), QS(0)};
         if (X >= 0 && Y >= 0 && Z >= 0) {
             long long i = ((long long)Z * L.ny + Y) * L.nx + X;
             m = args.g.mask[i];
@@ -364,9 +444,10 @@ fire_step_kernel(StepArgs<T> args) {
                 } else {
 #pragma unroll
                     for (int c = 0; c < 5; ++c) {
-                        T q = qin[c * N + i], v = vin[c * N + i], f = Fin[c * N + i];
+                        QS q = qin[c * N + i];
+                        T v = vin[c * N + i], f = Fin[c * N + i];
                         T vx = cv * v + cF * f;
-                        qh[c] = q + dt * vx + hdt2 * f;
+                        qh[c] = P::drift(q, dt, vx, hdt2, f, bad);
                         vm[c] = vx;
                         fo[c] = f;
                     }
@@ -410,14 +491,15 @@ fire_step_kernel(StepArgs<T> args) {
             mean_diff<1>(S, lx, ly, sc, 0, 0, my);
             jt_cross<2>(mx, my, args.L2, args.L3, xz_cur);
         }
-        T qa[5], qb[5];
+        QS qa[5], qb[5];
 #pragma unroll
         for (int c = 0; c < 5; ++c) { qa[c] = S.q((z0 - 1) & 3, c, lx, ly); qb[c] = S.q(z0 & 3, c, lx, ly); }
         link_flux<2, THREE>(S.m((z0 - 1) & 3, lx, ly), S.m(z0 & 3, lx, ly), qa, qb, xz_m, xz_cur,
                             L1, L23, phi_zm);
     }
 
-    double accP = 0.0, accF = 0.0, accV = 0.0, accR = 0.0;
+    Acc<T> accP, accF, accV;
+    T accR = T(0);
 
     for (int z = z0; z < z1; ++z) {
         const int sc = z & 3, sp = (z + 1) & 3, sm = (z - 1) & 3;
@@ -476,14 +558,14 @@ fire_step_kernel(StepArgs<T> args) {
         }
 
         const uint8_t m0 = S.m(sc, lx, ly);
-        T q0[5];
+        QS q0[5];
 #pragma unroll
         for (int c = 0; c < 5; ++c) q0[c] = S.q(sc, c, lx, ly);
 
         // z link (z, z+1) of the own column
         T phi_zp[5];
         {
-            T qb[5];
+            QS qb[5];
 #pragma unroll
             for (int c = 0; c < 5; ++c) qb[c] = S.q(sp, c, lx, ly);
             link_flux<2, THREE>(m0, S.m(sp, lx, ly), q0, qb, xz_cur, THREE ? xz_nxt : xz_cur, L1,
@@ -497,7 +579,8 @@ fire_step_kernel(StepArgs<T> args) {
             // x and y links on both sides
             {
                 const int xs = z & 1;
-                T qn[5], xa[5], xb[5], phi[5];
+                QS qn[5];
+                T xa[5], xb[5], phi[5];
                 // (x-1, x)
 #pragma unroll
                 for (int c = 0; c < 5; ++c) {
@@ -545,15 +628,17 @@ fire_step_kernel(StepArgs<T> args) {
 #pragma unroll
                 for (int c = 0; c < 5; ++c) Fn[c] = -grad[c];
             }
-            T fb[5];
-            bulk_force(q0, args.A, args.B, args.C, fb);
+            T qv[5], fb[5];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) qv[c] = P::val(q0[c]);
+            bulk_force(qv, args.A, args.B, args.C, fb);
 #pragma unroll
             for (int c = 0; c < 5; ++c) Fn[c] += fb[c];
             if (m0 & M_ANCH) {
                 const AnchorRec<T> *r = find_record<T>(args.g, L, gx, gy, z);
                 if (r) {
                     T fa[5];
-                    anchor_force(q0, *r, args.S0, fa);
+                    anchor_force(qv, q0, *r, args.S0, fa);
 #pragma unroll
                     for (int c = 0; c < 5; ++c) Fn[c] += fa[c];
                 }
@@ -563,20 +648,21 @@ fire_step_kernel(StepArgs<T> args) {
 #pragma unroll
                 for (int c = 0; c < 5; ++c) Fout[c * N + i] = Fn[c];
             } else {
-                double sf = 0.0;
+                T pv = T(0), ff = T(0), vv = T(0);
 #pragma unroll
                 for (int c = 0; c < 5; ++c) {
                     T vn = vm_cur[c] + hdt * (fo_cur[c] + Fn[c]);
                     qout[c * N + i] = q0[c];
                     vout[c * N + i] = vn;
                     Fout[c * N + i] = Fn[c];
-                    double fd = (double)Fn[c], vd = (double)vn;
-                    accP += fd * vd;
-                    sf += fd * fd;
-                    accV += vd * vd;
+                    pv += Fn[c] * vn;
+                    ff += Fn[c] * Fn[c];
+                    vv += vn * vn;
                 }
-                accF += sf;
-                accR = fmax(accR, sf);
+                accP.add(pv);
+                accF.add(ff);
+                accV.add(vv);
+                accR = fmax(accR, ff);
             }
         }
 
@@ -594,13 +680,16 @@ fire_step_kernel(StepArgs<T> args) {
 
     if (args.force_only) return;
 
-    // block reduction, then the last block reduces the partials in order
-    block_reduce4<NT>(accP, accF, accV, accR, red);
+    // block reduction, then the last block reduces the partials in order; a
+    // fixed-point range violation poisons the max with +inf (-> diverged)
+    double sP = accP.get(), sF = accF.get(), sV = accV.get();
+    double sR = bad ? (double)INFINITY : (double)accR;
+    block_reduce4<NT>(sP, sF, sV, sR, red);
     const int nblocks = gridDim.x * gridDim.y * gridDim.z;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     if (threadIdx.x == 0) {
         double *p = args.partials + 4 * (long long)bid;
-        p[0] = accP; p[1] = accF; p[2] = accV; p[3] = accR;
+        p[0] = sP; p[1] = sF; p[2] = sV; p[3] = sR;
         __threadfence();
         unsigned int t = atomicAdd(&args.st->counter, 1u);
         am_last = (t == (unsigned)(nblocks - 1));
@@ -608,14 +697,14 @@ fire_step_kernel(StepArgs<T> args) {
     __syncthreads();
     if (!am_last) return;
     __threadfence();
-    double P = 0.0, F2 = 0.0, V2 = 0.0, R2 = 0.0;
+    double P2 = 0.0, F2 = 0.0, V2 = 0.0, R2 = 0.0;
     for (int b = threadIdx.x; b < nblocks; b += NT) {
         const double *p = args.partials + 4 * (long long)b;
-        P += __ldcg(p); F2 += __ldcg(p + 1); V2 += __ldcg(p + 2); R2 = fmax(R2, __ldcg(p + 3));
+        P2 += __ldcg(p); F2 += __ldcg(p + 1); V2 += __ldcg(p + 2); R2 = fmax(R2, __ldcg(p + 3));
     }
-    block_reduce4<NT>(P, F2, V2, R2, red);
+    block_reduce4<NT>(P2, F2, V2, R2, red);
     if (threadIdx.x == 0) {
-        fire_update(args.st, P, F2, V2, R2);
+        fire_update(args.st, P2, F2, V2, R2);
         args.st->counter = 0;
     }
 }
@@ -625,7 +714,8 @@ fire_step_kernel(StepArgs<T> args) {
 template <typename T, bool THREE, int TX, int TY>
 static size_t step_smem_bytes() {
     constexpr int PL = (TX + 2) * (TY + 2);
-    size_t b = sizeof(T) * (4 * 5 * PL + (THREE ? 2 * 2 * 5 * PL : 0)) + 4 * PL;
+    size_t b = sizeof(typename Prec<T>::Q) * 4 * 5 * PL + sizeof(T) * (THREE ? 2 * 2 * 5 * PL : 0) +
+               4 * PL;
     return (b + 15) & ~size_t(15);
 }
 
@@ -633,12 +723,12 @@ template <typename T, bool THREE, int TX, int TY>
 static cudaError_t launch_impl(const StepLaunch &sl, cudaStream_t stream) {
     StepArgs<T> a;
     for (int b = 0; b < 2; ++b) {
-        a.q[b] = static_cast<T *>(sl.q[b]);
+        a.q[b] = static_cast<typename Prec<T>::Q *>(sl.q[b]);
         a.v[b] = static_cast<T *>(sl.v[b]);
         a.F[b] = static_cast<T *>(sl.F[b]);
     }
     a.Fonly = static_cast<T *>(sl.Fonly);
-    a.qonly = static_cast<const T *>(sl.qonly);
+    a.qonly = static_cast<const typename Prec<T>::Q *>(sl.qonly);
     a.g = sl.g;
     a.L = sl.L;
     a.A = T(sl.A); a.B = T(sl.B); a.C = T(sl.C);

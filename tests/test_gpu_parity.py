@@ -81,13 +81,19 @@ def test_force_fp32_form(oracle_mod, name):
     c = CASES[name]
     per = c.get("periodic", (1, 1, 1))
     s, o = make_pair(oracle_mod, c["shape"], c["L"], c["objects"], per, precision=1)
-    q = rand_q(o.N, 5).astype(np.float32).astype(np.float64)  # exactly representable
+    q = np.round(rand_q(o.N, 5) * 2.0 ** 28) / 2.0 ** 28   # on the form's fixed-point grid
     s.set_q(q)
     Fo = o.force(q)
     assert force_rel_err(s.force(), Fo, o.simulated()) < FORCE_TOL_FP32
-    Eo, _ = o.energy(q)
-    Eg, _ = s.energy()                # FP64 arithmetic on the FP32 state
-    assert abs(Eg - Eo) <= 1e-12 * abs(Eo)
+    Eo, po = o.energy(q)
+    Eg, pg = s.energy()               # FP64 arithmetic on the FP32 state
+    # bulk and distortion see the same (FP32-representable) Q: FP64 agreement
+    assert abs(pg[0] - po[0]) <= 1e-12 * abs(po[0]) + 1e-12
+    assert abs(pg[1] - po[1]) <= 1e-12 * abs(po[1]) + 1e-12
+    # the FP32 form keeps its anchoring targets on its Q grid (Q0) or in
+    # float (nu)
+    assert abs(pg[2] - po[2]) <= 1e-6 * abs(po[2]) + 1e-9
+    assert abs(Eg - Eo) <= 1e-7 * abs(Eo)
 
 
 def test_colloid_slab_128_full_force(oracle_mod):
