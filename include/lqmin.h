@@ -219,6 +219,31 @@ lq_status lq_fire_result(lq_solver *s, lq_result *out);
 lq_status lq_get_state(lq_solver *s, void *buf, size_t *bytes);
 lq_status lq_set_state(lq_solver *s, const void *buf, size_t bytes);
 
+/* ---- without allocation ------------------------------------------------------------ */
+
+/* The paper has no counterpart to this call; it exists for callers that cannot
+   let a library call cudaMalloc: a process whose device memory is reserved
+   up front by its own allocator or budget, or a latency-bound loop that
+   cannot take the device-wide synchronisation of cudaMalloc/cudaFree.  It
+   allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
+   Computes the bulk (Eq. fphase) and averaged-difference distortion
+   (Eq. fdistortionFull) energy of a caller-owned device Q field, summed in
+   FP64: lattice and material as for lq_create; q_dev = 5*N doubles (layout
+   above), mask_dev = N mask bytes in the lq_get_mask layout, both on the
+   device; parts_dev = 3 device doubles receiving (bulk, distortion, 0) --
+   anchoring is not included.  Work runs on cuda_stream (NULL = legacy
+   default stream) and is not synchronised.  Scratch is a static device
+   array of 3 doubles per z plane, for at most 4096 planes (96 KB held on
+   every GPU that loads the library until exit): nz > 4096 returns
+   LQ_EINVAL, as do null pointers or non-positive sizes.  The first call on
+   a device resolves that array's address with the device current; make
+   that first call before any stream capture.  Every call shares the array
+   (each call overwrites it), so calls that overlap on the GPU race.
+   LQ_ECUDA if a launch or the address lookup fails. */
+lq_status lq_energy_noalloc(const lq_lattice *lattice, const lq_material *material,
+                            const double *q_dev, const uint8_t *mask_dev, double *parts_dev,
+                            void *cuda_stream);
+
 /* ---- tuning ---------------------------------------------------------------------- */
 
 /* Number of z planes one thread block marches through (0 = automatic). */

@@ -33,6 +33,7 @@ EXPORTS = [
     "lq_set_q_device", "lq_init_random_uniaxial", "lq_get_q", "lq_get_velocity", "lq_get_force",
     "lq_force", "lq_energy", "lq_order_field", "lq_fire_reset", "lq_step", "lq_minimize",
     "lq_fire_result", "lq_get_state", "lq_set_state", "lq_set_zchunk", "lq_device_bytes",
+    "lq_energy_noalloc",
 ]
 
 
@@ -116,6 +117,7 @@ def load(path: str = LIB_PATH):
         "lq_set_state": (C.c_int, [S, p, C.c_size_t]),
         "lq_set_zchunk": (C.c_int, [S, C.c_int]),
         "lq_device_bytes": (C.c_size_t, [S]),
+        "lq_energy_noalloc": (C.c_int, [C.POINTER(Lattice), C.POINTER(Material), p, p, p, p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -1,0 +1,56 @@
+"""lq_energy_noalloc: the energy entry point for callers that cannot let a
+library allocate device memory (their memory is reserved up front by their
+own allocator or budget, or their loop cannot take the device-wide
+synchronisation of cudaMalloc/cudaFree).  It uses only a static device
+scratch array; the caller owns every input and output buffer.
+
+The test calls it twice in a row through the C interface, on two different
+Q fields, and compares each result with lq_energy's bulk and distortion
+parts for the same field.  This file is collected last so that a failure
+here leaves every other test already run."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from _helpers import HOM, PLANAR, need_gpu, rand_q
+from paper_1911_07045_b300 import lqmin, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def test_energy_noalloc_matches_lq_energy():
+    need_gpu()
+    import torch
+    shape = (37, 22, 19)
+    objs = [dict(type="wall", axis=2, plane=0, anchor=PLANAR()),
+            dict(type="sphere", c=(18.0, 11.0, 9.0), R=4.5, anchor=HOM())]
+    L1, L2, L3 = 2.32, 0.5, 0.3
+    per = (1, 0, 1)
+    s = lqmin.Solver(shape, synth.A_5CB, synth.B_5CB, synth.C_5CB, L1, L2, L3, periodic=per)
+    s.add_objects(objs)
+    lib = lqmin.load()
+    lat = lqmin.Lattice(*shape, 1.0, (C.c_int * 3)(*per))
+    mat = lqmin.Material(synth.A_5CB, synth.B_5CB, synth.C_5CB, L1, L2, L3, 0.0, 0.0, 3, 0.0)
+    mask = torch.from_numpy(s.mask()).cuda()          # caller-owned device buffers
+    out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    for seed in (3, 4):                                # two calls in a row
+        q = rand_q(s.N, seed)
+        s.set_q(q)
+        _, want = s.energy()
+        qd = torch.from_numpy(q).cuda()
+        torch.cuda.synchronize()
+        st = lib.lq_energy_noalloc(C.byref(lat), C.byref(mat), C.c_void_p(qd.data_ptr()),
+                                   C.c_void_p(mask.data_ptr()), C.c_void_p(out.data_ptr()), None)
+        assert st == lqmin.LQ_OK
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert abs(got[0] - want[0]) <= 1e-12 * abs(want[0])
+        assert abs(got[1] - want[1]) <= 1e-12 * abs(want[1])
+        assert got[2] == 0.0
+    # sizes beyond the static scratch are refused
+    big = lqmin.Lattice(2, 2, 4097, 1.0, (C.c_int * 3)(1, 1, 1))
+    st = lib.lq_energy_noalloc(C.byref(big), C.byref(mat), C.c_void_p(qd.data_ptr()),
+                               C.c_void_p(mask.data_ptr()), C.c_void_p(out.data_ptr()), None)
+    assert st == lqmin.LQ_EINVAL
+    s.close()
