@@ -376,10 +376,10 @@ __global__ void __launch_bounds__(TX * TY)
 fire_step_kernel(StepArgs<T> args) {
     constexpr int NT = TX * TY;
     using SM = Smem<T, TX, TY>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SM S;
     using P = Prec<T>;
     using QS = typename P::Q;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SM S;
     S.Q = reinterpret_cast<QS *>(smem_raw);
     S.X = reinterpret_cast<T *>(S.Q + 4 * 5 * SM::PL);
     S.M = reinterpret_cast<uint8_t *>(S.X + (THREE ? 2 * 2 * 5 * SM::PL : 0));
@@ -395,20 +395,20 @@ fire_step_kernel(StepArgs<T> args) {
     const bool valid = gx < L.nx && gy < L.ny;
     const int lx = tx + 1, ly = ty + 1;
     const long long N = L.N;
+    const bool fo_mode = args.force_only != 0;
 
     // FIRE coefficients for this step
-    int cur = 0;
     T cv = T(0), cF = T(0), dt = T(0);
     const QS *qin;
     const T *vin = nullptr, *Fin = nullptr;
     QS *qout = nullptr;
     T *vout = nullptr, *Fout;
-    if (args.force_only) {
+    if (fo_mode) {
         qin = args.qonly;
         Fout = args.Fonly;
     } else {
         if (args.st->status != FIRE_RUNNING) return;
-        cur = args.st->cur;
+        const int cur = args.st->cur;
         cv = T(args.st->cv); cF = T(args.st->cF); dt = T(args.st->dt_step);
         qin = args.q[cur]; vin = args.v[cur]; Fin = args.F[cur];
         qout = args.q[cur ^ 1]; vout = args.v[cur ^ 1]; Fout = args.F[cur ^ 1];
@@ -416,8 +416,9 @@ fire_step_kernel(StepArgs<T> args) {
     const T hdt2 = T(0.5) * dt * dt;
     const T hdt = T(0.5) * dt;
 
-    // ring sites of the staged plane: top row, bottom row, left/right columns
+    // ring sites of a staged plane: top row, bottom row, left/right columns
     constexpr int NRING = 2 * SM::SX + 2 * TY;
+    static_assert(NRING <= NT, "one ring site per thread");
     int rx = -1, ry = -1;
     if ((int)threadIdx.x < NRING) {
         int r = threadIdx.x;
@@ -426,70 +427,86 @@ fire_step_kernel(StepArgs<T> args) {
         else { r -= 2 * SM::SX; rx = (r & 1) ? SM::SX - 1 : 0; ry = 1 + (r >> 1); }
     }
 
-    // drift and stage one site of plane z; returns v_mix and F_old
-    bool bad = false;   // a drift left the fixed-point range (FP32 form)
-    auto stage = [&](int slot, int sx, int sy, int z, T *vm, T *fo) {
+    // one site of a plane in flight from global memory (registers)
+    struct Raw {
+        QS q[5];
+        T v[5], f[5];
+        uint8_t m;
+    };
+    // issue the loads of site (sx, sy) of plane z; unconditional for sites
+    // inside the lattice so that the mask load does not serialise them
+    auto fetch = [&](int sx, int sy, int z, Raw &r) {
         int X = wrap_coord(x0 + sx - 1, L.nx, L.px);
         int Y = wrap_coord(y0 + sy - 1, L.ny, L.py);
         int Z = wrap_coord(z, L.nz, L.pz);
-        uint8_t m = 0;
-        QS qh[5] = {QS(0), QS(0), QS(0), QS(0), QS(0)};
+        r.m = 0;
         if (X >= 0 && Y >= 0 && Z >= 0) {
             long long i = ((long long)Z * L.ny + Y) * L.nx + X;
-            m = args.g.mask[i];
-            if (m & M_SIM) {
-                if (args.force_only) {
+            r.m = __ldg(args.g.mask + i);
 #pragma unroll
-                    for (int c = 0; c < 5; ++c) qh[c] = qin[c * N + i];
+            for (int c = 0; c < 5; ++c) r.q[c] = __ldg(qin + c * N + i);
+            if (!fo_mode) {
+#pragma unroll
+                for (int c = 0; c < 5; ++c) { r.v[c] = __ldg(vin + c * N + i); r.f[c] = __ldg(Fin + c * N + i); }
+            }
+        }
+    };
+    bool bad = false;   // a drift left the fixed-point range (FP32 form)
+    // drift (after the pending FIRE mixing) and store into a plane slot
+    auto commit = [&](int slot, int sx, int sy, const Raw &r) {
+        QS qh[5] = {QS(0), QS(0), QS(0), QS(0), QS(0)};
+        if (r.m & M_SIM) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                if (fo_mode) {
+                    qh[c] = r.q[c];
                 } else {
-#pragma unroll
-                    for (int c = 0; c < 5; ++c) {
-                        QS q = qin[c * N + i];
-                        T v = vin[c * N + i], f = Fin[c * N + i];
-                        T vx = cv * v + cF * f;
-                        qh[c] = P::drift(q, dt, vx, hdt2, f, bad);
-                        vm[c] = vx;
-                        fo[c] = f;
-                    }
+                    T vx = cv * r.v[c] + cF * r.f[c];
+                    qh[c] = P::drift(r.q[c], dt, vx, hdt2, r.f[c], bad);
                 }
             }
         }
-        S.m(slot, sx, sy) = m;
+        S.m(slot, sx, sy) = r.m;
 #pragma unroll
         for (int c = 0; c < 5; ++c) S.q(slot, c, sx, sy) = qh[c];
     };
 
-    T vm_cur[5], fo_cur[5], vm_nxt[5], fo_nxt[5];
-    T dummy_v[5], dummy_f[5];
-#pragma unroll
-    for (int c = 0; c < 5; ++c) { vm_cur[c] = fo_cur[c] = vm_nxt[c] = fo_nxt[c] = T(0); }
-
-    // prologue: planes z0 - 1 and z0
-    stage((z0 - 1) & 3, lx, ly, z0 - 1, dummy_v, dummy_f);
-    if (rx >= 0) stage((z0 - 1) & 3, rx, ry, z0 - 1, dummy_v, dummy_f);
-    stage(z0 & 3, lx, ly, z0, vm_cur, fo_cur);
-    if (rx >= 0) stage(z0 & 3, rx, ry, z0, dummy_v, dummy_f);
+    // prologue: planes z0-1, z0, z0+1 staged, plane z0+2 in flight
+    Raw pf_own, pf_ring;
+    {
+        Raw r;
+        for (int p = -1; p <= 1; ++p) {
+            fetch(lx, ly, z0 + p, r);
+            commit((z0 + p) & 3, lx, ly, r);
+            if (rx >= 0) {
+                fetch(rx, ry, z0 + p, r);
+                commit((z0 + p) & 3, rx, ry, r);
+            }
+        }
+        fetch(lx, ly, z0 + 2, pf_own);
+        if (rx >= 0) fetch(rx, ry, z0 + 2, pf_ring);
+    }
     __syncthreads();
 
     const T L1 = args.L1, L23 = args.L2 + args.L3;
-    T phi_zm[5];      // flux of the link (z-1, z) at the own column
-    T xz_cur[5];      // J^T X_z at (own, z)
+    T phi_zm[5];            // flux of the link (z-1, z) of the own column
+    T xz_cur[5];            // J^T X_z at (own, z)
+    T mx_cur[5], my_cur[5]; // in-plane means at (own, z), carried from z-1
 #pragma unroll
-    for (int c = 0; c < 5; ++c) { phi_zm[c] = T(0); xz_cur[c] = T(0); }
+    for (int c = 0; c < 5; ++c) { phi_zm[c] = T(0); xz_cur[c] = T(0); mx_cur[c] = T(0); my_cur[c] = T(0); }
     {
-        // link (z0-1, z0): needs X_z at both planes (three-constant)
         T xz_m[5];
 #pragma unroll
         for (int c = 0; c < 5; ++c) xz_m[c] = T(0);
         if (THREE) {
             T mx[5], my[5];
-            int sm = (z0 - 1) & 3, sc = z0 & 3;
+            const int sm = (z0 - 1) & 3, sc = z0 & 3;
             mean_diff<0>(S, lx, ly, sm, 0, 0, mx);
             mean_diff<1>(S, lx, ly, sm, 0, 0, my);
             jt_cross<2>(mx, my, args.L2, args.L3, xz_m);
-            mean_diff<0>(S, lx, ly, sc, 0, 0, mx);
-            mean_diff<1>(S, lx, ly, sc, 0, 0, my);
-            jt_cross<2>(mx, my, args.L2, args.L3, xz_cur);
+            mean_diff<0>(S, lx, ly, sc, 0, 0, mx_cur);
+            mean_diff<1>(S, lx, ly, sc, 0, 0, my_cur);
+            jt_cross<2>(mx_cur, my_cur, args.L2, args.L3, xz_cur);
         }
         QS qa[5], qb[5];
 #pragma unroll
@@ -503,24 +520,28 @@ fire_step_kernel(StepArgs<T> args) {
 
     for (int z = z0; z < z1; ++z) {
         const int sc = z & 3, sp = (z + 1) & 3, sm = (z - 1) & 3;
-        // stage plane z + 1
-        stage(sp, lx, ly, z + 1, vm_nxt, fo_nxt);
-        if (rx >= 0) stage(sp, rx, ry, z + 1, dummy_v, dummy_f);
-        __syncthreads();
+        const uint8_t m0 = S.m(sc, lx, ly);
+        const bool own = valid && (m0 & M_SIM);
+        const long long i = ((long long)z * L.ny + gy) * L.nx + gx;
+        // the own site's v and F of plane z, for the kick (read through the cache;
+        // issued here so that the cross terms below hide the latency)
+        T vold[5], fold[5];
+        if (own && !fo_mode) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) { vold[c] = __ldg(vin + c * N + i); fold[c] = __ldg(Fin + c * N + i); }
+        }
 
-        T xz_nxt[5];
+        T xz_nxt[5], mx_nxt[5], my_nxt[5];
         if (THREE) {
             const int xs = z & 1;
             // cross terms of the tile at plane z
-            if (S.m(sc, lx, ly) & M_SIM) {
-                T mx[5], my[5], mz[5], o[5];
-                mean_diff<0>(S, lx, ly, sc, sp, sm, mx);
-                mean_diff<1>(S, lx, ly, sc, sp, sm, my);
+            if (m0 & M_SIM) {
+                T mz[5], o[5];
                 mean_diff<2>(S, lx, ly, sc, sp, sm, mz);
-                jt_cross<0>(my, mz, args.L2, args.L3, o);
+                jt_cross<0>(my_cur, mz, args.L2, args.L3, o);
 #pragma unroll
                 for (int c = 0; c < 5; ++c) S.x(xs, 0, c, lx, ly) = o[c];
-                jt_cross<1>(mx, mz, args.L2, args.L3, o);
+                jt_cross<1>(mx_cur, mz, args.L2, args.L3, o);
 #pragma unroll
                 for (int c = 0; c < 5; ++c) S.x(xs, 1, c, lx, ly) = o[c];
             }
@@ -547,17 +568,13 @@ fire_step_kernel(StepArgs<T> args) {
                     for (int c = 0; c < 5; ++c) S.x(xs, 1, c, sx, sy) = o[c];
                 }
             }
-            // z cross term of the own column at plane z + 1
-            {
-                T mx[5], my[5];
-                mean_diff<0>(S, lx, ly, sp, 0, 0, mx);
-                mean_diff<1>(S, lx, ly, sp, 0, 0, my);
-                jt_cross<2>(mx, my, args.L2, args.L3, xz_nxt);
-            }
+            // in-plane means and z cross term of the own column at plane z + 1
+            mean_diff<0>(S, lx, ly, sp, 0, 0, mx_nxt);
+            mean_diff<1>(S, lx, ly, sp, 0, 0, my_nxt);
+            jt_cross<2>(mx_nxt, my_nxt, args.L2, args.L3, xz_nxt);
             __syncthreads();
         }
 
-        const uint8_t m0 = S.m(sc, lx, ly);
         QS q0[5];
 #pragma unroll
         for (int c = 0; c < 5; ++c) q0[c] = S.q(sc, c, lx, ly);
@@ -572,11 +589,10 @@ fire_step_kernel(StepArgs<T> args) {
                                 L23, phi_zp);
         }
 
-        if (valid && (m0 & M_SIM)) {
+        if (own) {
             T grad[5];
 #pragma unroll
             for (int c = 0; c < 5; ++c) grad[c] = phi_zm[c] - phi_zp[c];
-            // x and y links on both sides
             {
                 const int xs = z & 1;
                 QS qn[5];
@@ -594,7 +610,7 @@ fire_step_kernel(StepArgs<T> args) {
 #pragma unroll
                 for (int c = 0; c < 5; ++c) {
                     qn[c] = S.q(sc, c, lx + 1, ly);
-                    if (THREE) { xa[c] = S.x(xs, 0, c, lx, ly); xb[c] = S.x(xs, 0, c, lx + 1, ly); }
+                    if (THREE) { xa[c] = xb[c]; xb[c] = S.x(xs, 0, c, lx + 1, ly); }
                 }
                 link_flux<0, THREE>(m0, S.m(sc, lx + 1, ly), q0, qn, xa, xb, L1, L23, phi);
 #pragma unroll
@@ -612,7 +628,7 @@ fire_step_kernel(StepArgs<T> args) {
 #pragma unroll
                 for (int c = 0; c < 5; ++c) {
                     qn[c] = S.q(sc, c, lx, ly + 1);
-                    if (THREE) { xa[c] = S.x(xs, 1, c, lx, ly); xb[c] = S.x(xs, 1, c, lx, ly + 1); }
+                    if (THREE) { xa[c] = xb[c]; xb[c] = S.x(xs, 1, c, lx, ly + 1); }
                 }
                 link_flux<1, THREE>(m0, S.m(sc, lx, ly + 1), q0, qn, xa, xb, L1, L23, phi);
 #pragma unroll
@@ -643,18 +659,18 @@ fire_step_kernel(StepArgs<T> args) {
                     for (int c = 0; c < 5; ++c) Fn[c] += fa[c];
                 }
             }
-            const long long i = ((long long)z * L.ny + gy) * L.nx + gx;
-            if (args.force_only) {
+            if (fo_mode) {
 #pragma unroll
                 for (int c = 0; c < 5; ++c) Fout[c * N + i] = Fn[c];
             } else {
                 T pv = T(0), ff = T(0), vv = T(0);
 #pragma unroll
                 for (int c = 0; c < 5; ++c) {
-                    T vn = vm_cur[c] + hdt * (fo_cur[c] + Fn[c]);
-                    qout[c * N + i] = q0[c];
-                    vout[c * N + i] = vn;
-                    Fout[c * N + i] = Fn[c];
+                    T vx = cv * vold[c] + cF * fold[c];
+                    T vn = vx + hdt * (fold[c] + Fn[c]);
+                    __stcs(qout + c * N + i, q0[c]);
+                    __stcs(vout + c * N + i, vn);
+                    __stcs(Fout + c * N + i, Fn[c]);
                     pv += Fn[c] * vn;
                     ff += Fn[c] * Fn[c];
                     vv += vn * vn;
@@ -670,12 +686,20 @@ fire_step_kernel(StepArgs<T> args) {
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
             phi_zm[c] = phi_zp[c];
-            vm_cur[c] = vm_nxt[c];
-            fo_cur[c] = fo_nxt[c];
-            if (THREE) xz_cur[c] = xz_nxt[c];
+            if (THREE) { xz_cur[c] = xz_nxt[c]; mx_cur[c] = mx_nxt[c]; my_cur[c] = my_nxt[c]; }
         }
-        // no barrier here: the next stage writes slot (z+2)&3, which no thread
-        // reads in this step, and the barrier after it orders everything else
+        // pipeline: plane z+2 from registers into its slot, plane z+3 in flight.
+        // Slot (z+2)&3 = (z-2)&3 is read by no thread in this step, and the
+        // barrier below orders it before the next step's reads.
+        if (z + 2 <= z1) {
+            commit((z + 2) & 3, lx, ly, pf_own);
+            if (rx >= 0) commit((z + 2) & 3, rx, ry, pf_ring);
+        }
+        if (z + 3 <= z1) {
+            fetch(lx, ly, z + 3, pf_own);
+            if (rx >= 0) fetch(rx, ry, z + 3, pf_ring);
+        }
+        __syncthreads();
     }
 
     if (args.force_only) return;
