@@ -39,11 +39,14 @@ struct AnchorRec {
 // FP32 form: Q is stored as 32-bit fixed point, q = n * 2^-28.  An FP32 Q
 // resolves only ~3e-8 at |Q| ~ 0.4, which is the size of the last FIRE
 // updates before max|F| < 1e-6, and the minimisation stalls there; the fixed
-// grid resolves 3.7e-9 everywhere in |Q| < 4 with the same 4 bytes, and the
-// differences of the stencil are exact integer subtractions.
+// grid resolves 3.7e-9 everywhere with the same 4 bytes, and the stencil's
+// differences are exact integer arithmetic.  Components are kept in
+// |q| < 2 (Q entries of a physical state are bounded by |S| <= 1), so that
+// second differences a + b - 2c and mixed differences a - b - c + d stay
+// inside int32.
 constexpr double QFIX_SCALE = 268435456.0;          // 2^28
 constexpr double QFIX_INV = 1.0 / 268435456.0;
-constexpr double QFIX_LIMIT = 4.0;                  // |q| must stay below
+constexpr double QFIX_LIMIT = 2.0;                  // |q| must stay below
 
 struct FireDev {
     // parameters

@@ -166,9 +166,9 @@ template <typename T, int TX, int TY>
 struct Smem {
     using QS = typename Prec<T>::Q;
     static constexpr int SX = TX + 2, SY = TY + 2, PL = SX * SY;
-    QS *Q;       // [4][5][PL] drifted Q in the storage format
+    QS *Q;       // [5][5][PL] drifted Q in the storage format
     T *X;        // [2][2][5][PL]
-    uint8_t *M;  // [4][PL]
+    uint8_t *M;  // [5][PL]
     __device__ __forceinline__ QS &q(int slot, int c, int lx, int ly) { return Q[(slot * 5 + c) * PL + ly * SX + lx]; }
     __device__ __forceinline__ uint8_t &m(int slot, int lx, int ly) { return M[slot * PL + ly * SX + lx]; }
     __device__ __forceinline__ T &x(int slot, int ax, int c, int lx, int ly) {
@@ -371,17 +371,90 @@ __device__ void fire_update(FireDev *st, double P, double F2, double v2, double 
     st->cv = a; st->cF = b; st->dt_step = st->dt;
 }
 
+// second differences and mixed differences in the storage format: exact
+// integer arithmetic for the fixed-point form, one conversion per value
+template <typename T>
+struct Stencil;
+template <>
+struct Stencil<double> {
+    static constexpr double scale = 1.0;
+    __device__ static __forceinline__ double sec(double a, double b, double c) { return (a - c) + (b - c); }
+    __device__ static __forceinline__ double mix(double a, double b, double c, double d) {
+        return (a - b) - (c - d);
+    }
+};
+template <>
+struct Stencil<float> {
+    static constexpr double scale = QFIX_INV;
+    __device__ static __forceinline__ float sec(int a, int b, int c) { return __int2float_rn(a + b - 2 * c); }
+    __device__ static __forceinline__ float mix(int a, int b, int c, int d) {
+        return __int2float_rn((a - b) - (c - d));
+    }
+};
+
+// Distortion force at a regular site: every site within the 19-point
+// stencil and at distance 2 along the axes is simulated, so every allowed
+// difference count is 2 and every weight 1/2.  Then the per-site cross terms
+// X_k(j) cancel between the links (j - e_k, j) and (j, j + e_k), and
+//   F = sum_k [ L1 J^T(D2_k) + (L2+L3) Jcol_k(D2_k) + 1/4 J^T X_k(E_ka, E_kb) ]
+// with D2_k = q(j+e_k) + q(j-e_k) - 2 q(j) and the mixed differences
+// E_ab = q(j+e_a+e_b) - q(j+e_a-e_b) - q(j-e_a+e_b) + q(j-e_a-e_b); an exact
+// rearrangement of the general link-flux form for such sites.
+template <bool THREE, typename T, int TX, int TY>
+__device__ __forceinline__ void regular_force(Smem<T, TX, TY> &S, int lx, int ly, int sc, int sp,
+                                              int sm, T L1s, T L23s, T L2q, T L3q, T *Fd) {
+    using ST = Stencil<T>;
+    T d2x[5], d2y[5], d2z[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        auto q0 = S.q(sc, c, lx, ly);
+        d2x[c] = ST::sec(S.q(sc, c, lx + 1, ly), S.q(sc, c, lx - 1, ly), q0);
+        d2y[c] = ST::sec(S.q(sc, c, lx, ly + 1), S.q(sc, c, lx, ly - 1), q0);
+        d2z[c] = ST::sec(S.q(sp, c, lx, ly), S.q(sm, c, lx, ly), q0);
+    }
+    T lap[5], j1[5], cx[5], cy[5], cz[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) lap[c] = d2x[c] + d2y[c] + d2z[c];
+    jt_sym(lap, j1);
+    if (!THREE) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) Fd[c] = L1s * j1[c];
+        return;
+    }
+    jt_col<0>(d2x, cx);
+    jt_col<1>(d2y, cy);
+    jt_col<2>(d2z, cz);
+    T exy[5], exz[5], eyz[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        exy[c] = ST::mix(S.q(sc, c, lx + 1, ly + 1), S.q(sc, c, lx + 1, ly - 1),
+                         S.q(sc, c, lx - 1, ly + 1), S.q(sc, c, lx - 1, ly - 1));
+        exz[c] = ST::mix(S.q(sp, c, lx + 1, ly), S.q(sm, c, lx + 1, ly),
+                         S.q(sp, c, lx - 1, ly), S.q(sm, c, lx - 1, ly));
+        eyz[c] = ST::mix(S.q(sp, c, lx, ly + 1), S.q(sm, c, lx, ly + 1),
+                         S.q(sp, c, lx, ly - 1), S.q(sm, c, lx, ly - 1));
+    }
+    T kx[5], ky[5], kz[5];
+    jt_cross<0>(exy, exz, L2q, L3q, kx);
+    jt_cross<1>(exy, eyz, L2q, L3q, ky);
+    jt_cross<2>(exz, eyz, L2q, L3q, kz);
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+        Fd[c] = L1s * j1[c] + L23s * (cx[c] + cy[c] + cz[c]) + (kx[c] + ky[c] + kz[c]);
+}
+
 template <typename T, bool THREE, int TX, int TY>
 __global__ void __launch_bounds__(TX * TY)
 fire_step_kernel(StepArgs<T> args) {
     constexpr int NT = TX * TY;
+    constexpr int NSLOT = 5;
     using SM = Smem<T, TX, TY>;
     using P = Prec<T>;
     using QS = typename P::Q;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SM S;
     S.Q = reinterpret_cast<QS *>(smem_raw);
-    S.X = reinterpret_cast<T *>(S.Q + 4 * 5 * SM::PL);
+    S.X = reinterpret_cast<T *>(S.Q + NSLOT * 5 * SM::PL);
     S.M = reinterpret_cast<uint8_t *>(S.X + (THREE ? 2 * 2 * 5 * SM::PL : 0));
     __shared__ double red[4 * (NT / 32)];
     __shared__ int am_last;
@@ -395,6 +468,7 @@ fire_step_kernel(StepArgs<T> args) {
     const bool valid = gx < L.nx && gy < L.ny;
     const int lx = tx + 1, ly = ty + 1;
     const long long N = L.N;
+    const long long NXY = (long long)L.nx * L.ny;
     const bool fo_mode = args.force_only != 0;
 
     // FIRE coefficients for this step
@@ -426,6 +500,14 @@ fire_step_kernel(StepArgs<T> args) {
         else if (r < 2 * SM::SX) { rx = r - SM::SX; ry = SM::SY - 1; }
         else { r -= 2 * SM::SX; rx = (r & 1) ? SM::SX - 1 : 0; ry = 1 + (r >> 1); }
     }
+    // in-plane offsets of the own and ring sites (-1: outside the lattice)
+    auto xy_of = [&](int sx, int sy) -> long long {
+        int X = wrap_coord(x0 + sx - 1, L.nx, L.px);
+        int Y = wrap_coord(y0 + sy - 1, L.ny, L.py);
+        return (X >= 0 && Y >= 0) ? (long long)Y * L.nx + X : -1;
+    };
+    const long long xy_own = xy_of(lx, ly);
+    const long long xy_ring = rx >= 0 ? xy_of(rx, ry) : -1;
 
     // one site of a plane in flight from global memory (registers)
     struct Raw {
@@ -433,15 +515,13 @@ fire_step_kernel(StepArgs<T> args) {
         T v[5], f[5];
         uint8_t m;
     };
-    // issue the loads of site (sx, sy) of plane z; unconditional for sites
-    // inside the lattice so that the mask load does not serialise them
-    auto fetch = [&](int sx, int sy, int z, Raw &r) {
-        int X = wrap_coord(x0 + sx - 1, L.nx, L.px);
-        int Y = wrap_coord(y0 + sy - 1, L.ny, L.py);
+    // loads are unconditional for sites inside the lattice, so that the mask
+    // load does not serialise them
+    auto fetch = [&](long long xy, int z, Raw &r) {
         int Z = wrap_coord(z, L.nz, L.pz);
         r.m = 0;
-        if (X >= 0 && Y >= 0 && Z >= 0) {
-            long long i = ((long long)Z * L.ny + Y) * L.nx + X;
+        if (xy >= 0 && Z >= 0) {
+            long long i = Z * NXY + xy;
             r.m = __ldg(args.g.mask + i);
 #pragma unroll
             for (int c = 0; c < 5; ++c) r.q[c] = __ldg(qin + c * N + i);
@@ -471,130 +551,153 @@ fire_step_kernel(StepArgs<T> args) {
         for (int c = 0; c < 5; ++c) S.q(slot, c, sx, sy) = qh[c];
     };
 
-    // prologue: planes z0-1, z0, z0+1 staged, plane z0+2 in flight
+    // plane z lives in slot z mod 5: at step z the slots of z-1, z, z+1 are
+    // read, z+2 is written before the barrier; slot z+3 = z-2 is the one the
+    // next step writes, which no thread of this step reads
+    auto slot_of = [&](int z) { return ((z % NSLOT) + NSLOT) % NSLOT; };
+
     Raw pf_own, pf_ring;
     {
         Raw r;
         for (int p = -1; p <= 1; ++p) {
-            fetch(lx, ly, z0 + p, r);
-            commit((z0 + p) & 3, lx, ly, r);
+            fetch(xy_own, z0 + p, r);
+            commit(slot_of(z0 + p), lx, ly, r);
             if (rx >= 0) {
-                fetch(rx, ry, z0 + p, r);
-                commit((z0 + p) & 3, rx, ry, r);
+                fetch(xy_ring, z0 + p, r);
+                commit(slot_of(z0 + p), rx, ry, r);
             }
         }
-        fetch(lx, ly, z0 + 2, pf_own);
-        if (rx >= 0) fetch(rx, ry, z0 + 2, pf_ring);
+        fetch(xy_own, z0 + 2, pf_own);
+        if (rx >= 0) fetch(xy_ring, z0 + 2, pf_ring);
     }
-    __syncthreads();
+    __syncthreads();   // the first regularity check reads neighbours' masks
 
     const T L1 = args.L1, L23 = args.L2 + args.L3;
-    T phi_zm[5];            // flux of the link (z-1, z) of the own column
-    T xz_cur[5];            // J^T X_z at (own, z)
-    T mx_cur[5], my_cur[5]; // in-plane means at (own, z), carried from z-1
+    const T sc_ = T(Stencil<T>::scale);
+    const T L1s = L1 * sc_, L23s = L23 * sc_;
+    const T L2q = T(0.25) * args.L2 * sc_, L3q = T(0.25) * args.L3 * sc_;
+    // quantities carried from plane to plane by the general (irregular) path
+    bool carry = false;
+    T phi_zm[5], xz_cur[5], mx_cur[5], my_cur[5];
 #pragma unroll
     for (int c = 0; c < 5; ++c) { phi_zm[c] = T(0); xz_cur[c] = T(0); mx_cur[c] = T(0); my_cur[c] = T(0); }
-    {
-        T xz_m[5];
-#pragma unroll
-        for (int c = 0; c < 5; ++c) xz_m[c] = T(0);
-        if (THREE) {
-            T mx[5], my[5];
-            const int sm = (z0 - 1) & 3, sc = z0 & 3;
-            mean_diff<0>(S, lx, ly, sm, 0, 0, mx);
-            mean_diff<1>(S, lx, ly, sm, 0, 0, my);
-            jt_cross<2>(mx, my, args.L2, args.L3, xz_m);
-            mean_diff<0>(S, lx, ly, sc, 0, 0, mx_cur);
-            mean_diff<1>(S, lx, ly, sc, 0, 0, my_cur);
-            jt_cross<2>(mx_cur, my_cur, args.L2, args.L3, xz_cur);
-        }
-        QS qa[5], qb[5];
-#pragma unroll
-        for (int c = 0; c < 5; ++c) { qa[c] = S.q((z0 - 1) & 3, c, lx, ly); qb[c] = S.q(z0 & 3, c, lx, ly); }
-        link_flux<2, THREE>(S.m((z0 - 1) & 3, lx, ly), S.m(z0 & 3, lx, ly), qa, qb, xz_m, xz_cur,
-                            L1, L23, phi_zm);
-    }
 
     Acc<T> accP, accF, accV;
     T accR = T(0);
+    const uint8_t FULL = M_SIM | 0xFC;
 
+    int sm = slot_of(z0 - 1), sc = slot_of(z0), sp = slot_of(z0 + 1), s2 = slot_of(z0 + 2);
     for (int z = z0; z < z1; ++z) {
-        const int sc = z & 3, sp = (z + 1) & 3, sm = (z - 1) & 3;
+        // pipeline: plane z+2 into its slot, plane z+3 in flight
+        if (z + 2 <= z1) {
+            commit(s2, lx, ly, pf_own);
+            if (rx >= 0) commit(s2, rx, ry, pf_ring);
+        }
+        if (z + 3 <= z1) {
+            fetch(xy_own, z + 3, pf_own);
+            if (rx >= 0) fetch(xy_ring, z + 3, pf_ring);
+        }
         const uint8_t m0 = S.m(sc, lx, ly);
         const bool own = valid && (m0 & M_SIM);
-        const long long i = ((long long)z * L.ny + gy) * L.nx + gx;
-        // the own site's v and F of plane z, for the kick (read through the cache;
-        // issued here so that the cross terms below hide the latency)
+        // regular own site: it and its six face neighbours have every neighbour
+        bool reg = true;
+        if (own) {
+            uint8_t a = S.m(sc, lx - 1, ly) & S.m(sc, lx + 1, ly) & S.m(sc, lx, ly - 1) &
+                        S.m(sc, lx, ly + 1) & S.m(sp, lx, ly) & S.m(sm, lx, ly) & m0;
+            reg = (m0 & FULL) == FULL && (a & 0xFC) == 0xFC;
+        }
+        const long long i = (long long)z * NXY + (long long)gy * L.nx + gx;
         T vold[5], fold[5];
         if (own && !fo_mode) {
 #pragma unroll
             for (int c = 0; c < 5; ++c) { vold[c] = __ldg(vin + c * N + i); fold[c] = __ldg(Fin + c * N + i); }
         }
+        // the barrier publishes plane z+2 and decides the path of this plane
+        const bool all_reg = __syncthreads_and(reg) != 0;
 
-        T xz_nxt[5], mx_nxt[5], my_nxt[5];
-        if (THREE) {
+        T Fd[5];
+        if (all_reg) {
+            if (own) regular_force<THREE>(S, lx, ly, sc, sp, sm, L1s, L23s, L2q, L3q, Fd);
+            carry = false;
+        } else {
+            if (!carry) {
+                // rebuild the carried z quantities for plane z
+                T xz_m[5];
+#pragma unroll
+                for (int c = 0; c < 5; ++c) xz_m[c] = T(0);
+                if (THREE) {
+                    T mx[5], my[5];
+                    mean_diff<0>(S, lx, ly, sm, 0, 0, mx);
+                    mean_diff<1>(S, lx, ly, sm, 0, 0, my);
+                    jt_cross<2>(mx, my, args.L2, args.L3, xz_m);
+                    mean_diff<0>(S, lx, ly, sc, 0, 0, mx_cur);
+                    mean_diff<1>(S, lx, ly, sc, 0, 0, my_cur);
+                    jt_cross<2>(mx_cur, my_cur, args.L2, args.L3, xz_cur);
+                }
+                QS qa[5], qb[5];
+#pragma unroll
+                for (int c = 0; c < 5; ++c) { qa[c] = S.q(sm, c, lx, ly); qb[c] = S.q(sc, c, lx, ly); }
+                link_flux<2, THREE>(S.m(sm, lx, ly), m0, qa, qb, xz_m, xz_cur, L1, L23, phi_zm);
+            }
+            T xz_nxt[5], mx_nxt[5], my_nxt[5];
             const int xs = z & 1;
-            // cross terms of the tile at plane z
-            if (m0 & M_SIM) {
-                T mz[5], o[5];
-                mean_diff<2>(S, lx, ly, sc, sp, sm, mz);
-                jt_cross<0>(my_cur, mz, args.L2, args.L3, o);
+            if (THREE) {
+                // cross terms of the tile at plane z
+                if (m0 & M_SIM) {
+                    T mz[5], o[5];
+                    mean_diff<2>(S, lx, ly, sc, sp, sm, mz);
+                    jt_cross<0>(my_cur, mz, args.L2, args.L3, o);
 #pragma unroll
-                for (int c = 0; c < 5; ++c) S.x(xs, 0, c, lx, ly) = o[c];
-                jt_cross<1>(mx_cur, mz, args.L2, args.L3, o);
+                    for (int c = 0; c < 5; ++c) S.x(xs, 0, c, lx, ly) = o[c];
+                    jt_cross<1>(mx_cur, mz, args.L2, args.L3, o);
 #pragma unroll
-                for (int c = 0; c < 5; ++c) S.x(xs, 1, c, lx, ly) = o[c];
-            }
-            // ring: X_x on the left/right columns, X_y on the top/bottom rows
-            if ((int)threadIdx.x < 2 * TY) {
-                int sx = (threadIdx.x & 1) ? SM::SX - 1 : 0, sy = 1 + (threadIdx.x >> 1);
-                if (S.m(sc, sx, sy) & M_SIM) {
-                    T my[5], mz[5], o[5];
-                    mean_diff<1>(S, sx, sy, sc, sp, sm, my);
-                    mean_diff<2>(S, sx, sy, sc, sp, sm, mz);
-                    jt_cross<0>(my, mz, args.L2, args.L3, o);
-#pragma unroll
-                    for (int c = 0; c < 5; ++c) S.x(xs, 0, c, sx, sy) = o[c];
+                    for (int c = 0; c < 5; ++c) S.x(xs, 1, c, lx, ly) = o[c];
                 }
-            } else if ((int)threadIdx.x < 2 * TY + 2 * TX) {
-                int r = threadIdx.x - 2 * TY;
-                int sx = 1 + (r >> 1), sy = (r & 1) ? SM::SY - 1 : 0;
-                if (S.m(sc, sx, sy) & M_SIM) {
-                    T mx[5], mz[5], o[5];
-                    mean_diff<0>(S, sx, sy, sc, sp, sm, mx);
-                    mean_diff<2>(S, sx, sy, sc, sp, sm, mz);
-                    jt_cross<1>(mx, mz, args.L2, args.L3, o);
+                // ring: X_x on the left/right columns, X_y on the top/bottom rows
+                if ((int)threadIdx.x < 2 * TY) {
+                    int sx = (threadIdx.x & 1) ? SM::SX - 1 : 0, sy = 1 + (threadIdx.x >> 1);
+                    if (S.m(sc, sx, sy) & M_SIM) {
+                        T my[5], mz[5], o[5];
+                        mean_diff<1>(S, sx, sy, sc, sp, sm, my);
+                        mean_diff<2>(S, sx, sy, sc, sp, sm, mz);
+                        jt_cross<0>(my, mz, args.L2, args.L3, o);
 #pragma unroll
-                    for (int c = 0; c < 5; ++c) S.x(xs, 1, c, sx, sy) = o[c];
+                        for (int c = 0; c < 5; ++c) S.x(xs, 0, c, sx, sy) = o[c];
+                    }
+                } else if ((int)threadIdx.x < 2 * TY + 2 * TX) {
+                    int r = threadIdx.x - 2 * TY;
+                    int sx = 1 + (r >> 1), sy = (r & 1) ? SM::SY - 1 : 0;
+                    if (S.m(sc, sx, sy) & M_SIM) {
+                        T mx[5], mz[5], o[5];
+                        mean_diff<0>(S, sx, sy, sc, sp, sm, mx);
+                        mean_diff<2>(S, sx, sy, sc, sp, sm, mz);
+                        jt_cross<1>(mx, mz, args.L2, args.L3, o);
+#pragma unroll
+                        for (int c = 0; c < 5; ++c) S.x(xs, 1, c, sx, sy) = o[c];
+                    }
                 }
+                // in-plane means and z cross term of the own column at plane z + 1
+                mean_diff<0>(S, lx, ly, sp, 0, 0, mx_nxt);
+                mean_diff<1>(S, lx, ly, sp, 0, 0, my_nxt);
+                jt_cross<2>(mx_nxt, my_nxt, args.L2, args.L3, xz_nxt);
+                __syncthreads();
             }
-            // in-plane means and z cross term of the own column at plane z + 1
-            mean_diff<0>(S, lx, ly, sp, 0, 0, mx_nxt);
-            mean_diff<1>(S, lx, ly, sp, 0, 0, my_nxt);
-            jt_cross<2>(mx_nxt, my_nxt, args.L2, args.L3, xz_nxt);
-            __syncthreads();
-        }
-
-        QS q0[5];
+            QS q0[5];
 #pragma unroll
-        for (int c = 0; c < 5; ++c) q0[c] = S.q(sc, c, lx, ly);
-
-        // z link (z, z+1) of the own column
-        T phi_zp[5];
-        {
-            QS qb[5];
-#pragma unroll
-            for (int c = 0; c < 5; ++c) qb[c] = S.q(sp, c, lx, ly);
-            link_flux<2, THREE>(m0, S.m(sp, lx, ly), q0, qb, xz_cur, THREE ? xz_nxt : xz_cur, L1,
-                                L23, phi_zp);
-        }
-
-        if (own) {
-            T grad[5];
-#pragma unroll
-            for (int c = 0; c < 5; ++c) grad[c] = phi_zm[c] - phi_zp[c];
+            for (int c = 0; c < 5; ++c) q0[c] = S.q(sc, c, lx, ly);
+            // z link (z, z+1) of the own column
+            T phi_zp[5];
             {
-                const int xs = z & 1;
+                QS qb[5];
+#pragma unroll
+                for (int c = 0; c < 5; ++c) qb[c] = S.q(sp, c, lx, ly);
+                link_flux<2, THREE>(m0, S.m(sp, lx, ly), q0, qb, xz_cur, THREE ? xz_nxt : xz_cur, L1,
+                                    L23, phi_zp);
+            }
+            if (own) {
+                T grad[5];
+#pragma unroll
+                for (int c = 0; c < 5; ++c) grad[c] = phi_zm[c] - phi_zp[c];
                 QS qn[5];
                 T xa[5], xb[5], phi[5];
                 // (x-1, x)
@@ -633,23 +736,32 @@ fire_step_kernel(StepArgs<T> args) {
                 link_flux<1, THREE>(m0, S.m(sc, lx, ly + 1), q0, qn, xa, xb, L1, L23, phi);
 #pragma unroll
                 for (int c = 0; c < 5; ++c) grad[c] -= phi[c];
+                if (!THREE) {
+                    T j[5];
+                    jt_sym(grad, j);
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) Fd[c] = -L1 * j[c];
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) Fd[c] = -grad[c];
+                }
             }
-            T Fn[5];
-            if (!THREE) {
-                T j[5];
-                jt_sym(grad, j);
 #pragma unroll
-                for (int c = 0; c < 5; ++c) Fn[c] = -L1 * j[c];
-            } else {
-#pragma unroll
-                for (int c = 0; c < 5; ++c) Fn[c] = -grad[c];
+            for (int c = 0; c < 5; ++c) {
+                phi_zm[c] = phi_zp[c];
+                if (THREE) { xz_cur[c] = xz_nxt[c]; mx_cur[c] = mx_nxt[c]; my_cur[c] = my_nxt[c]; }
             }
-            T qv[5], fb[5];
+            carry = true;
+        }
+
+        if (own) {
+            QS q0[5];
+            T qv[5], fb[5], Fn[5];
 #pragma unroll
-            for (int c = 0; c < 5; ++c) qv[c] = P::val(q0[c]);
+            for (int c = 0; c < 5; ++c) { q0[c] = S.q(sc, c, lx, ly); qv[c] = P::val(q0[c]); }
             bulk_force(qv, args.A, args.B, args.C, fb);
 #pragma unroll
-            for (int c = 0; c < 5; ++c) Fn[c] += fb[c];
+            for (int c = 0; c < 5; ++c) Fn[c] = Fd[c] + fb[c];
             if (m0 & M_ANCH) {
                 const AnchorRec<T> *r = find_record<T>(args.g, L, gx, gy, z);
                 if (r) {
@@ -681,25 +793,9 @@ fire_step_kernel(StepArgs<T> args) {
                 accR = fmax(accR, ff);
             }
         }
-
-        // advance the carried z quantities
-#pragma unroll
-        for (int c = 0; c < 5; ++c) {
-            phi_zm[c] = phi_zp[c];
-            if (THREE) { xz_cur[c] = xz_nxt[c]; mx_cur[c] = mx_nxt[c]; my_cur[c] = my_nxt[c]; }
-        }
-        // pipeline: plane z+2 from registers into its slot, plane z+3 in flight.
-        // Slot (z+2)&3 = (z-2)&3 is read by no thread in this step, and the
-        // barrier below orders it before the next step's reads.
-        if (z + 2 <= z1) {
-            commit((z + 2) & 3, lx, ly, pf_own);
-            if (rx >= 0) commit((z + 2) & 3, rx, ry, pf_ring);
-        }
-        if (z + 3 <= z1) {
-            fetch(lx, ly, z + 3, pf_own);
-            if (rx >= 0) fetch(rx, ry, z + 3, pf_ring);
-        }
-        __syncthreads();
+        // rotate the plane slots
+        int t = sm;
+        sm = sc; sc = sp; sp = s2; s2 = (t + 4) % NSLOT;   // plane z+3 = (z-1) + 4
     }
 
     if (args.force_only) return;
@@ -738,8 +834,8 @@ fire_step_kernel(StepArgs<T> args) {
 template <typename T, bool THREE, int TX, int TY>
 static size_t step_smem_bytes() {
     constexpr int PL = (TX + 2) * (TY + 2);
-    size_t b = sizeof(typename Prec<T>::Q) * 4 * 5 * PL + sizeof(T) * (THREE ? 2 * 2 * 5 * PL : 0) +
-               4 * PL;
+    size_t b = sizeof(typename Prec<T>::Q) * 5 * 5 * PL + sizeof(T) * (THREE ? 2 * 2 * 5 * PL : 0) +
+               5 * PL;
     return (b + 15) & ~size_t(15);
 }
 
