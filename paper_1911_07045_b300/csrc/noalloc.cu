@@ -16,7 +16,7 @@
 #include <cstdint>
 #include <mutex>
 
-#include "../../include/lqmin.h"
+#include "lqmin.h"
 #include "lq_common.cuh"
 
 namespace lq {

@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/lqmin.h"
+#include "lqmin.h"
 #include "lq_common.cuh"
 #include "lq_kernels.h"
 
@@ -105,10 +105,12 @@ int auto_zchunk(const lq_solver *s) {
     int tx, ty;
     step_tile(s->fp32, s->three, &tx, &ty);
     long long tiles = (long long)((s->L.nx + tx - 1) / tx) * ((s->L.ny + ty - 1) / ty);
-    // aim at several resident blocks per SM (148 SMs)
-    long long want = 148LL * 4;
+    // enough blocks for several waves on 148 SMs, marches of at most 128
+    // planes (measured best at 512^3), at least 8 planes to amortise the halo
+    long long want = 148LL * 16;
     long long chunks = std::max(1LL, (want + tiles - 1) / tiles);
     int zc = (int)((s->L.nz + chunks - 1) / chunks);
+    zc = std::min(zc, 128);
     return std::max(zc, std::min(8, s->L.nz));
 }
 

@@ -94,6 +94,8 @@ struct Prec<float> {
     __device__ static __forceinline__ float diff(int a, int b) {
         return __int2float_rn(b - a) * float(QFIX_INV);
     }
+    // a step that would leave |q| < 2 (or is not finite) keeps q and raises
+    // the divergence flag
     __device__ static __forceinline__ int drift(int q, float dt, float vx, float hdt2, float f,
                                                 bool &bad) {
         float u = (dt * vx + hdt2 * f) * float(QFIX_SCALE);
@@ -162,17 +164,60 @@ __device__ __forceinline__ void jt_cross(const T *ma, const T *mb, T L2, T L3, T
     o[4] = X[1][2] + X[2][1];
 }
 
+// Shared-memory staging of one block.  A plane slot keeps the drifted Q of
+// the tile and its ring with the five components of a site packed so that a
+// site loads in 2 (fixed point: int4 + int) or 3 (FP64: 2 double2 + double)
+// conflict-free instructions: [c0..c3 | c4] or [c0 c1 | c2 c3 | c4] arrays.
 template <typename T, int TX, int TY>
 struct Smem {
     using QS = typename Prec<T>::Q;
-    static constexpr int SX = TX + 2, SY = TY + 2, PL = SX * SY;
-    QS *Q;       // [5][5][PL] drifted Q in the storage format
-    T *X;        // [2][2][5][PL]
-    uint8_t *M;  // [5][PL]
-    __device__ __forceinline__ QS &q(int slot, int c, int lx, int ly) { return Q[(slot * 5 + c) * PL + ly * SX + lx]; }
-    __device__ __forceinline__ uint8_t &m(int slot, int lx, int ly) { return M[slot * PL + ly * SX + lx]; }
+    static constexpr int SX = TX + 2, SY = TY + 2;
+    static constexpr int PL = ((SX * SY + 3) / 4) * 4;          // sites per plane slot
+    static constexpr int SLOT_BYTES = 5 * sizeof(QS) * PL;      // multiple of 16
+    unsigned char *Q;  // [slots] x SLOT_BYTES
+    T *X;              // [2][2][5][PL] cross terms (general path)
+    uint8_t *M;        // [slots][PL]
+    __device__ __forceinline__ int idx(int lx, int ly) const { return ly * SX + lx; }
+    __device__ __forceinline__ QS &q(int slot, int c, int lx, int ly) {
+        unsigned char *b = Q + slot * SLOT_BYTES;
+        int i = idx(lx, ly);
+        if (sizeof(QS) == 4) {
+            if (c < 4) return reinterpret_cast<QS *>(b)[4 * i + c];
+            return reinterpret_cast<QS *>(b + 16 * PL)[i];
+        }
+        if (c < 2) return reinterpret_cast<QS *>(b)[2 * i + c];
+        if (c < 4) return reinterpret_cast<QS *>(b + 16 * PL)[2 * i + c - 2];
+        return reinterpret_cast<QS *>(b + 32 * PL)[i];
+    }
+    __device__ __forceinline__ void load5(int slot, int lx, int ly, QS *o) const {
+        const unsigned char *b = Q + slot * SLOT_BYTES;
+        int i = idx(lx, ly);
+        if constexpr (sizeof(QS) == 4) {
+            int4 a = reinterpret_cast<const int4 *>(b)[i];
+            o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+            o[4] = reinterpret_cast<const QS *>(b + 16 * PL)[i];
+        } else {
+            double2 a = reinterpret_cast<const double2 *>(b)[i];
+            double2 c = reinterpret_cast<const double2 *>(b + 16 * PL)[i];
+            o[0] = a.x; o[1] = a.y; o[2] = c.x; o[3] = c.y;
+            o[4] = reinterpret_cast<const QS *>(b + 32 * PL)[i];
+        }
+    }
+    __device__ __forceinline__ void store5(int slot, int lx, int ly, const QS *v) {
+        unsigned char *b = Q + slot * SLOT_BYTES;
+        int i = idx(lx, ly);
+        if constexpr (sizeof(QS) == 4) {
+            reinterpret_cast<int4 *>(b)[i] = make_int4(v[0], v[1], v[2], v[3]);
+            reinterpret_cast<QS *>(b + 16 * PL)[i] = v[4];
+        } else {
+            reinterpret_cast<double2 *>(b)[i] = make_double2(v[0], v[1]);
+            reinterpret_cast<double2 *>(b + 16 * PL)[i] = make_double2(v[2], v[3]);
+            reinterpret_cast<QS *>(b + 32 * PL)[i] = v[4];
+        }
+    }
+    __device__ __forceinline__ uint8_t &m(int slot, int lx, int ly) { return M[slot * PL + idx(lx, ly)]; }
     __device__ __forceinline__ T &x(int slot, int ax, int c, int lx, int ly) {
-        return X[((slot * 2 + ax) * 5 + c) * PL + ly * SX + lx];
+        return X[((slot * 2 + ax) * 5 + c) * PL + idx(lx, ly)];
     }
 };
 
@@ -399,52 +444,80 @@ struct Stencil<float> {
 //   F = sum_k [ L1 J^T(D2_k) + (L2+L3) Jcol_k(D2_k) + 1/4 J^T X_k(E_ka, E_kb) ]
 // with D2_k = q(j+e_k) + q(j-e_k) - 2 q(j) and the mixed differences
 // E_ab = q(j+e_a+e_b) - q(j+e_a-e_b) - q(j-e_a+e_b) + q(j-e_a-e_b); an exact
-// rearrangement of the general link-flux form for such sites.
+// rearrangement of the general link-flux form for such sites.  Expanded per
+// component (x, y, z: D2 along x, y, z; a, b, c: E_xy, E_xz, E_yz; s = x+y+z)
+// the L2 and L3 terms only enter as L2 + L3:
+//   F0 = L1 (2 s0 + s3) + L23 (x0 + z0 + z3) + L23/4 (a1 - c4)
+//   F1 = 2 L1 s1 + L23 (x1 + y1) + L23/4 (a0 + a3 + b4 + c2)
+//   F2 = 2 L1 s2 + L23 (x2 + z2) + L23/4 (a4 - b3 + c1)
+//   F3 = L1 (s0 + 2 s3) + L23 (y3 + z0 + z3) + L23/4 (a1 - b2)
+//   F4 = 2 L1 s4 + L23 (y4 + z4) + L23/4 (a2 + b1 - c0)
 template <bool THREE, typename T, int TX, int TY>
 __device__ __forceinline__ void regular_force(Smem<T, TX, TY> &S, int lx, int ly, int sc, int sp,
                                               int sm, T L1s, T L23s, T L2q, T L3q, T *Fd) {
     using ST = Stencil<T>;
-    T d2x[5], d2y[5], d2z[5];
+    using QS = typename Prec<T>::Q;
+    T dx[5], dy[5], dz[5];
+    {
+        QS c0[5], a[5], b[5];
+        S.load5(sc, lx, ly, c0);
+        S.load5(sc, lx + 1, ly, a);
+        S.load5(sc, lx - 1, ly, b);
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
-        auto q0 = S.q(sc, c, lx, ly);
-        d2x[c] = ST::sec(S.q(sc, c, lx + 1, ly), S.q(sc, c, lx - 1, ly), q0);
-        d2y[c] = ST::sec(S.q(sc, c, lx, ly + 1), S.q(sc, c, lx, ly - 1), q0);
-        d2z[c] = ST::sec(S.q(sp, c, lx, ly), S.q(sm, c, lx, ly), q0);
+        for (int c = 0; c < 5; ++c) dx[c] = ST::sec(a[c], b[c], c0[c]);
+        S.load5(sc, lx, ly + 1, a);
+        S.load5(sc, lx, ly - 1, b);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) dy[c] = ST::sec(a[c], b[c], c0[c]);
+        S.load5(sp, lx, ly, a);
+        S.load5(sm, lx, ly, b);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) dz[c] = ST::sec(a[c], b[c], c0[c]);
     }
-    T lap[5], j1[5], cx[5], cy[5], cz[5];
+    T s0 = dx[0] + dy[0] + dz[0], s1 = dx[1] + dy[1] + dz[1], s2 = dx[2] + dy[2] + dz[2];
+    T s3 = dx[3] + dy[3] + dz[3], s4 = dx[4] + dy[4] + dz[4];
+    const T L1s2 = T(2) * L1s;
+    Fd[0] = L1s * (T(2) * s0 + s3);
+    Fd[1] = L1s2 * s1;
+    Fd[2] = L1s2 * s2;
+    Fd[3] = L1s * (s0 + T(2) * s3);
+    Fd[4] = L1s2 * s4;
+    if (!THREE) return;
+    T a[5], b[5], c[5];   // E_xy, E_xz, E_yz
+    {
+        QS p0[5], p1[5], p2[5], p3[5];
+        S.load5(sc, lx + 1, ly + 1, p0);
+        S.load5(sc, lx + 1, ly - 1, p1);
+        S.load5(sc, lx - 1, ly + 1, p2);
+        S.load5(sc, lx - 1, ly - 1, p3);
 #pragma unroll
-    for (int c = 0; c < 5; ++c) lap[c] = d2x[c] + d2y[c] + d2z[c];
-    jt_sym(lap, j1);
-    if (!THREE) {
+        for (int k = 0; k < 5; ++k) a[k] = ST::mix(p0[k], p1[k], p2[k], p3[k]);
+        S.load5(sp, lx + 1, ly, p0);
+        S.load5(sm, lx + 1, ly, p1);
+        S.load5(sp, lx - 1, ly, p2);
+        S.load5(sm, lx - 1, ly, p3);
 #pragma unroll
-        for (int c = 0; c < 5; ++c) Fd[c] = L1s * j1[c];
-        return;
+        for (int k = 1; k < 5; ++k) b[k] = ST::mix(p0[k], p1[k], p2[k], p3[k]);
+        S.load5(sp, lx, ly + 1, p0);
+        S.load5(sm, lx, ly + 1, p1);
+        S.load5(sp, lx, ly - 1, p2);
+        S.load5(sm, lx, ly - 1, p3);
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+            if (k != 3) c[k] = ST::mix(p0[k], p1[k], p2[k], p3[k]);
     }
-    jt_col<0>(d2x, cx);
-    jt_col<1>(d2y, cy);
-    jt_col<2>(d2z, cz);
-    T exy[5], exz[5], eyz[5];
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-        exy[c] = ST::mix(S.q(sc, c, lx + 1, ly + 1), S.q(sc, c, lx + 1, ly - 1),
-                         S.q(sc, c, lx - 1, ly + 1), S.q(sc, c, lx - 1, ly - 1));
-        exz[c] = ST::mix(S.q(sp, c, lx + 1, ly), S.q(sm, c, lx + 1, ly),
-                         S.q(sp, c, lx - 1, ly), S.q(sm, c, lx - 1, ly));
-        eyz[c] = ST::mix(S.q(sp, c, lx, ly + 1), S.q(sm, c, lx, ly + 1),
-                         S.q(sp, c, lx, ly - 1), S.q(sm, c, lx, ly - 1));
-    }
-    T kx[5], ky[5], kz[5];
-    jt_cross<0>(exy, exz, L2q, L3q, kx);
-    jt_cross<1>(exy, eyz, L2q, L3q, ky);
-    jt_cross<2>(exz, eyz, L2q, L3q, kz);
-#pragma unroll
-    for (int c = 0; c < 5; ++c)
-        Fd[c] = L1s * j1[c] + L23s * (cx[c] + cy[c] + cz[c]) + (kx[c] + ky[c] + kz[c]);
+    const T kq = T(0.25) * L23s;
+    Fd[0] += L23s * (dx[0] + dz[0] + dz[3]) + kq * (a[1] - c[4]);
+    Fd[1] += L23s * (dx[1] + dy[1]) + kq * ((a[0] + a[3]) + (b[4] + c[2]));
+    Fd[2] += L23s * (dx[2] + dz[2]) + kq * (a[4] - b[3] + c[1]);
+    Fd[3] += L23s * (dy[3] + dz[0] + dz[3]) + kq * (a[1] - b[2]);
+    Fd[4] += L23s * (dy[4] + dz[4]) + kq * (a[2] + b[1] - c[0]);
+    (void)L2q; (void)L3q;
 }
 
+// FP32 form: 512 threads resident per SM (at most 128 registers per thread)
 template <typename T, bool THREE, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY)
+__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 512 / (TX * TY) : 1)
 fire_step_kernel(StepArgs<T> args) {
     constexpr int NT = TX * TY;
     constexpr int NSLOT = 5;
@@ -453,8 +526,8 @@ fire_step_kernel(StepArgs<T> args) {
     using QS = typename P::Q;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SM S;
-    S.Q = reinterpret_cast<QS *>(smem_raw);
-    S.X = reinterpret_cast<T *>(S.Q + NSLOT * 5 * SM::PL);
+    S.Q = smem_raw;
+    S.X = reinterpret_cast<T *>(smem_raw + NSLOT * SM::SLOT_BYTES);
     S.M = reinterpret_cast<uint8_t *>(S.X + (THREE ? 2 * 2 * 5 * SM::PL : 0));
     __shared__ double red[4 * (NT / 32)];
     __shared__ int am_last;
@@ -547,8 +620,7 @@ fire_step_kernel(StepArgs<T> args) {
             }
         }
         S.m(slot, sx, sy) = r.m;
-#pragma unroll
-        for (int c = 0; c < 5; ++c) S.q(slot, c, sx, sy) = qh[c];
+        S.store5(slot, sx, sy, qh);
     };
 
     // plane z lives in slot z mod 5: at step z the slots of z-1, z, z+1 are
@@ -576,11 +648,6 @@ fire_step_kernel(StepArgs<T> args) {
     const T sc_ = T(Stencil<T>::scale);
     const T L1s = L1 * sc_, L23s = L23 * sc_;
     const T L2q = T(0.25) * args.L2 * sc_, L3q = T(0.25) * args.L3 * sc_;
-    // quantities carried from plane to plane by the general (irregular) path
-    bool carry = false;
-    T phi_zm[5], xz_cur[5], mx_cur[5], my_cur[5];
-#pragma unroll
-    for (int c = 0; c < 5; ++c) { phi_zm[c] = T(0); xz_cur[c] = T(0); mx_cur[c] = T(0); my_cur[c] = T(0); }
 
     Acc<T> accP, accF, accV;
     T accR = T(0);
@@ -618,10 +685,13 @@ fire_step_kernel(StepArgs<T> args) {
         T Fd[5];
         if (all_reg) {
             if (own) regular_force<THREE>(S, lx, ly, sc, sp, sm, L1s, L23s, L2q, L3q, Fd);
-            carry = false;
         } else {
-            if (!carry) {
-                // rebuild the carried z quantities for plane z
+            // general path (planes touching objects or open edges): the z
+            // link below and the in-plane means are rebuilt on every such plane
+            T phi_zm[5], xz_cur[5], mx_cur[5], my_cur[5];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) { xz_cur[c] = T(0); mx_cur[c] = T(0); my_cur[c] = T(0); }
+            {
                 T xz_m[5];
 #pragma unroll
                 for (int c = 0; c < 5; ++c) xz_m[c] = T(0);
@@ -746,19 +816,14 @@ fire_step_kernel(StepArgs<T> args) {
                     for (int c = 0; c < 5; ++c) Fd[c] = -grad[c];
                 }
             }
-#pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                phi_zm[c] = phi_zp[c];
-                if (THREE) { xz_cur[c] = xz_nxt[c]; mx_cur[c] = mx_nxt[c]; my_cur[c] = my_nxt[c]; }
-            }
-            carry = true;
         }
 
         if (own) {
             QS q0[5];
             T qv[5], fb[5], Fn[5];
+            S.load5(sc, lx, ly, q0);
 #pragma unroll
-            for (int c = 0; c < 5; ++c) { q0[c] = S.q(sc, c, lx, ly); qv[c] = P::val(q0[c]); }
+            for (int c = 0; c < 5; ++c) qv[c] = P::val(q0[c]);
             bulk_force(qv, args.A, args.B, args.C, fb);
 #pragma unroll
             for (int c = 0; c < 5; ++c) Fn[c] = Fd[c] + fb[c];
@@ -833,9 +898,9 @@ fire_step_kernel(StepArgs<T> args) {
 
 template <typename T, bool THREE, int TX, int TY>
 static size_t step_smem_bytes() {
-    constexpr int PL = (TX + 2) * (TY + 2);
-    size_t b = sizeof(typename Prec<T>::Q) * 5 * 5 * PL + sizeof(T) * (THREE ? 2 * 2 * 5 * PL : 0) +
-               5 * PL;
+    using SM = Smem<T, TX, TY>;
+    constexpr int PL = SM::PL;
+    size_t b = 5 * (size_t)SM::SLOT_BYTES + sizeof(T) * (THREE ? 2 * 2 * 5 * PL : 0) + 5 * PL;
     return (b + 15) & ~size_t(15);
 }
 
@@ -868,10 +933,12 @@ dim3 step_grid(const LatticeDev &L, int zchunk, int tx, int ty) {
     return dim3((L.nx + tx - 1) / tx, (L.ny + ty - 1) / ty, (L.nz + zchunk - 1) / zchunk);
 }
 
+// tile of one block: the FP32 form runs 32x4 tiles at 4 blocks per SM (128
+// registers per thread), the FP64 form 32x8 tiles at one block per SM
 void step_tile(int fp32, int three, int *tx, int *ty) {
-    (void)fp32; (void)three;
+    (void)three;
     *tx = 32;
-    *ty = 8;
+    *ty = fp32 ? 4 : 8;
 }
 
 template <typename T, bool THREE, int TX, int TY>
@@ -882,14 +949,14 @@ static cudaError_t prepare_impl() {
 }
 
 cudaError_t prepare_fire_step(int fp32, int three) {
-    if (fp32) return three ? prepare_impl<float, true, 32, 8>() : prepare_impl<float, false, 32, 8>();
+    if (fp32) return three ? prepare_impl<float, true, 32, 4>() : prepare_impl<float, false, 32, 4>();
     return three ? prepare_impl<double, true, 32, 8>() : prepare_impl<double, false, 32, 8>();
 }
 
 cudaError_t launch_fire_step(const StepLaunch &sl, cudaStream_t stream) {
     if (sl.fp32) {
-        if (sl.three) return launch_impl<float, true, 32, 8>(sl, stream);
-        return launch_impl<float, false, 32, 8>(sl, stream);
+        if (sl.three) return launch_impl<float, true, 32, 4>(sl, stream);
+        return launch_impl<float, false, 32, 4>(sl, stream);
     }
     if (sl.three) return launch_impl<double, true, 32, 8>(sl, stream);
     return launch_impl<double, false, 32, 8>(sl, stream);
