@@ -219,6 +219,40 @@ lq_status lq_fire_result(lq_solver *s, lq_result *out);
 lq_status lq_get_state(lq_solver *s, void *buf, size_t *bytes);
 lq_status lq_set_state(lq_solver *s, const void *buf, size_t bytes);
 
+/* ---- batches: many lattices, one persistent kernel per FIRE iteration ------------------ */
+
+/* Independent minimisations advanced together (section III.B's per-site work
+   is independent across lattices): each FIRE iteration of every lattice in
+   the batch is one launch of a persistent kernel whose blocks stride over
+   (lattice, tile, z chunk) work items; launches are captured in CUDA graphs.
+   Every lattice keeps its own state, FIRE scalars (Algorithm 1) and
+   reductions; with the solvers' own tiling (the default) a one-constant
+   lattice advances bit-for-bit as it does alone, a three-constant one to
+   within rounding (the two kernels may fuse its products differently).  All solvers must share device, precision and
+   n_constants (LQ_EINVAL otherwise).  The batch runs on a stream of its own
+   (ordered against the solvers' streams by synchronising them around each
+   call) and borrows the solvers until lq_batch_destroy: destroy the batch
+   before them.  Allocates its work-item and reduction tables. */
+typedef struct lq_batch lq_batch;
+lq_status lq_batch_create(lq_solver *const *solvers, int n, lq_batch **out);
+void lq_batch_destroy(lq_batch *b);
+const char *lq_batch_last_error(const lq_batch *b);
+/* Tiling of the persistent kernel: tile 32 x tile_y (4 or 8), z chunk > 0. */
+lq_status lq_batch_set_tiling(lq_batch *b, int tile_y, int zchunk);
+lq_status lq_batch_get_tiling(const lq_batch *b, int *tile_y, int *zchunk);
+/* Autotuner: times every tile_y in {4, 8} and z chunk in {8, ..., 128} over
+   `launches` launches on shadow copies of the FIRE states (the lattices'
+   states do not advance) and keeps the fastest; *best_ms may be NULL.
+   Starts FIRE on lattices that have not started. */
+lq_status lq_batch_autotune(lq_batch *b, const lq_fire_params *p, int launches, double *best_ms);
+/* n more FIRE iterations of every lattice (converged ones stay put); out
+   holds one lq_result per solver, or NULL. */
+lq_status lq_batch_step(lq_batch *b, const lq_fire_params *p, int64_t n, lq_result *out);
+/* Minimise every lattice from its current Q (FIRE restarted); returns LQ_OK
+   when all converged, else the worst of LQ_EDIVERGED / LQ_ENOTCONVERGED /
+   LQ_ETIMEOUT; out as above, energies filled. */
+lq_status lq_batch_minimize(lq_batch *b, const lq_fire_params *p, lq_result *out);
+
 /* ---- without allocation ------------------------------------------------------------ */
 
 /* The paper has no counterpart to this call; it exists for callers that cannot

@@ -20,10 +20,26 @@ struct StepLaunch {
     int zchunk, force_only, fp32, three;
 };
 
+// one block's share of a batched step: lattice, tile, z range, and its
+// number among that lattice's nblk blocks (the single-lattice numbering)
+struct WorkItem {
+    int lattice, bx, by, z0, z1, nblk, bid, pad;
+};
+
 dim3 step_grid(const LatticeDev &L, int zchunk, int tx, int ty);
 void step_tile(int fp32, int three, int *tx, int *ty);
 cudaError_t prepare_fire_step(int fp32, int three);
 cudaError_t launch_fire_step(const StepLaunch &sl, cudaStream_t stream);
+
+// batched steps (tile 32 x ty, ty in {4, 8})
+size_t step_args_bytes(int fp32);
+void step_args_pack(const StepLaunch &sl, void *out);   // host memory, step_args_bytes()
+cudaError_t prepare_fire_batch(int fp32, int three, int ty);
+int fire_batch_blocks_per_sm(int fp32, int three, int ty);
+cudaError_t launch_fire_batch(int fp32, int three, int ty, const void *dev_args,
+                              const WorkItem *items, int nitems, int grid, cudaStream_t stream);
+// running[0] = number of lattices whose FIRE status is still running
+cudaError_t batch_running(FireDev *const *states, int n, unsigned int *running, cudaStream_t s);
 
 // geometry construction (device)
 struct AnchorSpecDev {

@@ -13,6 +13,7 @@
 #include "lqmin.h"
 #include "lq_common.cuh"
 #include "lq_kernels.h"
+#include "solver_internal.h"
 
 using namespace lq;
 
@@ -20,54 +21,14 @@ namespace {
 
 thread_local std::string g_create_error;
 
-struct HostObject {
-    int type;                       // 0 wall, 1 sphere, 2 object sites, 3 anchored sites
-    int axis = 0, plane = 0;
-    double c[3] = {0, 0, 0}, R = 0;
-    lq_anchoring anch{};
-    std::vector<int32_t> xyz;
-    std::vector<lq_anchoring> per_site;
-};
+
 
 }  // namespace
 
-struct lq_solver {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;        // created by lq_create when given NULL
-    int fp32 = 0, three = 0;
-    LatticeDev L{};
-    lq_material mat{};
-    double S0 = 0;
-    size_t esize = 8;
 
-    std::vector<HostObject> objects;
-    bool geom_dirty = true;
 
-    uint8_t *mask = nullptr;
-    int *row_start = nullptr, *rec_x = nullptr;
-    void *recs = nullptr;
-    long long nrec = 0, nsim = 0;
-
-    void *q[2] = {nullptr, nullptr}, *v[2] = {nullptr, nullptr}, *F[2] = {nullptr, nullptr};
-    double *xfer = nullptr;         // 5 N doubles for conversions and readback
-    FireDev *st = nullptr;
-    FireDev *st_host = nullptr;     // pinned mirror
-    double *partials = nullptr;
-    int partials_cap = 0;
-    double *out3 = nullptr;
-
-    int cur = 0;                    // buffer holding the state (host view)
-    bool fire_ready = false;
-    int zchunk = 0;                 // 0 = automatic
-
-    cudaGraphExec_t gexec = nullptr;
-    int graph_k = 0;
-    size_t bytes = 0;
-    std::string err;
-};
-
-namespace {
+namespace lq {
+namespace detail {
 
 lq_status fail(lq_solver *s, lq_status st, const char *fmt, ...) {
     char buf[512];
@@ -414,7 +375,10 @@ lq_status copy_out_state(lq_solver *s, const void *src, double *out, bool is_q =
     return LQ_OK;
 }
 
-}  // namespace
+}  // namespace detail
+}  // namespace lq
+
+using namespace lq::detail;
 
 // ---- C interface ---------------------------------------------------------------
 

@@ -216,6 +216,7 @@ struct Smem {
         }
     }
     __device__ __forceinline__ uint8_t &m(int slot, int lx, int ly) { return M[slot * PL + idx(lx, ly)]; }
+
     __device__ __forceinline__ T &x(int slot, int ax, int c, int lx, int ly) {
         return X[((slot * 2 + ax) * 5 + c) * PL + idx(lx, ly)];
     }
@@ -515,28 +516,26 @@ __device__ __forceinline__ void regular_force(Smem<T, TX, TY> &S, int lx, int ly
     (void)L2q; (void)L3q;
 }
 
-// FP32 form: 512 threads resident per SM (at most 128 registers per thread)
+// One block's work for one lattice: the tile with origin (bx*TX, by*TY),
+// planes [z0, z1), block number bid of the nblk blocks of that lattice's
+// step (its partial-sum slot).  Shared memory is the caller's.
 template <typename T, bool THREE, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 512 / (TX * TY) : 1)
-fire_step_kernel(StepArgs<T> args) {
+__device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int by, int z0, int z1,
+                                          int nblk, int bid, unsigned char *smem_raw, double *red,
+                                          int *am_last_p) {
     constexpr int NT = TX * TY;
     constexpr int NSLOT = 5;
     using SM = Smem<T, TX, TY>;
     using P = Prec<T>;
     using QS = typename P::Q;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int &am_last = *am_last_p;
     SM S;
     S.Q = smem_raw;
     S.X = reinterpret_cast<T *>(smem_raw + NSLOT * SM::SLOT_BYTES);
     S.M = reinterpret_cast<uint8_t *>(S.X + (THREE ? 2 * 2 * 5 * SM::PL : 0));
-    __shared__ double red[4 * (NT / 32)];
-    __shared__ int am_last;
-
     const LatticeDev L = args.L;
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * args.zchunk;
-    const int z1 = min(z0 + args.zchunk, L.nz);
+    const int x0 = bx * TX, y0 = by * TY;
     const int gx = x0 + tx, gy = y0 + ty;
     const bool valid = gx < L.nx && gy < L.ny;
     const int lx = tx + 1, ly = ty + 1;
@@ -870,8 +869,7 @@ fire_step_kernel(StepArgs<T> args) {
     double sP = accP.get(), sF = accF.get(), sV = accV.get();
     double sR = bad ? (double)INFINITY : (double)accR;
     block_reduce4<NT>(sP, sF, sV, sR, red);
-    const int nblocks = gridDim.x * gridDim.y * gridDim.z;
-    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int nblocks = nblk;
     if (threadIdx.x == 0) {
         double *p = args.partials + 4 * (long long)bid;
         p[0] = sP; p[1] = sF; p[2] = sV; p[3] = sR;
@@ -894,6 +892,41 @@ fire_step_kernel(StepArgs<T> args) {
     }
 }
 
+
+// one FIRE iteration of one lattice: one block per tile and z chunk
+template <typename T, bool THREE, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 512 / (TX * TY) : 1)
+fire_step_kernel(StepArgs<T> args) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[4 * (TX * TY / 32)];
+    __shared__ int am_last;
+    const int z0 = blockIdx.z * args.zchunk;
+    const int z1 = min(z0 + args.zchunk, args.L.nz);
+    const int nblk = gridDim.x * gridDim.y * gridDim.z;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    step_tile<T, THREE, TX, TY>(args, blockIdx.x, blockIdx.y, z0, z1, nblk, bid, smem_raw, red,
+                                &am_last);
+}
+
+// one FIRE iteration of every lattice of a batch: a persistent grid strides
+// over the work items (lattice, tile, z chunk); each lattice keeps its own
+// partial sums, last-block ticket and FIRE state, so a lattice advances
+// exactly as it would alone with the same tile and z chunk
+template <typename T, bool THREE, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 512 / (TX * TY) : 1)
+fire_batch_kernel(const StepArgs<T> *__restrict__ args, const WorkItem *__restrict__ items,
+                  int nitems) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[4 * (TX * TY / 32)];
+    __shared__ int am_last;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const WorkItem w = items[it];
+        step_tile<T, THREE, TX, TY>(args[w.lattice], w.bx, w.by, w.z0, w.z1, w.nblk, w.bid,
+                                    smem_raw, red, &am_last);
+        __syncthreads();   // shared memory is reused by the next item
+    }
+}
+
 // ---- host launchers ---------------------------------------------------------
 
 template <typename T, bool THREE, int TX, int TY>
@@ -904,9 +937,8 @@ static size_t step_smem_bytes() {
     return (b + 15) & ~size_t(15);
 }
 
-template <typename T, bool THREE, int TX, int TY>
-static cudaError_t launch_impl(const StepLaunch &sl, cudaStream_t stream) {
-    StepArgs<T> a;
+template <typename T>
+static void pack_args(const StepLaunch &sl, StepArgs<T> &a) {
     for (int b = 0; b < 2; ++b) {
         a.q[b] = static_cast<typename Prec<T>::Q *>(sl.q[b]);
         a.v[b] = static_cast<T *>(sl.v[b]);
@@ -922,6 +954,12 @@ static cudaError_t launch_impl(const StepLaunch &sl, cudaStream_t stream) {
     a.partials = sl.partials;
     a.zchunk = sl.zchunk;
     a.force_only = sl.force_only;
+}
+
+template <typename T, bool THREE, int TX, int TY>
+static cudaError_t launch_impl(const StepLaunch &sl, cudaStream_t stream) {
+    StepArgs<T> a;
+    pack_args<T>(sl, a);
     size_t smem = step_smem_bytes<T, THREE, TX, TY>();
     auto kern = fire_step_kernel<T, THREE, TX, TY>;
     dim3 grid = step_grid(sl.L, sl.zchunk, TX, TY);
@@ -960,6 +998,76 @@ cudaError_t launch_fire_step(const StepLaunch &sl, cudaStream_t stream) {
     }
     if (sl.three) return launch_impl<double, true, 32, 8>(sl, stream);
     return launch_impl<double, false, 32, 8>(sl, stream);
+}
+
+// ---- batched launches ----------------------------------------------------------
+
+size_t step_args_bytes(int fp32) { return fp32 ? sizeof(StepArgs<float>) : sizeof(StepArgs<double>); }
+
+void step_args_pack(const StepLaunch &sl, void *out) {
+    if (sl.fp32) pack_args<float>(sl, *static_cast<StepArgs<float> *>(out));
+    else pack_args<double>(sl, *static_cast<StepArgs<double> *>(out));
+}
+
+template <typename T, bool THREE, int TY>
+static cudaError_t prepare_batch_impl() {
+    return cudaFuncSetAttribute(fire_batch_kernel<T, THREE, 32, TY>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)step_smem_bytes<T, THREE, 32, TY>());
+}
+
+template <typename T, bool THREE, int TY>
+static int blocks_impl() {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fire_batch_kernel<T, THREE, 32, TY>, 32 * TY,
+                                                  step_smem_bytes<T, THREE, 32, TY>());
+    return nb;
+}
+
+template <typename T, bool THREE, int TY>
+static cudaError_t batch_impl(const void *args, const WorkItem *items, int nitems, int grid,
+                              cudaStream_t stream) {
+    fire_batch_kernel<T, THREE, 32, TY><<<grid, 32 * TY, step_smem_bytes<T, THREE, 32, TY>(), stream>>>(
+        static_cast<const StepArgs<T> *>(args), items, nitems);
+    return cudaGetLastError();
+}
+
+#define LQ_BATCH_DISPATCH(FN, ...)                                                         \
+    do {                                                                                   \
+        if (fp32) {                                                                        \
+            if (three) return ty == 4 ? FN<float, true, 4>(__VA_ARGS__) : FN<float, true, 8>(__VA_ARGS__); \
+            return ty == 4 ? FN<float, false, 4>(__VA_ARGS__) : FN<float, false, 8>(__VA_ARGS__);          \
+        }                                                                                  \
+        if (three) return ty == 4 ? FN<double, true, 4>(__VA_ARGS__) : FN<double, true, 8>(__VA_ARGS__);   \
+        return ty == 4 ? FN<double, false, 4>(__VA_ARGS__) : FN<double, false, 8>(__VA_ARGS__);            \
+    } while (0)
+
+cudaError_t prepare_fire_batch(int fp32, int three, int ty) { LQ_BATCH_DISPATCH(prepare_batch_impl); }
+
+int fire_batch_blocks_per_sm(int fp32, int three, int ty) { LQ_BATCH_DISPATCH(blocks_impl); }
+
+cudaError_t launch_fire_batch(int fp32, int three, int ty, const void *dev_args,
+                              const WorkItem *items, int nitems, int grid, cudaStream_t stream) {
+    LQ_BATCH_DISPATCH(batch_impl, dev_args, items, nitems, grid, stream);
+}
+
+__global__ void k_batch_running(FireDev *const *states, int n, unsigned int *running) {
+    unsigned int c = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) c += (states[i]->status == FIRE_RUNNING) ? 1u : 0u;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    __shared__ unsigned int part[8];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int t = 0;
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += part[w];
+        *running = t;
+    }
+}
+
+cudaError_t batch_running(FireDev *const *states, int n, unsigned int *running, cudaStream_t s) {
+    k_batch_running<<<1, 256, 0, s>>>(states, n, running);
+    return cudaGetLastError();
 }
 
 }  // namespace lq

@@ -33,7 +33,9 @@ EXPORTS = [
     "lq_set_q_device", "lq_init_random_uniaxial", "lq_get_q", "lq_get_velocity", "lq_get_force",
     "lq_force", "lq_energy", "lq_order_field", "lq_fire_reset", "lq_step", "lq_minimize",
     "lq_fire_result", "lq_get_state", "lq_set_state", "lq_set_zchunk", "lq_device_bytes",
-    "lq_energy_noalloc",
+    "lq_energy_noalloc", "lq_batch_create", "lq_batch_destroy", "lq_batch_last_error",
+    "lq_batch_set_tiling", "lq_batch_get_tiling", "lq_batch_autotune", "lq_batch_step",
+    "lq_batch_minimize",
 ]
 
 
@@ -118,6 +120,14 @@ def load(path: str = LIB_PATH):
         "lq_set_zchunk": (C.c_int, [S, C.c_int]),
         "lq_device_bytes": (C.c_size_t, [S]),
         "lq_energy_noalloc": (C.c_int, [C.POINTER(Lattice), C.POINTER(Material), p, p, p, p]),
+        "lq_batch_create": (C.c_int, [p, C.c_int, C.POINTER(p)]),
+        "lq_batch_destroy": (None, [p]),
+        "lq_batch_last_error": (C.c_char_p, [p]),
+        "lq_batch_set_tiling": (C.c_int, [p, C.c_int, C.c_int]),
+        "lq_batch_get_tiling": (C.c_int, [p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "lq_batch_autotune": (C.c_int, [p, C.POINTER(FireParams), C.c_int, C.POINTER(d)]),
+        "lq_batch_step": (C.c_int, [p, C.POINTER(FireParams), i64, p]),
+        "lq_batch_minimize": (C.c_int, [p, C.POINTER(FireParams), p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -308,6 +318,61 @@ class Solver:
 
     def device_bytes(self):
         return self.lib.lq_device_bytes(self.h)
+
+
+class Batch:
+    """Several solvers advanced by one persistent kernel (see lq_batch_create).
+    Keeps references to the solvers; destroy the batch before them."""
+
+    def __init__(self, solvers):
+        self.lib = load()
+        self.solvers = list(solvers)
+        arr = (C.c_void_p * len(self.solvers))(*[s.h.value for s in self.solvers])
+        h = C.c_void_p()
+        st = self.lib.lq_batch_create(arr, len(self.solvers), C.byref(h))
+        if st != LQ_OK:
+            raise LqError(st, "lq_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lq_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, st, ok=(LQ_OK,)):
+        if st not in ok:
+            raise LqError(st, self.lib.lq_batch_last_error(self.h).decode())
+        return st
+
+    def tiling(self):
+        a, b = C.c_int(), C.c_int()
+        self._ck(self.lib.lq_batch_get_tiling(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def set_tiling(self, tile_y, zchunk):
+        self._ck(self.lib.lq_batch_set_tiling(self.h, int(tile_y), int(zchunk)))
+
+    def autotune(self, params: FireParams, launches=5):
+        ms = C.c_double()
+        self._ck(self.lib.lq_batch_autotune(self.h, C.byref(params), int(launches), C.byref(ms)))
+        return self.tiling(), ms.value
+
+    def step(self, params: FireParams, n: int):
+        out = (Result * len(self.solvers))()
+        self._ck(self.lib.lq_batch_step(self.h, C.byref(params), int(n), C.cast(out, C.c_void_p)))
+        return list(out)
+
+    def minimize(self, params: FireParams):
+        out = (Result * len(self.solvers))()
+        st = self._ck(self.lib.lq_batch_minimize(self.h, C.byref(params), C.cast(out, C.c_void_p)),
+                      ok=(LQ_OK, LQ_ENOTCONVERGED, LQ_ETIMEOUT, LQ_EDIVERGED))
+        return st, list(out)
 
 
 def solver_for(cfg: dict, precision=LQ_FP64, stream=None, A=None, B=None, C_=None,

@@ -1,0 +1,141 @@
+"""Batched form: several uneven lattices advanced by one persistent kernel.
+Each lattice's result in the mix equals its result alone: bit for bit for
+one-constant lattices with the same tiling (their arithmetic has no product
+the compiler could fuse differently in the two kernels), within rounding for
+three-constant lattices and after autotuning; a converged lattice stays put
+while the others advance."""
+import numpy as np
+import pytest
+
+from _helpers import HOM, PLANAR, need_gpu, rand_q
+from paper_1911_07045_b300 import lqmin, synth
+
+pytestmark = pytest.mark.gpu
+
+A, B, C = synth.A_5CB, synth.B_5CB, synth.C_5CB
+FP = dict(synth.FIRE_DEFAULTS)
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def lattices(three):
+    L = (2.32, 0.5, 0.3) if three else (2.32, 0.0, 0.0)
+    return [
+        dict(shape=(40, 24, 20), L=L, objects=[dict(type="sphere", c=(20.0, 12.0, 10.0), R=5.0,
+                                                    anchor=HOM())]),
+        dict(shape=(32, 32, 32), L=L, objects=[]),
+        dict(shape=(33, 17, 9), L=L, objects=[dict(type="wall", axis=2, plane=0, anchor=PLANAR())]),
+        dict(shape=(48, 48, 16), L=L, objects=[dict(type="sphere", c=(10.0, 30.0, 8.0), R=3.5,
+                                                    anchor=HOM()),
+                                               dict(type="sphere", c=(35.0, 12.0, 8.0), R=4.0,
+                                                    anchor=HOM())]),
+        dict(shape=(16, 16, 64), L=L, objects=[dict(type="wall", axis=2, plane=0, anchor=HOM()),
+                                               dict(type="wall", axis=2, plane=63, anchor=HOM())]),
+    ]
+
+
+def make(cfg, prec):
+    s = lqmin.Solver(cfg["shape"], A, B, C, *cfg["L"], precision=prec)
+    s.add_objects(cfg["objects"])
+    return s
+
+
+@pytest.mark.parametrize("prec,three", [(1, False), (0, False), (0, True), (1, True)])
+def test_batch_matches_alone(prec, three):
+    cfgs = lattices(three)
+    alone = [make(c, prec) for c in cfgs]
+    mixed = [make(c, prec) for c in cfgs]
+    for k, (a, m, c) in enumerate(zip(alone, mixed, cfgs)):
+        q = synth.random_uniaxial_q(c["shape"], 100 + k)
+        a.set_q(q)
+        m.set_q(q)
+    batch = lqmin.Batch(mixed)
+    ty, zc = batch.tiling()
+    p = lqmin.fire_params(**dict(FP, max_iter=10 ** 6, force_tol=1e-14))
+    res_b = batch.step(p, 23)
+    for a, m, rb in zip(alone, mixed, res_b):
+        a.set_zchunk(zc)
+        ra = a.step(p, 23)
+        assert ra.iterations == rb.iterations == 23
+        assert ra.dt == rb.dt and ra.alpha == rb.alpha and ra.npos == rb.npos
+        if not three:
+            assert np.array_equal(a.get_q(), m.get_q())
+            assert np.array_equal(a.get_velocity(), m.get_velocity())
+            assert np.array_equal(a.get_force(), m.get_force())
+        else:
+            tol = 1e-11 if prec == 0 else 2e-6
+            for x, y in ((a.get_q(), m.get_q()), (a.get_force(), m.get_force())):
+                assert np.abs(x - y).max() <= tol * np.abs(x).max()
+    batch.close()
+
+
+def test_batch_minimize_matches_alone():
+    cfgs = lattices(True)[:3]
+    alone = [make(c, 0) for c in cfgs]
+    mixed = [make(c, 0) for c in cfgs]
+    for k, (a, m, c) in enumerate(zip(alone, mixed, cfgs)):
+        n = np.array([0.2, 0.1, 1.0])
+        S0 = synth.s0_closed_form(A, B, C)
+        q = np.repeat(synth.uniaxial_q((n / np.linalg.norm(n))[:, None], S0),
+                      int(np.prod(c["shape"])), axis=1)
+        q = q + 0.02 * rand_q(q.shape[1], 7 + k, 1.0)
+        a.set_q(q)
+        m.set_q(q)
+    batch = lqmin.Batch(mixed)
+    ty, zc = batch.tiling()
+    p = lqmin.fire_params(**dict(FP, max_iter=200000, force_tol=1e-7))
+    code, res = batch.minimize(p)
+    assert code == lqmin.LQ_OK
+    for a, r in zip(alone, res):
+        a.set_zchunk(zc)
+        ca, ra = a.minimize(p)
+        assert ca == lqmin.LQ_OK and r.fire_status == lqmin.FIRE_CONVERGED
+        assert abs(ra.iterations - r.iterations) <= max(2, ra.iterations // 100)
+        assert abs(ra.energy - r.energy) <= 1e-10 * abs(ra.energy)
+    batch.close()
+
+
+def test_autotune_leaves_state_and_tuned_run_agrees():
+    cfgs = lattices(False)
+    alone = [make(c, 1) for c in cfgs]
+    mixed = [make(c, 1) for c in cfgs]
+    for k, (a, m, c) in enumerate(zip(alone, mixed, cfgs)):
+        q = synth.random_uniaxial_q(c["shape"], 300 + k)
+        a.set_q(q)
+        m.set_q(q)
+    batch = lqmin.Batch(mixed)
+    p = lqmin.fire_params(**dict(FP, max_iter=10 ** 6, force_tol=1e-14))
+    before = [m.get_q() for m in mixed]
+    (ty, zc), ms = batch.autotune(p, launches=3)
+    assert ty in (4, 8) and zc in (8, 16, 32, 64, 128) and ms > 0
+    for m, q in zip(mixed, before):
+        assert np.array_equal(m.get_q(), q)
+        assert m.fire_result().iterations == 0
+    res = batch.step(p, 10)
+    for a, m, r in zip(alone, mixed, res):
+        ra = a.step(p, 10)
+        assert ra.iterations == r.iterations == 10
+        qa, qm = a.get_q(), m.get_q()
+        assert np.abs(qa - qm).max() <= 1e-5 * max(np.abs(qa).max(), 1e-30)
+    batch.close()
+
+
+def test_converged_lattice_stays_put():
+    cfgs = lattices(False)[:3]
+    ss = [make(c, 0) for c in cfgs]
+    n = np.array([0.0, 0.0, 1.0])
+    S0 = synth.s0_closed_form(A, B, C)
+    uniform = np.repeat(synth.uniaxial_q(n[:, None], S0), int(np.prod(cfgs[1]["shape"])), axis=1)
+    ss[0].set_q(synth.random_uniaxial_q(cfgs[0]["shape"], 1))
+    ss[1].set_q(uniform)                      # already at the minimum
+    ss[2].set_q(synth.random_uniaxial_q(cfgs[2]["shape"], 2))
+    batch = lqmin.Batch(ss)
+    p = lqmin.fire_params(**dict(FP, max_iter=10 ** 6, force_tol=1e-9))
+    res = batch.step(p, 15)
+    assert res[1].fire_status == lqmin.FIRE_CONVERGED and res[1].iterations == 0
+    assert np.array_equal(ss[1].get_q(), uniform)
+    assert res[0].iterations == 15 and res[2].iterations == 15
+    batch.close()
