@@ -40,6 +40,7 @@ extern "C" {
 #endif
 
 typedef struct lq_solver lq_solver;
+typedef struct lq_server lq_server;
 
 typedef enum {
     LQ_OK = 0,
@@ -252,6 +253,64 @@ lq_status lq_batch_step(lq_batch *b, const lq_fire_params *p, int64_t n, lq_resu
    when all converged, else the worst of LQ_EDIVERGED / LQ_ENOTCONVERGED /
    LQ_ETIMEOUT; out as above, energies filled. */
 lq_status lq_batch_minimize(lq_batch *b, const lq_fire_params *p, lq_result *out);
+
+/* ---- serving: continuous batching of minimisation requests -------------------------- */
+
+/* An object of a request, the same objects lq_add_* take (section V). */
+enum { LQ_OBJ_WALL = 0, LQ_OBJ_SPHERE = 1, LQ_OBJ_SITES = 2, LQ_OBJ_ANCHORED = 3 };
+typedef struct {
+    int type;                       /* LQ_OBJ_* */
+    int axis, plane;                /* wall */
+    double c[3], R;                 /* sphere */
+    lq_anchoring anch;              /* wall, sphere, object sites */
+    int64_t n;                      /* site lists: number of sites */
+    const int32_t *xyz;             /* site lists: 3n coordinates */
+    const lq_anchoring *per_site;   /* anchored sites: n records */
+} lq_object;
+
+/* One minimisation (section V: set up a lattice and objects, start from a
+   given or seeded random Q, minimise to a force tolerance). */
+typedef struct {
+    lq_lattice lattice;
+    lq_material material;
+    int n_objects;
+    const lq_object *objects;
+    const double *q0;               /* 5N host values, or NULL: seeded random start */
+    uint64_t seed;                  /* random start (lq_init_random_uniaxial) */
+    double S;                       /* its order, <= 0: S0 */
+    lq_fire_params params;          /* wall_timeout_s counts from admission */
+    int want_order_field;           /* keep lambda_max per site for the poll */
+} lq_request;
+
+typedef struct {
+    int64_t queued, active, completed;
+    size_t bytes_in_use, budget;    /* estimated device bytes of the active solves */
+    double site_updates;            /* sum over finished solves of N x iterations */
+} lq_server_stats;
+
+/* A server on the current device: a worker thread admits queued requests
+   while the estimated device memory of the active solves stays within
+   hbm_budget_bytes and at most max_active run at once; every active solve
+   is advanced by the same persistent-kernel launches (one batch per
+   distortion form), and finished solves are retired between rounds of
+   launches, so requests arriving while others run join them as memory frees
+   up.  A one-constant solve follows the same trajectory as it would alone. */
+lq_status lq_server_create(size_t hbm_budget_bytes, int precision, int max_active, lq_server **out);
+/* Stops the worker (running solves are dropped) and frees everything. */
+void lq_server_destroy(lq_server *sv);
+/* Queue a request (its arrays are copied); LQ_ENOMEM if it could never fit
+   the budget.  *ticket identifies it. */
+lq_status lq_server_submit(lq_server *sv, const lq_request *rq, uint64_t *ticket);
+/* LQ_EBUSY while queued or running; then the solve's status (LQ_OK when
+   converged, LQ_ENOTCONVERGED, LQ_EDIVERGED, LQ_ETIMEOUT, or the error that
+   stopped its set-up), *out with out->seconds = time from submission to
+   completion and the final energy, S_out (N doubles, may be NULL) the order
+   field if requested.  A finished ticket can be read once. */
+lq_status lq_server_poll(lq_server *sv, uint64_t ticket, lq_result *out, double *S_out);
+/* As lq_server_poll, waiting up to timeout_s (<= 0: no limit). */
+lq_status lq_server_wait(lq_server *sv, uint64_t ticket, double timeout_s, lq_result *out,
+                         double *S_out);
+lq_status lq_server_stats_get(lq_server *sv, lq_server_stats *out);
 
 /* ---- without allocation ------------------------------------------------------------ */
 

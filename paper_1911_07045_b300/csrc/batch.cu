@@ -26,7 +26,9 @@ struct lq_batch {
     std::vector<lq_solver *> solvers;
     int device = 0, fp32 = 0, three = 0, nsm = 148;
     cudaStream_t stream = nullptr;
-    int ty = 0, zchunk = 0;           // current tiling (0 = not chosen)
+    int ty = 0, zchunk = 0;           // tiling; zchunk 0 = each lattice's own
+    bool tables_ok = false;
+    int cap = 0;                      // lattices the device arrays hold
     // device tables
     void *args = nullptr;             // StepArgs per lattice
     void *shadow_args = nullptr;      // the same, pointing at shadow FIRE states
@@ -68,12 +70,15 @@ void drop_graph(lq_batch *b) {
 }
 
 // work items and reduction slots for tile 32 x ty and z chunk zc
-lq_status build_items(lq_batch *b, int ty, int zc, bool shadow) {
+lq_status build_items(lq_batch *b, int ty, int zc_all, bool shadow) {
     std::vector<WorkItem> items;
     std::vector<long long> base(b->solvers.size());
+    std::vector<int> zcs(b->solvers.size());
     long long slots = 0;
     for (size_t l = 0; l < b->solvers.size(); ++l) {
         const LatticeDev &L = b->solvers[l]->L;
+        int zc = zc_all > 0 ? zc_all : effective_zchunk(b->solvers[l]);
+        zcs[l] = zc;
         int gx = (L.nx + 31) / 32, gy = (L.ny + ty - 1) / ty, gz = (L.nz + zc - 1) / zc;
         int nblk = gx * gy * gz;
         base[l] = slots;
@@ -114,7 +119,7 @@ lq_status build_items(lq_batch *b, int ty, int zc, bool shadow) {
         lq_solver *s = b->solvers[l];
         StepLaunch sl = make_launch(s, 0);
         sl.partials = b->partials + 4 * base[l];
-        sl.zchunk = zc;
+        sl.zchunk = zcs[l];
         if (shadow) sl.st = b->shadow + l;
         step_args_pack(sl, host.data() + ab * l);
     }
@@ -130,12 +135,18 @@ int persistent_grid(lq_batch *b, int ty) {
 }
 
 lq_status set_tiling(lq_batch *b, int ty, int zc) {
-    if (b->ty == ty && b->zchunk == zc) return LQ_OK;
+    if (b->tables_ok && b->ty == ty && b->zchunk == zc) return LQ_OK;
     drop_graph(b);
-    lq_status r = build_items(b, ty, zc, false);
-    if (r != LQ_OK) return r;
+    b->tables_ok = false;
+    if (!b->solvers.empty()) {
+        lq_status r = build_items(b, ty, zc, false);
+        if (r != LQ_OK) return r;
+    } else {
+        b->nitems = 0;
+    }
     b->ty = ty;
     b->zchunk = zc;
+    b->tables_ok = true;
     return LQ_OK;
 }
 
@@ -192,60 +203,111 @@ lq_status collect(lq_batch *b, lq_result *out, double secs) {
 
 }  // namespace
 
-extern "C" {
+namespace lq {
+namespace detail {
 
-lq_status lq_batch_create(lq_solver *const *solvers, int n, lq_batch **out) {
-    if (!solvers || n <= 0 || !out) return LQ_EINVAL;
+lq_status batch_new(int device, int fp32, int three, lq_batch **out) {
     *out = nullptr;
     lq_batch *b = new lq_batch();
-    b->solvers.assign(solvers, solvers + n);
-    for (lq_solver *s : b->solvers)
-        if (!s) { delete b; return LQ_EINVAL; }
-    lq_solver *s0 = b->solvers[0];
-    b->device = s0->device; b->fp32 = s0->fp32; b->three = s0->three;
-    for (lq_solver *s : b->solvers)
-        if (s->device != b->device || s->fp32 != b->fp32 || s->three != b->three) {
-            delete b;
-            return LQ_EINVAL;   // one device, one precision, one distortion form per batch
-        }
-    cudaSetDevice(b->device);
+    b->device = device; b->fp32 = fp32; b->three = three;
+    cudaSetDevice(device);
     // the batch's own stream: its destruction never touches a solver
     if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
         delete b;
         return LQ_ECUDA;
     }
     cudaDeviceProp prop;
-    if (cudaGetDeviceProperties(&prop, b->device) == cudaSuccess) b->nsm = prop.multiProcessorCount;
-    auto bad = [&](cudaError_t e) {
+    if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) b->nsm = prop.multiProcessorCount;
+    cudaError_t e = cudaSuccess;
+    for (int ty : {4, 8})
+        if (e == cudaSuccess) e = prepare_fire_batch(fp32, three, ty);
+    if (e == cudaSuccess) e = cudaMalloc(&b->running, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->running_host, sizeof(unsigned int));
+    if (e != cudaSuccess) {
         lq_batch_destroy(b);
         return e == cudaErrorMemoryAllocation ? LQ_ENOMEM : LQ_ECUDA;
-    };
-    cudaError_t e;
-    for (int ty : {4, 8})
-        if ((e = prepare_fire_batch(b->fp32, b->three, ty)) != cudaSuccess) return bad(e);
-    size_t ab = step_args_bytes(b->fp32);
-    if ((e = cudaMalloc(&b->args, ab * n)) != cudaSuccess) return bad(e);
-    if ((e = cudaMalloc(&b->shadow_args, ab * n)) != cudaSuccess) return bad(e);
-    if ((e = cudaMalloc(&b->shadow, sizeof(FireDev) * n)) != cudaSuccess) return bad(e);
-    if ((e = cudaMalloc(&b->states, sizeof(FireDev *) * n)) != cudaSuccess) return bad(e);
-    if ((e = cudaMalloc(&b->running, sizeof(unsigned int))) != cudaSuccess) return bad(e);
-    if ((e = cudaMallocHost(&b->running_host, sizeof(unsigned int))) != cudaSuccess) return bad(e);
-    std::vector<FireDev *> st(n);
+    }
+    int tx, ty;
+    step_tile(fp32, three, &tx, &ty);
+    b->ty = ty;          // default tiling: the solvers' own (z chunk 0 = each lattice's)
+    b->zchunk = 0;
+    *out = b;
+    return LQ_OK;
+}
+
+// replace the lattices of the batch (device tables grow as needed)
+lq_status batch_set_members(lq_batch *b, lq_solver *const *solvers, int n) {
+    for (int l = 0; l < n; ++l)
+        if (!solvers[l] || solvers[l]->device != b->device || solvers[l]->fp32 != b->fp32 ||
+            solvers[l]->three != b->three)
+            return bfail(b, LQ_EINVAL, "one device, one precision, one distortion form per batch");
+    cudaSetDevice(b->device);
+    drop_graph(b);
+    b->tables_ok = false;
+    b->solvers.assign(solvers, solvers + n);
+    b->sites = 0;
+    if (n > b->cap) {
+        cudaFree(b->args); cudaFree(b->shadow_args); cudaFree(b->shadow); cudaFree(b->states);
+        b->args = b->shadow_args = nullptr; b->shadow = nullptr; b->states = nullptr;
+        b->cap = 0;
+        size_t ab = step_args_bytes(b->fp32);
+        int cap = std::max(n, 8);
+        BK(cudaMalloc(&b->args, ab * cap));
+        BK(cudaMalloc(&b->shadow_args, ab * cap));
+        BK(cudaMalloc(&b->shadow, sizeof(FireDev) * cap));
+        BK(cudaMalloc(&b->states, sizeof(FireDev *) * cap));
+        b->cap = cap;
+    }
+    std::vector<FireDev *> st(std::max(n, 1));
     for (int l = 0; l < n; ++l) {
+        lq_status r = build_geometry(b->solvers[l]);
+        if (r != LQ_OK) return bfail(b, r, b->solvers[l]->err.c_str());
         st[l] = b->solvers[l]->st;
         b->sites += b->solvers[l]->L.N;
     }
-    if ((e = cudaMemcpy(b->states, st.data(), sizeof(FireDev *) * n, cudaMemcpyHostToDevice)) != cudaSuccess)
-        return bad(e);
-    for (lq_solver *s : b->solvers) {
-        if (build_geometry(s) != LQ_OK) { lq_batch_destroy(b); return LQ_ECUDA; }
+    if (n > 0) BK(cudaMemcpyAsync(b->states, st.data(), sizeof(FireDev *) * n, cudaMemcpyHostToDevice, b->stream));
+    int ty = b->ty, zc = b->zchunk;
+    b->ty = 0;
+    return set_tiling(b, ty, zc);
+}
+
+int batch_members(const lq_batch *b) { return b ? (int)b->solvers.size() : 0; }
+
+// k batched FIRE iterations (direct launches), then the number of lattices
+// still running
+lq_status batch_round(lq_batch *b, int k, unsigned int *running) {
+    cudaSetDevice(b->device);
+    if (b->solvers.empty()) { *running = 0; return LQ_OK; }
+    // stale tables could name lattices that are gone: never launch on them
+    if (!b->tables_ok) return bfail(b, LQ_EINVAL, "batch tables are not built");
+    int grid = persistent_grid(b, b->ty);
+    for (int t = 0; t < k; ++t)
+        BK(launch_fire_batch(b->fp32, b->three, b->ty, b->args, b->items, b->nitems, grid, b->stream));
+    BK(batch_running(b->states, (int)b->solvers.size(), b->running, b->stream));
+    BK(cudaMemcpyAsync(b->running_host, b->running, sizeof(unsigned int), cudaMemcpyDeviceToHost, b->stream));
+    BK(cudaStreamSynchronize(b->stream));
+    *running = *b->running_host;
+    return LQ_OK;
+}
+
+}  // namespace detail
+}  // namespace lq
+
+extern "C" {
+
+lq_status lq_batch_create(lq_solver *const *solvers, int n, lq_batch **out) {
+    if (!solvers || n <= 0 || !out) return LQ_EINVAL;
+    *out = nullptr;
+    for (int l = 0; l < n; ++l)
+        if (!solvers[l]) return LQ_EINVAL;
+    lq_batch *b = nullptr;
+    lq_status r = batch_new(solvers[0]->device, solvers[0]->fp32, solvers[0]->three, &b);
+    if (r != LQ_OK) return r;
+    r = batch_set_members(b, solvers, n);
+    if (r != LQ_OK) {
+        lq_batch_destroy(b);
+        return r;
     }
-    // default tiling: the solvers' own (bit-identical to running them alone)
-    int tx, ty;
-    step_tile(b->fp32, b->three, &tx, &ty);
-    int zc = effective_zchunk(b->solvers[0]);
-    lq_status r = set_tiling(b, ty, zc);
-    if (r != LQ_OK) { lq_batch_destroy(b); return r; }
     *out = b;
     return LQ_OK;
 }
@@ -265,7 +327,7 @@ void lq_batch_destroy(lq_batch *b) {
 const char *lq_batch_last_error(const lq_batch *b) { return b ? b->err.c_str() : "null batch"; }
 
 lq_status lq_batch_set_tiling(lq_batch *b, int tile_y, int zchunk) {
-    if (!b || (tile_y != 4 && tile_y != 8) || zchunk <= 0) return LQ_EINVAL;
+    if (!b || (tile_y != 4 && tile_y != 8) || zchunk < 0) return LQ_EINVAL;
     cudaSetDevice(b->device);
     return set_tiling(b, tile_y, zchunk);
 }
@@ -291,6 +353,7 @@ lq_status lq_batch_autotune(lq_batch *b, const lq_fire_params *p, int launches, 
     int n = (int)b->solvers.size();
     double best = 1e300;
     int bty = b->ty, bzc = b->zchunk;
+    if (b->solvers.empty()) return LQ_OK;
     for (int ty : {4, 8}) {
         for (int zc : {8, 16, 32, 64, 128}) {
             if (zc > nz_max && zc != 8) continue;
@@ -323,7 +386,7 @@ lq_status lq_batch_autotune(lq_batch *b, const lq_fire_params *p, int launches, 
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->ty = 0;   // force the rebuild of the real tables
+    b->tables_ok = false;   // force the rebuild of the real tables
     drop_graph(b);
     lq_status r2 = set_tiling(b, bty, bzc);
     if (r != LQ_OK) return r;
@@ -337,6 +400,7 @@ lq_status lq_batch_step(lq_batch *b, const lq_fire_params *p, int64_t n, lq_resu
     auto t0 = std::chrono::steady_clock::now();
     lq_status r = prepare_run(b, p, false);
     if (r != LQ_OK) return r;
+    if (!b->tables_ok) return bfail(b, LQ_EINVAL, "batch tables are not built");
     r = ensure_graph(b);
     if (r != LQ_OK) return r;
     int64_t full = n / b->graph_k, rest = n % b->graph_k;
@@ -354,6 +418,7 @@ lq_status lq_batch_minimize(lq_batch *b, const lq_fire_params *p, lq_result *out
     auto t0 = std::chrono::steady_clock::now();
     lq_status r = prepare_run(b, p, true);
     if (r != LQ_OK) return r;
+    if (!b->tables_ok) return bfail(b, LQ_EINVAL, "batch tables are not built");
     r = ensure_graph(b);
     if (r != LQ_OK) return r;
     bool timed_out = false;

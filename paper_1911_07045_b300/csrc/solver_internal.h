@@ -74,5 +74,12 @@ void fill_result(lq_solver *s, lq_result *out, double seconds);
 lq_status fire_reset(lq_solver *s, const lq_fire_params *p);
 lq_status update_params(lq_solver *s, const lq_fire_params *p);
 
+// batches (batch.cu): an empty batch for one device / precision / form, its
+// lattices replaced in place, and k persistent-kernel iterations
+lq_status batch_new(int device, int fp32, int three, lq_batch **out);
+lq_status batch_set_members(lq_batch *b, lq_solver *const *solvers, int n);
+lq_status batch_round(lq_batch *b, int k, unsigned int *running);
+int batch_members(const lq_batch *b);
+
 }  // namespace detail
 }  // namespace lq

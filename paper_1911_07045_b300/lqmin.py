@@ -35,7 +35,8 @@ EXPORTS = [
     "lq_fire_result", "lq_get_state", "lq_set_state", "lq_set_zchunk", "lq_device_bytes",
     "lq_energy_noalloc", "lq_batch_create", "lq_batch_destroy", "lq_batch_last_error",
     "lq_batch_set_tiling", "lq_batch_get_tiling", "lq_batch_autotune", "lq_batch_step",
-    "lq_batch_minimize",
+    "lq_batch_minimize", "lq_server_create", "lq_server_destroy", "lq_server_submit",
+    "lq_server_poll", "lq_server_wait", "lq_server_stats_get",
 ]
 
 
@@ -72,6 +73,26 @@ class Result(C.Structure):
                 ("norm_force", C.c_double), ("norm_velocity", C.c_double), ("power", C.c_double),
                 ("dt", C.c_double), ("alpha", C.c_double), ("npos", C.c_int64),
                 ("energy", C.c_double), ("fire_status", C.c_int), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Object(C.Structure):
+    _fields_ = [("type", C.c_int), ("axis", C.c_int), ("plane", C.c_int), ("c", C.c_double * 3),
+                ("R", C.c_double), ("anch", Anchoring), ("n", C.c_int64),
+                ("xyz", C.c_void_p), ("per_site", C.c_void_p)]
+
+
+class Request(C.Structure):
+    _fields_ = [("lattice", Lattice), ("material", Material), ("n_objects", C.c_int),
+                ("objects", C.c_void_p), ("q0", C.c_void_p), ("seed", C.c_uint64), ("S", C.c_double),
+                ("params", FireParams), ("want_order_field", C.c_int)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("queued", C.c_int64), ("active", C.c_int64), ("completed", C.c_int64),
+                ("bytes_in_use", C.c_size_t), ("budget", C.c_size_t), ("site_updates", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -128,6 +149,12 @@ def load(path: str = LIB_PATH):
         "lq_batch_autotune": (C.c_int, [p, C.POINTER(FireParams), C.c_int, C.POINTER(d)]),
         "lq_batch_step": (C.c_int, [p, C.POINTER(FireParams), i64, p]),
         "lq_batch_minimize": (C.c_int, [p, C.POINTER(FireParams), p]),
+        "lq_server_create": (C.c_int, [C.c_size_t, C.c_int, C.c_int, C.POINTER(p)]),
+        "lq_server_destroy": (None, [p]),
+        "lq_server_submit": (C.c_int, [p, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+        "lq_server_poll": (C.c_int, [p, C.c_uint64, C.POINTER(Result), p]),
+        "lq_server_wait": (C.c_int, [p, C.c_uint64, d, C.POINTER(Result), p]),
+        "lq_server_stats_get": (C.c_int, [p, C.POINTER(ServerStats)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -373,6 +400,110 @@ class Batch:
         st = self._ck(self.lib.lq_batch_minimize(self.h, C.byref(params), C.cast(out, C.c_void_p)),
                       ok=(LQ_OK, LQ_ENOTCONVERGED, LQ_ETIMEOUT, LQ_EDIVERGED))
         return st, list(out)
+
+
+OBJ_TYPES = {"wall": 0, "sphere": 1, "sites": 2, "anchored": 3}
+
+
+class Server:
+    """Continuous-batching server (see lq_server_create) on the current device."""
+
+    def __init__(self, hbm_budget_bytes, precision=LQ_FP32_BULK_FP64_RED, max_active=64):
+        self.lib = load()
+        h = C.c_void_p()
+        st = self.lib.lq_server_create(int(hbm_budget_bytes), int(precision), int(max_active),
+                                       C.byref(h))
+        if st != LQ_OK:
+            raise LqError(st, "lq_server_create")
+        self.h = h
+        self.sizes = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lq_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, cfg, params: FireParams, seed=0, q0=None, want_S=False, S=0.0,
+               A=None, B=None, C_=None, periodic=(1, 1, 1)):
+        """Queue the workload dict ``cfg`` (synth format); returns a ticket."""
+        from . import synth
+        nx, ny, nz = cfg["shape"]
+        L2, L3 = cfg.get("L2", 0.0), cfg.get("L3", 0.0)
+        mat = Material(synth.A_5CB if A is None else A, synth.B_5CB if B is None else B,
+                       synth.C_5CB if C_ is None else C_, cfg["L1"], L2, L3, 0.0, 0.0,
+                       1 if (L2 == 0.0 and L3 == 0.0) else 3, 0.0)
+        lat = Lattice(nx, ny, nz, 1.0, (C.c_int * 3)(*cfg.get("periodic", periodic)))
+        keep = []
+        objs = (Object * max(1, len(cfg.get("objects", []))))()
+        for o, spec in zip(objs, cfg.get("objects", [])):
+            o.type = OBJ_TYPES[spec["type"]]
+            if "anchor" in spec:
+                o.anch = anchoring(*spec["anchor"])
+            if spec["type"] == "wall":
+                o.axis, o.plane = spec["axis"], spec["plane"]
+            elif spec["type"] == "sphere":
+                o.c = (C.c_double * 3)(*spec["c"])
+                o.R = spec["R"]
+            else:
+                xyz = np.ascontiguousarray(spec["xyz"], dtype=np.int32).reshape(-1, 3)
+                keep.append(xyz)
+                o.n = xyz.shape[0]
+                o.xyz = xyz.ctypes.data
+                if spec["type"] == "anchored":
+                    n = xyz.shape[0]
+                    per = (Anchoring * max(1, n))()
+                    kinds = np.broadcast_to(np.asarray(spec["kinds"]), (n,))
+                    Ws = np.broadcast_to(np.asarray(spec["W"], dtype=float), (n,))
+                    dirs = np.broadcast_to(np.asarray(spec["dirs"], dtype=float), (n, 3))
+                    for t in range(n):
+                        per[t] = anchoring(kinds[t], Ws[t], dirs[t])
+                    keep.append(per)
+                    o.per_site = C.cast(per, C.c_void_p).value
+        rq = Request(lat, mat, len(cfg.get("objects", [])), C.cast(objs, C.c_void_p).value, None,
+                     int(seed), float(S), params, int(bool(want_S)))
+        if q0 is not None:
+            q0 = np.ascontiguousarray(q0, dtype=np.float64)
+            keep.append(q0)
+            rq.q0 = q0.ctypes.data
+        t = C.c_uint64()
+        st = self.lib.lq_server_submit(self.h, C.byref(rq), C.byref(t))
+        if st != LQ_OK:
+            raise LqError(st, "lq_server_submit")
+        self.sizes[t.value] = nx * ny * nz
+        return t.value
+
+    def _out(self, ticket, S):
+        return (np.empty(self.sizes[ticket]) if S else None)
+
+    def poll(self, ticket, S=False):
+        """None while busy, else (status, Result, S field or None)."""
+        r = Result()
+        Sbuf = self._out(ticket, S)
+        st = self.lib.lq_server_poll(self.h, int(ticket), C.byref(r),
+                                     None if Sbuf is None else Sbuf.ctypes.data)
+        if st == LQ_EBUSY:
+            return None
+        return st, r, Sbuf
+
+    def wait(self, ticket, timeout=0.0, S=False):
+        r = Result()
+        Sbuf = self._out(ticket, S)
+        st = self.lib.lq_server_wait(self.h, int(ticket), float(timeout), C.byref(r),
+                                     None if Sbuf is None else Sbuf.ctypes.data)
+        if st == LQ_EBUSY:
+            return None
+        return st, r, Sbuf
+
+    def stats(self):
+        out = ServerStats()
+        self.lib.lq_server_stats_get(self.h, C.byref(out))
+        return out.as_dict()
 
 
 def solver_for(cfg: dict, precision=LQ_FP64, stream=None, A=None, B=None, C_=None,
