@@ -218,6 +218,72 @@ def run_form(precision: str, L: int, steps: int, warmup: int, dist: Dist, sample
     return out
 
 
+def run_batch(steps: int):
+    """64 uneven lattices (edges 32..128, 0-3 colloids, one constant, FP32
+    form) advanced by the persistent batch kernel; the tiling is autotuned."""
+    from paper_1911_07045_b300 import lqmin
+    cfgs = synth.config_batch()
+    solvers = []
+    for c in cfgs:
+        s = lqmin.solver_for(c, precision=lqmin.LQ_FP32_BULK_FP64_RED)
+        s.init_random_uniaxial(c["seed"])
+        solvers.append(s)
+    sites = sum(int(np.prod(c["shape"])) for c in cfgs)
+    batch = lqmin.Batch(solvers)
+    p = lqmin.fire_params(**dict(synth.FIRE_DEFAULTS, max_iter=10 ** 12, force_tol=0.0))
+    (ty, zc), tuned_ms = batch.autotune(p, launches=3)
+    batch.step(p, 3)                                  # warm-up
+    t0 = time.perf_counter(); batch.step(p, steps); t1 = time.perf_counter()
+    batch.step(p, 2 * steps); t2 = time.perf_counter()
+    sec = (t2 - t1) - (t1 - t0)                       # host overhead of a call cancels
+    out = {"workload": f"{len(cfgs)} cubic lattices, edges {{32,48,64,96,128}}, 0-3 colloids "
+                       f"R~U[6,16] (W=5.3), one constant, FP32 form",
+           "sites": sites, "steps": steps, "value": sites * steps / sec, "unit": UNIT,
+           "ms_per_step": sec / steps * 1e3, "tiling": {"tile": f"32x{ty}", "zchunk": zc},
+           "autotune_ms_per_step": tuned_ms, "launches_per_step": 1}
+    batch.close()
+    for s in solvers:
+        s.close()
+    return out
+
+
+def run_serving(count: int, rate: float, budget_gb: float = 120.0):
+    """The seeded request stream of the serving workload (Poisson arrivals,
+    edges 48..192, half patterned substrate + homeotropic top wall, half 1-2
+    colloids, one constant, FP32 form, max|F| < 1e-6), submitted in real
+    time to a continuous-batching server with an HBM budget."""
+    from paper_1911_07045_b300 import lqmin
+    reqs = synth.serving_requests(count=count, rate=rate)
+    p = lqmin.fire_params(**dict(synth.FIRE_DEFAULTS, max_iter=200000, force_tol=1e-6))
+    sv = lqmin.Server(int(budget_gb * (1 << 30)), max_active=64)
+    t0 = time.perf_counter()
+    tickets = []
+    for r in reqs:
+        delay = r["t_arrival"] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(sv.submit(r, p, seed=r["seed"]))
+    lat, its, conv = [], [], 0
+    for t in tickets:
+        got = sv.wait(t, timeout=900.0)
+        if got is None:
+            raise RuntimeError("served request did not finish within 900 s")
+        code, res, _ = got
+        conv += int(code == lqmin.LQ_OK and res.fire_status == lqmin.FIRE_CONVERGED)
+        lat.append(res.seconds)
+        its.append(res.iterations)
+    wall = time.perf_counter() - t0
+    st = sv.stats()
+    sv.close()
+    lat = np.array(lat)
+    return {"workload": f"first {count} requests of the seeded serving stream (seed 5), Poisson "
+                        f"{rate}/s, edges 48..192, FP32 form, tol 1e-6, HBM budget {budget_gb} GB",
+            "requests": count, "converged": conv,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_iterations": float(np.mean(its)),
+            "site_updates_per_s": st["site_updates"] / wall, "wall_s": wall}
+
+
 def cpu_baseline(L_sample=128, steps=6):
     """The oracle as it stands, on the host cores: FIRE iterations on a
     L_sample^3 lattice with the same structure (colloids scaled by L/512,
@@ -280,6 +346,10 @@ def main_ours(args, dist: Dist):
         "gpu_launches": sum(f["launches"] for f in forms.values()),
         "clocks": h["clocks"],
     }
+    if dist.world == 1 and args.batch_steps > 0:
+        line["batched"] = run_batch(args.batch_steps)
+    if dist.world == 1 and args.serving_requests > 0:
+        line["served"] = run_serving(args.serving_requests, args.serving_rate)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if not all(f["ok"] for f in forms.values()):
@@ -328,6 +398,9 @@ def main(argv=None):
     ap.add_argument("--size", type=int, default=512)
     ap.add_argument("--precision", default="fp32,fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=50)
+    ap.add_argument("--serving-requests", type=int, default=24)
+    ap.add_argument("--serving-rate", type=float, default=20.0)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
