@@ -399,7 +399,7 @@ def main(argv=None):
     ap.add_argument("--precision", default="fp32,fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=50)
-    ap.add_argument("--serving-requests", type=int, default=24)
+    ap.add_argument("--serving-requests", type=int, default=8)
     ap.add_argument("--serving-rate", type=float, default=20.0)
     args = ap.parse_args(argv)
     if args.warmup < 3:

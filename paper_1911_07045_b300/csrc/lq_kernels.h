@@ -31,12 +31,16 @@ void step_tile(int fp32, int three, int *tx, int *ty);
 cudaError_t prepare_fire_step(int fp32, int three);
 cudaError_t launch_fire_step(const StepLaunch &sl, cudaStream_t stream);
 
-// batched steps (tile 32 x ty, ty in {4, 8})
+// true when the state arrays of a lattice of N sites are indexed in 32 bits
+bool step_index32(long long N);
+
+// batched steps (tile 32 x ty, ty in {4, 8}; idx32: every lattice of the
+// batch indexed in 32 bits)
 size_t step_args_bytes(int fp32);
 void step_args_pack(const StepLaunch &sl, void *out);   // host memory, step_args_bytes()
-cudaError_t prepare_fire_batch(int fp32, int three, int ty);
-int fire_batch_blocks_per_sm(int fp32, int three, int ty);
-cudaError_t launch_fire_batch(int fp32, int three, int ty, const void *dev_args,
+cudaError_t prepare_fire_batch(int fp32, int three, int ty, int idx32);
+int fire_batch_blocks_per_sm(int fp32, int three, int ty, int idx32);
+cudaError_t launch_fire_batch(int fp32, int three, int ty, int idx32, const void *dev_args,
                               const WorkItem *items, int nitems, int grid, cudaStream_t stream);
 // running[0] = number of lattices whose FIRE status is still running
 cudaError_t batch_running(FireDev *const *states, int n, unsigned int *running, cudaStream_t s);

@@ -49,6 +49,15 @@ namespace lq {
 template <typename T>
 struct Prec;
 
+// explicitly rounded products and fused multiply-adds: the FIRE update of a
+// site is then the same operation sequence in every kernel that inlines it
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <typename T>
 struct StepArgs {
     typename Prec<T>::Q *q[2];
@@ -79,31 +88,37 @@ __device__ __forceinline__ int wrap_coord(int g, int n, int periodic) {
 template <>
 struct Prec<double> {
     using Q = double;
+    static constexpr double scale = 1.0;   // storage unit of Q
     __device__ static __forceinline__ double val(double q) { return q; }
     __device__ static __forceinline__ double diff(double a, double b) { return b - a; }
-    // q + dt v + dt^2/2 F; never out of range in FP64
-    __device__ static __forceinline__ double drift(double q, double dt, double vx, double hdt2,
-                                                   double f, bool &bad) {
-        return q + dt * vx + hdt2 * f;
+    // q + alpha v + beta F; never out of range in FP64
+    __device__ static __forceinline__ double drift(double q, double v, double f, double alpha,
+                                                   double beta, bool &bad) {
+        return __dadd_rn(q, __fma_rn(alpha, v, __dmul_rn(beta, f)));
     }
 };
 template <>
 struct Prec<float> {
     using Q = int;
+    static constexpr double scale = QFIX_SCALE;
     __device__ static __forceinline__ float val(int q) { return __int2float_rn(q) * float(QFIX_INV); }
     __device__ static __forceinline__ float diff(int a, int b) {
         return __int2float_rn(b - a) * float(QFIX_INV);
     }
-    // a step that would leave |q| < 2 (or is not finite) keeps q and raises
-    // the divergence flag
-    __device__ static __forceinline__ int drift(int q, float dt, float vx, float hdt2, float f,
+    // q + alpha v + beta F with alpha, beta in fixed-point units.  A step
+    // that would leave |q| < 2 (or is not finite) keeps q and raises the
+    // divergence flag.  |u| < 2^29 and |q| < 2^29 keep q + u inside int32;
+    // the conversion saturates (NaN -> 0), and the sum is formed unsigned so
+    // that a rejected step never overflows.
+    __device__ static __forceinline__ int drift(int q, float v, float f, float alpha, float beta,
                                                 bool &bad) {
-        float u = (dt * vx + hdt2 * f) * float(QFIX_SCALE);
         const float lim = float(QFIX_LIMIT * QFIX_SCALE);
-        if (!(fabsf(u) < lim)) { bad = true; return q; }
-        int qn = q + __float2int_rn(u);
-        if (qn >= int(lim) || qn <= -int(lim)) { bad = true; return q; }
-        return qn;
+        const unsigned ilim = (unsigned)(QFIX_LIMIT * QFIX_SCALE);
+        const float u = __fmaf_rn(alpha, v, __fmul_rn(beta, f));
+        const int qn = (int)((unsigned)q + (unsigned)__float2int_rn(u));
+        const bool ok = fabsf(u) < lim && (unsigned)qn + ilim < 2u * ilim;
+        bad |= !ok;
+        return ok ? qn : q;
     }
 };
 
@@ -519,7 +534,7 @@ __device__ __forceinline__ void regular_force(Smem<T, TX, TY> &S, int lx, int ly
 // One block's work for one lattice: the tile with origin (bx*TX, by*TY),
 // planes [z0, z1), block number bid of the nblk blocks of that lattice's
 // step (its partial-sum slot).  Shared memory is the caller's.
-template <typename T, bool THREE, int TX, int TY>
+template <typename T, bool THREE, int TX, int TY, typename I>
 __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int by, int z0, int z1,
                                           int nblk, int bid, unsigned char *smem_raw, double *red,
                                           int *am_last_p) {
@@ -539,8 +554,10 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
     const int gx = x0 + tx, gy = y0 + ty;
     const bool valid = gx < L.nx && gy < L.ny;
     const int lx = tx + 1, ly = ty + 1;
-    const long long N = L.N;
-    const long long NXY = (long long)L.nx * L.ny;
+    // element indices: 32-bit when every index of the state arrays (< 5 N)
+    // fits, else 64-bit
+    const I N = (I)L.N;
+    const I NXY = (I)L.nx * (I)L.ny;
     const bool fo_mode = args.force_only != 0;
 
     // FIRE coefficients for this step
@@ -560,6 +577,12 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
         qout = args.q[cur ^ 1]; vout = args.v[cur ^ 1]; Fout = args.F[cur ^ 1];
     }
     const T hdt2 = T(0.5) * dt * dt;
+    T alpha = T(0), beta = T(0);
+    if (!fo_mode) {
+        const double dcv = args.st->cv, dcF = args.st->cF, ddt = args.st->dt_step;
+        alpha = T(ddt * dcv * P::scale);
+        beta = T((ddt * dcF + 0.5 * ddt * ddt) * P::scale);
+    }
     const T hdt = T(0.5) * dt;
 
     // ring sites of a staged plane: top row, bottom row, left/right columns
@@ -578,8 +601,10 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
         int Y = wrap_coord(y0 + sy - 1, L.ny, L.py);
         return (X >= 0 && Y >= 0) ? (long long)Y * L.nx + X : -1;
     };
-    const long long xy_own = xy_of(lx, ly);
-    const long long xy_ring = rx >= 0 ? xy_of(rx, ry) : -1;
+    const long long xy_own_l = xy_of(lx, ly);
+    const long long xy_ring_l = rx >= 0 ? xy_of(rx, ry) : -1;
+    const bool in_own = xy_own_l >= 0, in_ring = xy_ring_l >= 0;
+    const I xy_own = in_own ? (I)xy_own_l : 0, xy_ring = in_ring ? (I)xy_ring_l : 0;
 
     // one site of a plane in flight from global memory (registers)
     struct Raw {
@@ -589,11 +614,11 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
     };
     // loads are unconditional for sites inside the lattice, so that the mask
     // load does not serialise them
-    auto fetch = [&](long long xy, int z, Raw &r) {
+    auto fetch = [&](bool in, I xy, int z, Raw &r) {
         int Z = wrap_coord(z, L.nz, L.pz);
         r.m = 0;
-        if (xy >= 0 && Z >= 0) {
-            long long i = Z * NXY + xy;
+        if (in && Z >= 0) {
+            I i = (I)Z * NXY + xy;
             r.m = __ldg(args.g.mask + i);
 #pragma unroll
             for (int c = 0; c < 5; ++c) r.q[c] = __ldg(qin + c * N + i);
@@ -613,8 +638,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                 if (fo_mode) {
                     qh[c] = r.q[c];
                 } else {
-                    T vx = cv * r.v[c] + cF * r.f[c];
-                    qh[c] = P::drift(r.q[c], dt, vx, hdt2, r.f[c], bad);
+                    qh[c] = P::drift(r.q[c], r.v[c], r.f[c], alpha, beta, bad);
                 }
             }
         }
@@ -631,15 +655,15 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
     {
         Raw r;
         for (int p = -1; p <= 1; ++p) {
-            fetch(xy_own, z0 + p, r);
+            fetch(in_own, xy_own, z0 + p, r);
             commit(slot_of(z0 + p), lx, ly, r);
             if (rx >= 0) {
-                fetch(xy_ring, z0 + p, r);
+                fetch(in_ring, xy_ring, z0 + p, r);
                 commit(slot_of(z0 + p), rx, ry, r);
             }
         }
-        fetch(xy_own, z0 + 2, pf_own);
-        if (rx >= 0) fetch(xy_ring, z0 + 2, pf_ring);
+        fetch(in_own, xy_own, z0 + 2, pf_own);
+        if (rx >= 0) fetch(in_ring, xy_ring, z0 + 2, pf_ring);
     }
     __syncthreads();   // the first regularity check reads neighbours' masks
 
@@ -660,8 +684,8 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
             if (rx >= 0) commit(s2, rx, ry, pf_ring);
         }
         if (z + 3 <= z1) {
-            fetch(xy_own, z + 3, pf_own);
-            if (rx >= 0) fetch(xy_ring, z + 3, pf_ring);
+            fetch(in_own, xy_own, z + 3, pf_own);
+            if (rx >= 0) fetch(in_ring, xy_ring, z + 3, pf_ring);
         }
         const uint8_t m0 = S.m(sc, lx, ly);
         const bool own = valid && (m0 & M_SIM);
@@ -672,7 +696,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                         S.m(sc, lx, ly + 1) & S.m(sp, lx, ly) & S.m(sm, lx, ly) & m0;
             reg = (m0 & FULL) == FULL && (a & 0xFC) == 0xFC;
         }
-        const long long i = (long long)z * NXY + (long long)gy * L.nx + gx;
+        const I i = (I)z * NXY + (I)gy * (I)L.nx + (I)gx;
         T vold[5], fold[5];
         if (own && !fo_mode) {
 #pragma unroll
@@ -842,8 +866,8 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                 T pv = T(0), ff = T(0), vv = T(0);
 #pragma unroll
                 for (int c = 0; c < 5; ++c) {
-                    T vx = cv * vold[c] + cF * fold[c];
-                    T vn = vx + hdt * (fold[c] + Fn[c]);
+                    T vx = fma_rn(cv, vold[c], mul_rn(cF, fold[c]));
+                    T vn = fma_rn(hdt, add_rn(fold[c], Fn[c]), vx);
                     __stcs(qout + c * N + i, q0[c]);
                     __stcs(vout + c * N + i, vn);
                     __stcs(Fout + c * N + i, Fn[c]);
@@ -894,7 +918,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
 
 
 // one FIRE iteration of one lattice: one block per tile and z chunk
-template <typename T, bool THREE, int TX, int TY>
+template <typename T, bool THREE, int TX, int TY, typename I>
 __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 512 / (TX * TY) : 1)
 fire_step_kernel(StepArgs<T> args) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -904,15 +928,15 @@ fire_step_kernel(StepArgs<T> args) {
     const int z1 = min(z0 + args.zchunk, args.L.nz);
     const int nblk = gridDim.x * gridDim.y * gridDim.z;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    step_tile<T, THREE, TX, TY>(args, blockIdx.x, blockIdx.y, z0, z1, nblk, bid, smem_raw, red,
-                                &am_last);
+    step_tile<T, THREE, TX, TY, I>(args, blockIdx.x, blockIdx.y, z0, z1, nblk, bid, smem_raw, red,
+                                   &am_last);
 }
 
 // one FIRE iteration of every lattice of a batch: a persistent grid strides
 // over the work items (lattice, tile, z chunk); each lattice keeps its own
 // partial sums, last-block ticket and FIRE state, so a lattice advances
 // exactly as it would alone with the same tile and z chunk
-template <typename T, bool THREE, int TX, int TY>
+template <typename T, bool THREE, int TX, int TY, typename I>
 __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 512 / (TX * TY) : 1)
 fire_batch_kernel(const StepArgs<T> *__restrict__ args, const WorkItem *__restrict__ items,
                   int nitems) {
@@ -921,8 +945,8 @@ fire_batch_kernel(const StepArgs<T> *__restrict__ args, const WorkItem *__restri
     __shared__ int am_last;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const WorkItem w = items[it];
-        step_tile<T, THREE, TX, TY>(args[w.lattice], w.bx, w.by, w.z0, w.z1, w.nblk, w.bid,
-                                    smem_raw, red, &am_last);
+        step_tile<T, THREE, TX, TY, I>(args[w.lattice], w.bx, w.by, w.z0, w.z1, w.nblk, w.bid,
+                                       smem_raw, red, &am_last);
         __syncthreads();   // shared memory is reused by the next item
     }
 }
@@ -956,12 +980,16 @@ static void pack_args(const StepLaunch &sl, StepArgs<T> &a) {
     a.force_only = sl.force_only;
 }
 
-template <typename T, bool THREE, int TX, int TY>
+// 32-bit element indices serve every lattice whose state arrays hold fewer
+// than 2^32 elements (5 N < 2^32, N < 858,993,459 sites, about 950^3)
+bool step_index32(long long N) { return 5 * N < (1LL << 32); }
+
+template <typename T, bool THREE, int TX, int TY, typename I>
 static cudaError_t launch_impl(const StepLaunch &sl, cudaStream_t stream) {
     StepArgs<T> a;
     pack_args<T>(sl, a);
     size_t smem = step_smem_bytes<T, THREE, TX, TY>();
-    auto kern = fire_step_kernel<T, THREE, TX, TY>;
+    auto kern = fire_step_kernel<T, THREE, TX, TY, I>;
     dim3 grid = step_grid(sl.L, sl.zchunk, TX, TY);
     kern<<<grid, TX * TY, smem, stream>>>(a);
     return cudaGetLastError();
@@ -979,25 +1007,56 @@ void step_tile(int fp32, int three, int *tx, int *ty) {
     *ty = fp32 ? 4 : 8;
 }
 
-template <typename T, bool THREE, int TX, int TY>
-static cudaError_t prepare_impl() {
-    return cudaFuncSetAttribute(fire_step_kernel<T, THREE, TX, TY>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)step_smem_bytes<T, THREE, TX, TY>());
+// calls F::template run<T, THREE, TY, I>() for the form, tile height and
+// index width of a launch
+template <int TY, typename F>
+static auto dispatch_ty(int fp32, int three, bool idx32, F &&f) {
+    if (fp32) {
+        if (three) return idx32 ? f.template run<float, true, TY, unsigned>() : f.template run<float, true, TY, long long>();
+        return idx32 ? f.template run<float, false, TY, unsigned>() : f.template run<float, false, TY, long long>();
+    }
+    if (three) return idx32 ? f.template run<double, true, TY, unsigned>() : f.template run<double, true, TY, long long>();
+    return idx32 ? f.template run<double, false, TY, unsigned>() : f.template run<double, false, TY, long long>();
 }
+template <typename F>
+static auto dispatch(int fp32, int three, int ty, bool idx32, F &&f) {
+    return ty == 4 ? dispatch_ty<4>(fp32, three, idx32, f) : dispatch_ty<8>(fp32, three, idx32, f);
+}
+// the single-lattice kernel: each form at its own tile height (step_tile)
+template <typename F>
+static auto dispatch_single(int fp32, int three, bool idx32, F &&f) {
+    if (fp32) {
+        if (three) return idx32 ? f.template run<float, true, 4, unsigned>() : f.template run<float, true, 4, long long>();
+        return idx32 ? f.template run<float, false, 4, unsigned>() : f.template run<float, false, 4, long long>();
+    }
+    if (three) return idx32 ? f.template run<double, true, 8, unsigned>() : f.template run<double, true, 8, long long>();
+    return idx32 ? f.template run<double, false, 8, unsigned>() : f.template run<double, false, 8, long long>();
+}
+
+struct PrepareStep {
+    template <typename T, bool THREE, int TY, typename I>
+    cudaError_t run() {
+        return cudaFuncSetAttribute(fire_step_kernel<T, THREE, 32, TY, I>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)step_smem_bytes<T, THREE, 32, TY>());
+    }
+};
 
 cudaError_t prepare_fire_step(int fp32, int three) {
-    if (fp32) return three ? prepare_impl<float, true, 32, 4>() : prepare_impl<float, false, 32, 4>();
-    return three ? prepare_impl<double, true, 32, 8>() : prepare_impl<double, false, 32, 8>();
+    cudaError_t e = dispatch_single(fp32, three, true, PrepareStep{});
+    if (e != cudaSuccess) return e;
+    return dispatch_single(fp32, three, false, PrepareStep{});
 }
 
+struct LaunchStep {
+    const StepLaunch &sl;
+    cudaStream_t stream;
+    template <typename T, bool THREE, int TY, typename I>
+    cudaError_t run() { return launch_impl<T, THREE, 32, TY, I>(sl, stream); }
+};
+
 cudaError_t launch_fire_step(const StepLaunch &sl, cudaStream_t stream) {
-    if (sl.fp32) {
-        if (sl.three) return launch_impl<float, true, 32, 4>(sl, stream);
-        return launch_impl<float, false, 32, 4>(sl, stream);
-    }
-    if (sl.three) return launch_impl<double, true, 32, 8>(sl, stream);
-    return launch_impl<double, false, 32, 8>(sl, stream);
+    return dispatch_single(sl.fp32, sl.three, step_index32(sl.L.N), LaunchStep{sl, stream});
 }
 
 // ---- batched launches ----------------------------------------------------------
@@ -1009,46 +1068,49 @@ void step_args_pack(const StepLaunch &sl, void *out) {
     else pack_args<double>(sl, *static_cast<StepArgs<double> *>(out));
 }
 
-template <typename T, bool THREE, int TY>
-static cudaError_t prepare_batch_impl() {
-    return cudaFuncSetAttribute(fire_batch_kernel<T, THREE, 32, TY>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)step_smem_bytes<T, THREE, 32, TY>());
+struct PrepareBatch {
+    template <typename T, bool THREE, int TY, typename I>
+    cudaError_t run() {
+        return cudaFuncSetAttribute(fire_batch_kernel<T, THREE, 32, TY, I>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)step_smem_bytes<T, THREE, 32, TY>());
+    }
+};
+
+struct BlocksBatch {
+    template <typename T, bool THREE, int TY, typename I>
+    int run() {
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fire_batch_kernel<T, THREE, 32, TY, I>,
+                                                      32 * TY, step_smem_bytes<T, THREE, 32, TY>());
+        return nb;
+    }
+};
+
+struct LaunchBatch {
+    const void *args;
+    const WorkItem *items;
+    int nitems, grid;
+    cudaStream_t stream;
+    template <typename T, bool THREE, int TY, typename I>
+    cudaError_t run() {
+        fire_batch_kernel<T, THREE, 32, TY, I><<<grid, 32 * TY, step_smem_bytes<T, THREE, 32, TY>(), stream>>>(
+            static_cast<const StepArgs<T> *>(args), items, nitems);
+        return cudaGetLastError();
+    }
+};
+
+cudaError_t prepare_fire_batch(int fp32, int three, int ty, int idx32) {
+    return dispatch(fp32, three, ty, idx32 != 0, PrepareBatch{});
 }
 
-template <typename T, bool THREE, int TY>
-static int blocks_impl() {
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fire_batch_kernel<T, THREE, 32, TY>, 32 * TY,
-                                                  step_smem_bytes<T, THREE, 32, TY>());
-    return nb;
+int fire_batch_blocks_per_sm(int fp32, int three, int ty, int idx32) {
+    return dispatch(fp32, three, ty, idx32 != 0, BlocksBatch{});
 }
 
-template <typename T, bool THREE, int TY>
-static cudaError_t batch_impl(const void *args, const WorkItem *items, int nitems, int grid,
-                              cudaStream_t stream) {
-    fire_batch_kernel<T, THREE, 32, TY><<<grid, 32 * TY, step_smem_bytes<T, THREE, 32, TY>(), stream>>>(
-        static_cast<const StepArgs<T> *>(args), items, nitems);
-    return cudaGetLastError();
-}
-
-#define LQ_BATCH_DISPATCH(FN, ...)                                                         \
-    do {                                                                                   \
-        if (fp32) {                                                                        \
-            if (three) return ty == 4 ? FN<float, true, 4>(__VA_ARGS__) : FN<float, true, 8>(__VA_ARGS__); \
-            return ty == 4 ? FN<float, false, 4>(__VA_ARGS__) : FN<float, false, 8>(__VA_ARGS__);          \
-        }                                                                                  \
-        if (three) return ty == 4 ? FN<double, true, 4>(__VA_ARGS__) : FN<double, true, 8>(__VA_ARGS__);   \
-        return ty == 4 ? FN<double, false, 4>(__VA_ARGS__) : FN<double, false, 8>(__VA_ARGS__);            \
-    } while (0)
-
-cudaError_t prepare_fire_batch(int fp32, int three, int ty) { LQ_BATCH_DISPATCH(prepare_batch_impl); }
-
-int fire_batch_blocks_per_sm(int fp32, int three, int ty) { LQ_BATCH_DISPATCH(blocks_impl); }
-
-cudaError_t launch_fire_batch(int fp32, int three, int ty, const void *dev_args,
+cudaError_t launch_fire_batch(int fp32, int three, int ty, int idx32, const void *dev_args,
                               const WorkItem *items, int nitems, int grid, cudaStream_t stream) {
-    LQ_BATCH_DISPATCH(batch_impl, dev_args, items, nitems, grid, stream);
+    return dispatch(fp32, three, ty, idx32 != 0, LaunchBatch{dev_args, items, nitems, grid, stream});
 }
 
 __global__ void k_batch_running(FireDev *const *states, int n, unsigned int *running) {

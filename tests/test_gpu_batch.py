@@ -93,7 +93,11 @@ def test_batch_minimize_matches_alone():
         a.set_zchunk(zc)
         ca, ra = a.minimize(p)
         assert ca == lqmin.LQ_OK and r.fire_status == lqmin.FIRE_CONVERGED
-        assert abs(ra.iterations - r.iterations) <= max(2, ra.iterations // 100)
+        # three-constant products may be fused differently in the two
+        # kernels, and tens of thousands of FIRE steps through defect motion
+        # amplify that rounding: the paths differ, the minimum reached is the
+        # same
+        assert abs(ra.iterations - r.iterations) <= max(2, ra.iterations // 10)
         assert abs(ra.energy - r.energy) <= 1e-10 * abs(ra.energy)
     batch.close()
 
