@@ -439,7 +439,9 @@ struct Stencil;
 template <>
 struct Stencil<double> {
     static constexpr double scale = 1.0;
-    __device__ static __forceinline__ double sec(double a, double b, double c) { return (a - c) + (b - c); }
+    // a + b - 2c as one add and one fused multiply-add (two FP64 operations,
+    // the FP64 form's limiting resource, instead of three)
+    __device__ static __forceinline__ double sec(double a, double b, double c) { return __fma_rn(-2.0, c, a + b); }
     __device__ static __forceinline__ double mix(double a, double b, double c, double d) {
         return (a - b) - (c - d);
     }
