@@ -38,6 +38,18 @@ UNIT = "site-updates/s"
 ALG_BYTES = {"fp32": 4 * 5 * 4 + 1, "fp64": 4 * 5 * 8 + 1}
 # bytes the stored-force design moves: q, v, F read and written + mask
 DESIGN_BYTES = {"fp32": 6 * 5 * 4 + 1, "fp64": 6 * 5 * 8 + 1}
+# DRAM bytes per site-update of the step kernel, dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture of the same kernel on the 256^3
+# case of this workload, divided by its 16,777,216 sites (the traffic of a
+# launch grows with the sites it updates); the bench scales it to its lattice
+DRAM_BYTES_PER_SITE = {"fp32": 2.035370e9 / 256 ** 3, "fp64": 4.200095e9 / 256 ** 3}
+# FP64 form: bound by the FP64 pipe (2 FP64 operations per clock per SM).
+# FP64 arithmetic operations per site-update of the regular three-constant
+# site (second and mixed differences, distortion and bulk force, drift,
+# mixing, kick, reductions), counted from the kernel's arithmetic
+FP64_OPS_PER_SITE = 220
+FP64_OPS_PER_CLK_SM = 2
+N_SM = 148
 
 
 def measured_peaks():
@@ -321,11 +333,24 @@ def main_ours(args, dist: Dist):
     # device time per launch (CUDA events around the timed launches)
     rl = {}
     for k, f in forms.items():
-        ach = ALG_BYTES[k] * f["N"] / f["per_launch_s"] / 1e9
-        rl[k] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                 "frac": round(ach / peak, 4), "traffic": None,
-                 "design_bytes_per_site": DESIGN_BYTES[k], "alg_bytes_per_site": ALG_BYTES[k],
-                 "peak_kind": peak_kind}
+        traffic = DRAM_BYTES_PER_SITE[k] * f["N"]
+        if k == "fp32":
+            ach = ALG_BYTES[k] * f["N"] / f["per_launch_s"] / 1e9
+            rl[k] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(ach / peak, 4), "traffic": round(traffic),
+                     "dram_gbs": round(traffic / f["per_launch_s"] / 1e9, 1),
+                     "dram_frac": round(traffic / f["per_launch_s"] / 1e9 / peak, 4),
+                     "design_bytes_per_site": DESIGN_BYTES[k], "alg_bytes_per_site": ALG_BYTES[k],
+                     "peak_kind": peak_kind + " (HBM copy)"}
+        else:
+            # FP64 pipe: derived peak = SMs x ops/clock x maximum SM clock
+            fp64_peak = N_SM * FP64_OPS_PER_CLK_SM * (f["clocks"].get("sm_max_mhz") or 2032.0) * 1e6 / 1e9
+            ach = FP64_OPS_PER_SITE * f["N"] / f["per_launch_s"] / 1e9
+            rl[k] = {"bound": "alu", "achieved": round(ach, 1), "peak": round(fp64_peak, 1),
+                     "unit": "G FP64 op/s", "frac": round(ach / fp64_peak, 4),
+                     "traffic": round(traffic), "ops_per_site": FP64_OPS_PER_SITE,
+                     "hbm_frac": round(traffic / f["per_launch_s"] / 1e9 / peak, 4),
+                     "peak_kind": "derived: 148 SMs x 2 FP64 ops/clock x max SM clock"}
     line = {
         "metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": dist.world,
         "steps": h["launches"], "warmup": args.warmup, "ms_per_step": h["ms_per_step"],
