@@ -122,6 +122,119 @@ struct Prec<float> {
     }
 };
 
+// ---- the FIRE update of a site, five components at a time -------------------
+// FP64: scalar.  FP32 form: components (0,1) and (2,3) as pairs through the
+// packed two-lane FP32 instructions (FFMA2 / FADD2 / FMUL2 of sm_100 and
+// later), component 4 alone; each lane rounds exactly as the scalar
+// instruction would.
+template <typename T>
+struct Site5;
+template <>
+struct Site5<double> {
+    // q + alpha v + beta F; never out of range in FP64
+    __device__ static __forceinline__ void drift(const double *q, const double *v, const double *f,
+                                                 double alpha, double beta, double *out, bool &bad,
+                                                 bool checked) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) out[c] = Prec<double>::drift(q[c], v[c], f[c], alpha, beta, bad);
+    }
+    // v_new = v_mix + dt/2 (F_old + F_new) and the site's P, |F|^2, |v|^2
+    __device__ static __forceinline__ void kick(const double *vold, const double *fold, const double *fn,
+                                                double cv, double cF, double hdt, double *vn, double &pv,
+                                                double &ff, double &vv) {
+        pv = ff = vv = 0.0;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            double vx = fma_rn(cv, vold[c], mul_rn(cF, fold[c]));
+            vn[c] = fma_rn(hdt, add_rn(fold[c], fn[c]), vx);
+            pv = fma_rn(fn[c], vn[c], pv);
+            ff = fma_rn(fn[c], fn[c], ff);
+            vv = fma_rn(vn[c], vn[c], vv);
+        }
+    }
+};
+template <>
+struct Site5<float> {
+    // fixed-point drift; a staged ring site (checked = false) is also the
+    // own site of the block that stores it, which checks its range
+    __device__ static __forceinline__ void drift(const int *q, const float *v, const float *f,
+                                                 float alpha, float beta, int *out, bool &bad,
+                                                 bool checked) {
+        const float2 A = make_float2(alpha, alpha), B = make_float2(beta, beta);
+        float u[5];
+#pragma unroll
+        for (int c = 0; c < 4; c += 2) {
+            float2 w = __ffma2_rn(A, make_float2(v[c], v[c + 1]),
+                                  __fmul2_rn(B, make_float2(f[c], f[c + 1])));
+            u[c] = w.x; u[c + 1] = w.y;
+        }
+        u[4] = __fmaf_rn(alpha, v[4], __fmul_rn(beta, f[4]));
+        const float lim = float(QFIX_LIMIT * QFIX_SCALE);
+        const unsigned ilim = (unsigned)(QFIX_LIMIT * QFIX_SCALE);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            const int qn = (int)((unsigned)q[c] + (unsigned)__float2int_rn(u[c]));
+            if (checked) {
+                const bool ok = fabsf(u[c]) < lim && (unsigned)qn + ilim < 2u * ilim;
+                bad |= !ok;
+                out[c] = ok ? qn : q[c];
+            } else {
+                out[c] = qn;
+            }
+        }
+    }
+    __device__ static __forceinline__ void kick(const float *vold, const float *fold, const float *fn,
+                                                float cv, float cF, float hdt, float *vn, float &pv,
+                                                float &ff, float &vv) {
+        const float2 CV = make_float2(cv, cv), CF = make_float2(cF, cF), H = make_float2(hdt, hdt);
+        float2 p2 = make_float2(0.f, 0.f), f2 = p2, v2 = p2;
+#pragma unroll
+        for (int c = 0; c < 4; c += 2) {
+            const float2 vo = make_float2(vold[c], vold[c + 1]), fo = make_float2(fold[c], fold[c + 1]);
+            const float2 fnew = make_float2(fn[c], fn[c + 1]);
+            const float2 vx = __ffma2_rn(CV, vo, __fmul2_rn(CF, fo));
+            const float2 w = __ffma2_rn(H, __fadd2_rn(fo, fnew), vx);
+            vn[c] = w.x; vn[c + 1] = w.y;
+            p2 = __ffma2_rn(fnew, w, p2);
+            f2 = __ffma2_rn(fnew, fnew, f2);
+            v2 = __ffma2_rn(w, w, v2);
+        }
+        const float vx4 = __fmaf_rn(cv, vold[4], __fmul_rn(cF, fold[4]));
+        vn[4] = __fmaf_rn(hdt, __fadd_rn(fold[4], fn[4]), vx4);
+        pv = __fmaf_rn(fn[4], vn[4], __fadd_rn(p2.x, p2.y));
+        ff = __fmaf_rn(fn[4], fn[4], __fadd_rn(f2.x, f2.y));
+        vv = __fmaf_rn(vn[4], vn[4], __fadd_rn(v2.x, v2.y));
+    }
+};
+
+// five-component sums: FP32 pairs (0,1), (2,3) through FADD2, then 4
+__device__ __forceinline__ void add5(const double *a, const double *b, double *o) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) o[c] = a[c] + b[c];
+}
+__device__ __forceinline__ void add5(const float *a, const float *b, float *o) {
+#pragma unroll
+    for (int c = 0; c < 4; c += 2) {
+        float2 w = __fadd2_rn(make_float2(a[c], a[c + 1]), make_float2(b[c], b[c + 1]));
+        o[c] = w.x; o[c + 1] = w.y;
+    }
+    o[4] = __fadd_rn(a[4], b[4]);
+}
+// FP32 form: Q in its storage unit (fixed point) to float
+__device__ __forceinline__ void q_values(const double *q, double *o) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) o[c] = q[c];
+}
+__device__ __forceinline__ void q_values(const int *q, float *o) {
+    const float2 s = make_float2(float(QFIX_INV), float(QFIX_INV));
+#pragma unroll
+    for (int c = 0; c < 4; c += 2) {
+        float2 w = __fmul2_rn(make_float2(__int2float_rn(q[c]), __int2float_rn(q[c + 1])), s);
+        o[c] = w.x; o[c + 1] = w.y;
+    }
+    o[4] = __fmul_rn(__int2float_rn(q[4]), float(QFIX_INV));
+}
+
 // per-thread accumulation of the FIRE sums: plain FP64 for the FP64 form;
 // compensated float-float (Knuth's two-sum) for the FP32 form, so that the
 // sums keep ~48 bits without FP64 work per site, and are FP64 from then on
@@ -144,6 +257,30 @@ struct Acc<float> {
         lo = __fadd_rn(lo, e);
     }
     __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
+};
+// two sums side by side: the same two-sum per lane, as FADD2 pairs
+template <typename T>
+struct Acc2 {
+    Acc<T> a, b;
+    __device__ __forceinline__ void add(T x, T y) { a.add(x); b.add(y); }
+    __device__ __forceinline__ double get0() const { return a.get(); }
+    __device__ __forceinline__ double get1() const { return b.get(); }
+};
+template <>
+struct Acc2<float> {
+    float2 hi = make_float2(0.f, 0.f), lo = make_float2(0.f, 0.f);
+    // a - b as fma(-1, b, a): exact product, one rounding, as the subtraction
+    __device__ __forceinline__ void add(float x, float y) {
+        const float2 M1 = make_float2(-1.f, -1.f);
+        const float2 X = make_float2(x, y);
+        const float2 t = __fadd2_rn(hi, X);
+        const float2 bp = __ffma2_rn(M1, hi, t);
+        const float2 e = __fadd2_rn(__ffma2_rn(M1, __ffma2_rn(M1, bp, t), hi), __ffma2_rn(M1, bp, X));
+        hi = t;
+        lo = __fadd2_rn(lo, e);
+    }
+    __device__ __forceinline__ double get0() const { return (double)hi.x + (double)lo.x; }
+    __device__ __forceinline__ double get1() const { return (double)hi.y + (double)lo.y; }
 };
 
 template <typename T>
@@ -632,16 +769,14 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
     };
     bool bad = false;   // a drift left the fixed-point range (FP32 form)
     // drift (after the pending FIRE mixing) and store into a plane slot
-    auto commit = [&](int slot, int sx, int sy, const Raw &r) {
+    auto commit = [&](int slot, int sx, int sy, const Raw &r, bool checked) {
         QS qh[5] = {QS(0), QS(0), QS(0), QS(0), QS(0)};
         if (r.m & M_SIM) {
+            if (fo_mode) {
 #pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                if (fo_mode) {
-                    qh[c] = r.q[c];
-                } else {
-                    qh[c] = P::drift(r.q[c], r.v[c], r.f[c], alpha, beta, bad);
-                }
+                for (int c = 0; c < 5; ++c) qh[c] = r.q[c];
+            } else {
+                Site5<T>::drift(r.q, r.v, r.f, alpha, beta, qh, bad, checked);
             }
         }
         S.m(slot, sx, sy) = r.m;
@@ -658,10 +793,10 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
         Raw r;
         for (int p = -1; p <= 1; ++p) {
             fetch(in_own, xy_own, z0 + p, r);
-            commit(slot_of(z0 + p), lx, ly, r);
+            commit(slot_of(z0 + p), lx, ly, r, true);
             if (rx >= 0) {
                 fetch(in_ring, xy_ring, z0 + p, r);
-                commit(slot_of(z0 + p), rx, ry, r);
+                commit(slot_of(z0 + p), rx, ry, r, false);
             }
         }
         fetch(in_own, xy_own, z0 + 2, pf_own);
@@ -674,7 +809,8 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
     const T L1s = L1 * sc_, L23s = L23 * sc_;
     const T L2q = T(0.25) * args.L2 * sc_, L3q = T(0.25) * args.L3 * sc_;
 
-    Acc<T> accP, accF, accV;
+    Acc2<T> accPF;
+    Acc<T> accV;
     T accR = T(0);
     const uint8_t FULL = M_SIM | 0xFC;
 
@@ -682,8 +818,8 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
     for (int z = z0; z < z1; ++z) {
         // pipeline: plane z+2 into its slot, plane z+3 in flight
         if (z + 2 <= z1) {
-            commit(s2, lx, ly, pf_own);
-            if (rx >= 0) commit(s2, rx, ry, pf_ring);
+            commit(s2, lx, ly, pf_own, true);
+            if (rx >= 0) commit(s2, rx, ry, pf_ring, false);
         }
         if (z + 3 <= z1) {
             fetch(in_own, xy_own, z + 3, pf_own);
@@ -847,11 +983,9 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
             QS q0[5];
             T qv[5], fb[5], Fn[5];
             S.load5(sc, lx, ly, q0);
-#pragma unroll
-            for (int c = 0; c < 5; ++c) qv[c] = P::val(q0[c]);
+            q_values(q0, qv);
             bulk_force(qv, args.A, args.B, args.C, fb);
-#pragma unroll
-            for (int c = 0; c < 5; ++c) Fn[c] = Fd[c] + fb[c];
+            add5(Fd, fb, Fn);
             if (m0 & M_ANCH) {
                 const AnchorRec<T> *r = find_record<T>(args.g, L, gx, gy, z);
                 if (r) {
@@ -865,20 +999,15 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
 #pragma unroll
                 for (int c = 0; c < 5; ++c) Fout[c * N + i] = Fn[c];
             } else {
-                T pv = T(0), ff = T(0), vv = T(0);
+                T pv, ff, vv, vn[5];
+                Site5<T>::kick(vold, fold, Fn, cv, cF, hdt, vn, pv, ff, vv);
 #pragma unroll
                 for (int c = 0; c < 5; ++c) {
-                    T vx = fma_rn(cv, vold[c], mul_rn(cF, fold[c]));
-                    T vn = fma_rn(hdt, add_rn(fold[c], Fn[c]), vx);
                     __stcs(qout + c * N + i, q0[c]);
-                    __stcs(vout + c * N + i, vn);
+                    __stcs(vout + c * N + i, vn[c]);
                     __stcs(Fout + c * N + i, Fn[c]);
-                    pv += Fn[c] * vn;
-                    ff += Fn[c] * Fn[c];
-                    vv += vn * vn;
                 }
-                accP.add(pv);
-                accF.add(ff);
+                accPF.add(pv, ff);
                 accV.add(vv);
                 accR = fmax(accR, ff);
             }
@@ -892,7 +1021,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
 
     // block reduction, then the last block reduces the partials in order; a
     // fixed-point range violation poisons the max with +inf (-> diverged)
-    double sP = accP.get(), sF = accF.get(), sV = accV.get();
+    double sP = accPF.get0(), sF = accPF.get1(), sV = accV.get();
     double sR = bad ? (double)INFINITY : (double)accR;
     block_reduce4<NT>(sP, sF, sV, sR, red);
     const int nblocks = nblk;
