@@ -99,18 +99,31 @@ typedef struct {
     double dir[3];  /* preferred director or normal, see above; need not be unit */
 } lq_anchoring;
 
-/* FIRE parameters, Algorithm 1 (after Bitzek et al. 2006).  Velocity Verlet
-   steps of size dt; alpha mixes v toward |v| F/|F|; after more than n_min
-   consecutive steps with P = F.v > 0, dt <- min(dt f_inc, dt_max) and
-   alpha <- alpha f_alpha; when P <= 0, dt <- dt f_dec, alpha <- alpha0,
-   v <- 0.  Converged when max over sites of the five-component force norm
-   is below force_tol.  wall_timeout_s <= 0 disables the wall-clock limit. */
+/* Minimiser parameters.  method LQ_MIN_FIRE (0): FIRE, Algorithm 1 (after
+   Bitzek et al. 2006).  Velocity Verlet steps of size dt; alpha mixes v
+   toward |v| F/|F|; after more than n_min consecutive steps with
+   P = F.v > 0, dt <- min(dt f_inc, dt_max) and alpha <- alpha f_alpha; when
+   P <= 0, dt <- dt f_dec, alpha <- alpha0, v <- 0.
+   The paper's other minimisers (section III.C, which names gradient descent
+   and Nesterov's accelerated gradient; Fig. 2 compares FIRE with gradient
+   descent) use dt0 as the step eta and ignore the FIRE-only fields:
+   LQ_MIN_GD (1): x <- x + eta F(x);
+   LQ_MIN_NESTEROV (2): y = x_k + mu (x_k - x_{k-1}), x_{k+1} = y + eta F(y),
+   momentum mu in [0, 1); the state (q, force, residual) is that of y, where
+   the force is evaluated.
+   All: converged when max over sites of the five-component force norm is
+   below force_tol; wall_timeout_s <= 0 disables the wall-clock limit.  A
+   zero-initialised method and momentum give FIRE. */
+typedef enum { LQ_MIN_FIRE = 0, LQ_MIN_GD = 1, LQ_MIN_NESTEROV = 2 } lq_minimizer;
+
 typedef struct {
     double dt0, dt_max, alpha0, f_alpha, f_inc, f_dec;
     int n_min;
     int64_t max_iter;
     double force_tol;
     double wall_timeout_s;
+    int method;        /* lq_minimizer */
+    double momentum;   /* LQ_MIN_NESTEROV: mu */
 } lq_fire_params;
 
 typedef enum { LQ_FIRE_RUNNING = 0, LQ_FIRE_CONVERGED = 1, LQ_FIRE_MAXITER = 2,

@@ -109,6 +109,11 @@ class _FireState(C.Structure):
 _lib = None
 
 
+class _DescentState(C.Structure):
+    _fields_ = [("iter", C.c_int64), ("initialized", C.c_int), ("status", C.c_int),
+                ("normF", C.c_double), ("rmax", C.c_double)]
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -130,6 +135,9 @@ def lib():
         _lib.orc_fire_run.argtypes = [C.POINTER(_Model), C.POINTER(_Geometry),
                                       C.POINTER(_FireParams), p, p, p,
                                       C.POINTER(_FireState), i64]
+        _lib.orc_descent_run.restype = C.c_int
+        _lib.orc_descent_run.argtypes = [C.POINTER(_Model), C.POINTER(_Geometry), C.c_int, d, d,
+                                         i64, d, p, p, p, p, C.POINTER(_DescentState), i64]
         _lib.orc_eig_sym3.argtypes = [p, p, p]
         _lib.orc_order_field.argtypes = [C.POINTER(_Geometry), p, i64, p]
         _lib.orc_num_threads.restype = C.c_int
@@ -278,6 +286,30 @@ class Oracle:
                            _ptr(q), _ptr(v), _ptr(F), C.byref(st), int(max_steps))
         out = {k: getattr(st, k) for k, _ in _FireState._fields_}
         return q, v, F, out
+
+    def descent(self, x, method, eta, mu=0.0, max_iter=10 ** 9, force_tol=1e-9, max_steps=1,
+                state=None):
+        """Run up to ``max_steps`` iterations of gradient descent (method GD)
+        or Nesterov's accelerated gradient (NESTEROV).  ``state`` is None
+        (start from ``x``) or the dict returned by a previous call.  Returns
+        a dict with x, xprev, y (where F is evaluated), F and the scalars."""
+        st = _DescentState()
+        if state is None:
+            x = self._q(x).copy()
+            xprev, y, F = np.zeros_like(x), np.zeros_like(x), np.zeros_like(x)
+        else:
+            x, xprev, y, F = (state[k].copy() for k in ("x", "xprev", "y", "F"))
+            for k, _ in _DescentState._fields_:
+                setattr(st, k, state[k])
+        lib().orc_descent_run(C.byref(self.model), C.byref(self.geom), int(method), float(eta),
+                              float(mu), int(max_iter), float(force_tol), _ptr(x), _ptr(xprev),
+                              _ptr(y), _ptr(F), C.byref(st), int(max_steps))
+        out = {k: getattr(st, k) for k, _ in _DescentState._fields_}
+        out.update(x=x, xprev=xprev, y=y, F=F)
+        return out
+
+
+GD, NESTEROV = 1, 2
 
 
 def fire_params(dt0=1e-3, dt_max=1e-2, alpha0=0.99, f_alpha=0.99, f_inc=1.1, f_dec=0.5,

@@ -694,6 +694,52 @@ int orc_fire_run(const orc_model *m, const orc_geometry *g, const orc_fire_param
     return st->status;
 }
 
+/* ---- gradient descent and Nesterov's accelerated gradient ---------------- */
+
+static void descent_norms(const orc_model *m, const orc_geometry *g, const double *F,
+                          double *normF, double *rmax) {
+    double P, F2, v2, r2;
+    fire_reduce(g, F, F, m->nz, &P, &F2, &v2, &r2);   /* |F|^2 and max site |F|^2 */
+    *normF = sqrt(F2);
+    *rmax = sqrt(r2);
+}
+
+int orc_descent_run(const orc_model *m, const orc_geometry *g, int method, double eta,
+                    double mu, int64_t max_iter, double force_tol, double *x, double *xprev,
+                    double *y, double *F, orc_descent_state *st, int64_t max_steps) {
+    int64_t N = g->N;
+    if (method != 2) mu = 0.0;
+    if (!st->initialized) {
+        for (int64_t t = 0; t < 5 * N; ++t) { xprev[t] = x[t]; y[t] = x[t]; }
+        orc_force(m, g, y, F);
+        st->iter = 0;
+        st->status = ORC_RUNNING;
+        st->initialized = 1;
+        descent_norms(m, g, F, &st->normF, &st->rmax);
+        if (!isfinite(st->normF)) st->status = ORC_DIVERGED;
+        else if (st->rmax < force_tol) st->status = ORC_CONVERGED;
+    }
+    for (int64_t step = 0; step < max_steps && st->status == ORC_RUNNING; ++step) {
+        for (int64_t i = 0; i < N; ++i) {
+            if (!g->sim[i]) continue;
+            for (int c = 0; c < 5; ++c) {
+                int64_t t = c * N + i;
+                double xn = y[t] + eta * F[t];            /* x_{k+1} = y_k + eta F(y_k) */
+                xprev[t] = x[t];
+                x[t] = xn;
+                y[t] = xn + mu * (xn - xprev[t]);        /* y_{k+1} */
+            }
+        }
+        orc_force(m, g, y, F);
+        st->iter += 1;
+        descent_norms(m, g, F, &st->normF, &st->rmax);
+        if (!isfinite(st->normF)) { st->status = ORC_DIVERGED; break; }
+        if (st->rmax < force_tol) { st->status = ORC_CONVERGED; break; }
+        if (st->iter >= max_iter) { st->status = ORC_MAXITER; break; }
+    }
+    return st->status;
+}
+
 /* ---- readback: largest eigenvalue (cyclic Jacobi, Golub & Van Loan 8.5) -- */
 
 void orc_eig_sym3(const double q5[5], double evals[3], double evecs[9]) {

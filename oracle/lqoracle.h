@@ -110,6 +110,25 @@ int  orc_fire_run(const orc_model *m, const orc_geometry *g,
                   const orc_fire_params *p, double *q, double *v, double *F,
                   orc_fire_state *st, int64_t max_steps);
 
+/* Gradient descent and Nesterov's accelerated gradient, two of the
+   minimisers section III.C names (Fig. 2 compares gradient descent with
+   FIRE), in their textbook forms:
+     method 1 (GD):        x_{k+1} = x_k + eta F(x_k)
+     method 2 (Nesterov):  y_k = x_k + mu (x_k - x_{k-1}),
+                           x_{k+1} = y_k + eta F(y_k)
+   x is the iterate, xprev the previous one (equal to x at the start), y the
+   point where the force is evaluated (GD: y = x) and F = F(y); residual and
+   convergence test on F(y).  iter counts completed iterations after the
+   initial evaluation, as for FIRE. */
+typedef struct {
+    int64_t iter;
+    int initialized, status;
+    double normF, rmax;
+} orc_descent_state;
+int  orc_descent_run(const orc_model *m, const orc_geometry *g, int method, double eta,
+                     double mu, int64_t max_iter, double force_tol, double *x, double *xprev,
+                     double *y, double *F, orc_descent_state *st, int64_t max_steps);
+
 /* eigen-decomposition of one Q by cyclic Jacobi; values descending */
 void orc_eig_sym3(const double q5[5], double evals[3], double evecs[9]);
 /* largest eigenvalue per site (0 at object sites) */

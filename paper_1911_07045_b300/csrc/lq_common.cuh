@@ -56,8 +56,14 @@ struct FireDev {
     double dt, alpha;
     long long npos, iter, kcount;
     int status, cur;          // cur: which ping-pong buffer holds the state
-    // coefficients of the next step: v_mix = cv v + cF F, drift with dt_step
+    // coefficients of the next step: v_mix = cv v + cF F, drift
+    // q + c_alpha v + c_beta F, kick v_mix + c_kick (F_old + F_new); dt_step
+    // is FIRE's dt of that step
     double cv, cF, dt_step;
+    double c_alpha, c_beta, c_kick;
+    // minimiser (lq_minimizer), Nesterov momentum, descent step
+    long long method;
+    double mu, eta;
     // reductions of the last evaluated state
     double P, F2, v2, r2;
     long long nsim;

@@ -237,11 +237,18 @@ lq_status build_geometry(lq_solver *s) {
 }
 
 lq_status check_params(lq_solver *s, const lq_fire_params *p) {
-    if (!p) return fail(s, LQ_EINVAL, "null FIRE parameters");
-    if (!(p->dt0 > 0) || !(p->dt_max >= p->dt0) || !(p->alpha0 >= 0 && p->alpha0 <= 1) ||
-        !(p->f_alpha > 0 && p->f_alpha <= 1) || !(p->f_inc >= 1) || !(p->f_dec > 0 && p->f_dec <= 1) ||
-        p->n_min < 0 || p->max_iter < 0 || !(p->force_tol >= 0))
+    if (!p) return fail(s, LQ_EINVAL, "null minimiser parameters");
+    if (p->method < LQ_MIN_FIRE || p->method > LQ_MIN_NESTEROV)
+        return fail(s, LQ_EINVAL, "unknown minimiser %d", p->method);
+    if (!(p->dt0 > 0) || !std::isfinite(p->dt0) || p->max_iter < 0 || !(p->force_tol >= 0))
+        return fail(s, LQ_EINVAL, "invalid minimiser parameters");
+    if (p->method == LQ_MIN_FIRE &&
+        (!(p->dt_max >= p->dt0) || !(p->alpha0 >= 0 && p->alpha0 <= 1) ||
+         !(p->f_alpha > 0 && p->f_alpha <= 1) || !(p->f_inc >= 1) || !(p->f_dec > 0 && p->f_dec <= 1) ||
+         p->n_min < 0))
         return fail(s, LQ_EINVAL, "invalid FIRE parameters");
+    if (p->method == LQ_MIN_NESTEROV && !(p->momentum >= 0 && p->momentum < 1))
+        return fail(s, LQ_EINVAL, "Nesterov momentum must be in [0, 1)");
     return LQ_OK;
 }
 
@@ -249,6 +256,9 @@ void fill_params(FireDev &f, const lq_fire_params *p) {
     f.dt0 = p->dt0; f.dt_max = p->dt_max; f.alpha0 = p->alpha0; f.f_alpha = p->f_alpha;
     f.f_inc = p->f_inc; f.f_dec = p->f_dec; f.tol = p->force_tol;
     f.n_min = p->n_min; f.max_iter = p->max_iter;
+    f.method = p->method;
+    f.eta = p->dt0;
+    f.mu = p->method == LQ_MIN_NESTEROV ? p->momentum : 0.0;
 }
 
 lq_status sync_state(lq_solver *s) {
@@ -268,7 +278,7 @@ void fill_result(lq_solver *s, lq_result *out, double seconds) {
     out->norm_velocity = std::sqrt(f.v2);
     out->rms_force = s->nsim > 0 ? std::sqrt(f.F2 / (double)s->nsim) : 0.0;
     out->power = f.P;
-    out->dt = f.dt;
+    out->dt = f.method == LQ_MIN_FIRE ? f.dt : f.eta;
     out->alpha = f.alpha;
     out->npos = f.npos;
     out->fire_status = f.status;
@@ -346,8 +356,17 @@ lq_status launch_steps(lq_solver *s, int64_t n) {
 lq_status update_params(lq_solver *s, const lq_fire_params *p) {
     lq_status r = sync_state(s);
     if (r != LQ_OK) return r;
+    // another minimiser restarts from the current Q
+    if (s->st_host->method != p->method) return fire_reset(s, p);
     FireDev f = *s->st_host;
     fill_params(f, p);
+    if (f.method != LQ_MIN_FIRE && f.kcount >= 1) {
+        // a new step or momentum applies from the next step on
+        f.cv = f.mu; f.cF = f.eta; f.dt_step = f.eta;
+        f.c_alpha = f.mu * f.mu;
+        f.c_beta = f.eta * (1.0 + f.mu);
+        f.c_kick = 0.0;
+    }
     if (f.status == FIRE_MAXITER && f.iter < f.max_iter) f.status = FIRE_RUNNING;
     if (f.status == FIRE_CONVERGED && std::sqrt(f.r2) >= f.tol) f.status = FIRE_RUNNING;
     *s->st_host = f;
@@ -774,7 +793,7 @@ struct StateHeader {
     int32_t fp32, fire_ready;
     FireDev fire;
 };
-static const uint64_t STATE_MAGIC = 0x4c514d494e535431ull;  // "LQMINST1"
+static const uint64_t STATE_MAGIC = 0x4c514d494e535432ull;  // "LQMINST2"
 
 lq_status lq_get_state(lq_solver *s, void *buf, size_t *bytes) {
     if (check_solver(s)) return LQ_EINVAL;

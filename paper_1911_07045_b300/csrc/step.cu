@@ -533,7 +533,26 @@ __device__ __forceinline__ void block_reduce4(double &p, double &f, double &w, d
     __syncthreads();
 }
 
-// FIRE scalar machine (Algorithm 1), run by one thread after the reductions
+// coefficients of the next step from (cv, cF, dt_step) for FIRE, fixed for
+// the descent methods: GD drifts x + eta F; Nesterov keeps y = x + mu v and
+// advances it by y' = y + mu^2 v + eta (1 + mu) F(y), v' = mu v + eta F(y)
+__device__ __forceinline__ void set_coefficients(FireDev *st) {
+    if (st->method == 0) {
+        st->c_alpha = st->dt_step * st->cv;
+        st->c_beta = st->dt_step * st->cF + 0.5 * st->dt_step * st->dt_step;
+        st->c_kick = 0.5 * st->dt_step;
+    } else {
+        const double mu = st->method == 2 ? st->mu : 0.0;
+        st->cv = mu; st->cF = st->eta; st->dt_step = st->eta;
+        st->c_alpha = mu * mu;
+        st->c_beta = st->eta * (1.0 + mu);
+        st->c_kick = 0.0;
+    }
+}
+
+// FIRE scalar machine (Algorithm 1), run by one thread after the reductions;
+// the descent methods share its bookkeeping (iterations, convergence,
+// divergence, max_iter) with fixed coefficients
 __device__ void fire_update(FireDev *st, double P, double F2, double v2, double r2) {
     st->P = P; st->F2 = F2; st->v2 = v2; st->r2 = r2;
     st->cur ^= 1;
@@ -545,12 +564,14 @@ __device__ void fire_update(FireDev *st, double P, double F2, double v2, double 
         if (bad) st->status = FIRE_DIVERGED;
         else if (rmax < st->tol) st->status = FIRE_CONVERGED;
         st->dt_step = st->dt;
+        set_coefficients(st);
         return;
     }
     st->iter += 1;
     if (bad) { st->status = FIRE_DIVERGED; return; }
     if (rmax < st->tol) { st->status = FIRE_CONVERGED; return; }
     if (st->iter >= st->max_iter) { st->status = FIRE_MAXITER; return; }
+    if (st->method != 0) { set_coefficients(st); return; }
     double a = 1.0, b = 0.0;
     double nF = sqrt(F2), nv = sqrt(v2);
     if (nF > 0.0) { a = 1.0 - st->alpha; b = st->alpha * nv / nF; }
@@ -567,6 +588,7 @@ __device__ void fire_update(FireDev *st, double P, double F2, double v2, double 
         a = 0.0; b = 0.0;
     }
     st->cv = a; st->cF = b; st->dt_step = st->dt;
+    set_coefficients(st);
 }
 
 // second differences and mixed differences in the storage format: exact
@@ -700,7 +722,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
     const bool fo_mode = args.force_only != 0;
 
     // FIRE coefficients for this step
-    T cv = T(0), cF = T(0), dt = T(0);
+    T cv = T(0), cF = T(0);
     const QS *qin;
     const T *vin = nullptr, *Fin = nullptr;
     QS *qout = nullptr;
@@ -711,18 +733,19 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
     } else {
         if (args.st->status != FIRE_RUNNING) return;
         const int cur = args.st->cur;
-        cv = T(args.st->cv); cF = T(args.st->cF); dt = T(args.st->dt_step);
+        cv = T(args.st->cv); cF = T(args.st->cF);
         qin = args.q[cur]; vin = args.v[cur]; Fin = args.F[cur];
         qout = args.q[cur ^ 1]; vout = args.v[cur ^ 1]; Fout = args.F[cur ^ 1];
     }
-    const T hdt2 = T(0.5) * dt * dt;
-    T alpha = T(0), beta = T(0);
+    // drift q + alpha v + beta F (alpha, beta in the storage unit of Q) and
+    // kick v_mix + hdt (F_old + F_new), as the last block of the previous
+    // step left them
+    T alpha = T(0), beta = T(0), hdt = T(0);
     if (!fo_mode) {
-        const double dcv = args.st->cv, dcF = args.st->cF, ddt = args.st->dt_step;
-        alpha = T(ddt * dcv * P::scale);
-        beta = T((ddt * dcF + 0.5 * ddt * ddt) * P::scale);
+        alpha = T(args.st->c_alpha * P::scale);
+        beta = T(args.st->c_beta * P::scale);
+        hdt = T(args.st->c_kick);
     }
-    const T hdt = T(0.5) * dt;
 
     // ring sites of a staged plane: top row, bottom row, left/right columns
     constexpr int NRING = 2 * SM::SX + 2 * TY;

@@ -25,6 +25,7 @@ STATUS_NAMES = ["LQ_OK", "LQ_EINVAL", "LQ_ENOMEM", "LQ_ECUDA", "LQ_ENOTCONVERGED
 LQ_FP64, LQ_FP32_BULK_FP64_RED = 0, 1
 ND_HOMEOTROPIC, ND_ORIENTED, FG_PLANAR = 0, 1, 2
 FIRE_RUNNING, FIRE_CONVERGED, FIRE_MAXITER, FIRE_DIVERGED = 0, 1, 2, 3
+LQ_MIN_FIRE, LQ_MIN_GD, LQ_MIN_NESTEROV = 0, 1, 2
 
 # every symbol include/lqmin.h declares
 EXPORTS = [
@@ -65,7 +66,7 @@ class FireParams(C.Structure):
     _fields_ = [("dt0", C.c_double), ("dt_max", C.c_double), ("alpha0", C.c_double),
                 ("f_alpha", C.c_double), ("f_inc", C.c_double), ("f_dec", C.c_double),
                 ("n_min", C.c_int), ("max_iter", C.c_int64), ("force_tol", C.c_double),
-                ("wall_timeout_s", C.c_double)]
+                ("wall_timeout_s", C.c_double), ("method", C.c_int), ("momentum", C.c_double)]
 
 
 class Result(C.Structure):
@@ -169,9 +170,19 @@ def _ptr(a: np.ndarray):
 
 
 def fire_params(dt0=1e-3, dt_max=1e-2, alpha0=0.99, f_alpha=0.99, f_inc=1.1, f_dec=0.5, n_min=5,
-                max_iter=10 ** 9, force_tol=1e-9, wall_timeout_s=0.0) -> FireParams:
+                max_iter=10 ** 9, force_tol=1e-9, wall_timeout_s=0.0, method=0,
+                momentum=0.0) -> FireParams:
+    """Minimiser parameters (lq_fire_params): FIRE by default; method
+    LQ_MIN_GD / LQ_MIN_NESTEROV take dt0 as the step and momentum as mu."""
     return FireParams(dt0, dt_max, alpha0, f_alpha, f_inc, f_dec, n_min, max_iter, force_tol,
-                      wall_timeout_s)
+                      wall_timeout_s, int(method), float(momentum))
+
+
+def descent_params(method, step, momentum=0.0, max_iter=10 ** 9, force_tol=1e-9,
+                   wall_timeout_s=0.0) -> FireParams:
+    """Gradient descent (LQ_MIN_GD) or Nesterov (LQ_MIN_NESTEROV) with step eta."""
+    return fire_params(dt0=step, dt_max=step, max_iter=max_iter, force_tol=force_tol,
+                       wall_timeout_s=wall_timeout_s, method=method, momentum=momentum)
 
 
 def anchoring(kind, W, dir=(0.0, 0.0, 1.0)) -> Anchoring:

@@ -536,3 +536,74 @@ def test_fire_reduces_to_velocity_verlet_on_a_harmonic_well(oracle_mod):
         assert st["iter"] == k
         assert abs(qk[1, 0] - want[0]) < 1e-14 and abs(vk[1, 0] - want[1]) < 1e-14
         assert abs(Fk[1, 0] + w2 * qk[1, 0]) < 1e-15
+
+
+# ---- gradient descent and Nesterov's accelerated gradient (section III.C) ----
+
+def test_descent_single_site_reaches_uniaxial_s0(oracle_mod):
+    """Gradient descent and Nesterov from a biaxial single site (no
+    distortion) stop at the uniaxial bulk minimum: eigenvalues (S0, -S0/2,
+    -S0/2) with S0 from the closed form of Eq. (S0def)."""
+    q0 = np.array([[0.30], [0.05], [-0.02], [-0.12], [0.04]])
+    S0 = synth.s0_closed_form(A, B, C)
+    for method, eta, mu in ((oracle_mod.GD, 0.5, 0.0), (oracle_mod.NESTEROV, 0.2, 0.8)):
+        o = oracle_mod.Oracle((1, 1, 1), A, B, C, 2.32, 0.5, 0.3)
+        r = o.descent(q0, method, eta, mu=mu, max_iter=100000, force_tol=1e-12, max_steps=100000)
+        assert r["status"] == oracle_mod.CONVERGED
+        ev, _ = oracle_mod.eig_sym3(r["y"][:, 0])
+        assert np.allclose(ev, [S0, -S0 / 2, -S0 / 2], atol=1e-10)
+
+
+def test_gradient_descent_lowers_the_energy_every_step(oracle_mod):
+    """A small step is a descent direction: the energy of a three-constant
+    lattice with a colloid and a wall falls at every step (a sign error in
+    the update or the force raises it)."""
+    objs = [dict(type="sphere", c=(3.0, 3.0, 2.5), R=1.5, anchor=(0, 5.3, (0, 0, 1))),
+            dict(type="wall", axis=2, plane=0, anchor=(2, 1.0, (0, 0, 1)))]
+    o = oracle_mod.Oracle((7, 6, 6), A, B, C, 2.32, 0.5, 0.3, objects=objs)
+    q = synth.random_uniaxial_q((7, 6, 6), 11)
+    E = o.energy(q)[0]
+    r = None
+    for _ in range(30):
+        r = o.descent(q, oracle_mod.GD, 0.01, max_steps=1, state=r)
+        En = o.energy(r["x"])[0]
+        assert En < E
+        E = En
+    assert r["iter"] == 30 and np.array_equal(r["x"], r["y"])
+
+
+def test_nesterov_on_a_plane_wave_follows_its_recurrence(oracle_mod):
+    """With A = B = C = 0 the energy is quadratic and a Q_xy wave
+    eps cos(2 pi m x / L) is an eigenvector of the force, F = -lam q with
+    lam = 2 L1 (2 - 2 cos(2 pi m / L)) (the symmetric pair Q_xy = Q_yx
+    times the periodic second difference).  Nesterov's amplitudes then obey
+    a_{k+1} = (1 - eta lam) b_k, b_k = a_k + mu (a_k - a_{k-1}), a_{-1} = a_0;
+    the oracle's iterates (x) and evaluation points (y) must follow it."""
+    L, L1, eps, eta, mu = 12, 1.3, 1e-3, 0.05, 0.7
+    o = oracle_mod.Oracle((L, 2, 2), 0.0, 0.0, 0.0, L1)
+    x = np.tile(np.arange(L), 4).astype(float)
+    for m in (1, 3):
+        wave = np.cos(2 * math.pi * m * x / L)
+        q = np.zeros((5, o.N))
+        q[1] = eps * wave
+        lam = 2 * L1 * (2 - 2 * math.cos(2 * math.pi * m / L))
+        a_prev, a = eps, eps
+        r = None
+        for k in range(40):
+            r = o.descent(q, oracle_mod.NESTEROV, eta, mu=mu, max_steps=1, force_tol=0.0,
+                          state=r)
+            b = a + mu * (a - a_prev)
+            a_prev, a = a, (1 - eta * lam) * b
+            b_next = a + mu * (a - a_prev)
+            assert np.abs(r["x"][1] - a * wave).max() <= 1e-12 * eps
+            assert np.abs(r["y"][1] - b_next * wave).max() <= 1e-12 * eps
+            assert np.abs(r["F"][1] + lam * b_next * wave).max() <= 1e-11 * eps
+        assert np.abs(r["x"][[0, 2, 3, 4]]).max() == 0.0
+
+
+def test_nesterov_without_momentum_is_gradient_descent(oracle_mod):
+    o = oracle_mod.Oracle((6, 5, 4), A, B, C, 2.32, 0.5, 0.3)
+    q = synth.random_uniaxial_q((6, 5, 4), 5)
+    g = o.descent(q, oracle_mod.GD, 0.02, max_steps=25, force_tol=0.0)
+    n = o.descent(q, oracle_mod.NESTEROV, 0.02, mu=0.0, max_steps=25, force_tol=0.0)
+    assert np.array_equal(g["x"], n["x"]) and np.array_equal(g["F"], n["F"])
