@@ -296,6 +296,53 @@ def run_serving(count: int, rate: float, budget_gb: float = 120.0):
             "site_updates_per_s": st["site_updates"] / wall, "wall_s": wall}
 
 
+def run_minimizers(L: int, seconds: float):
+    """FIRE against gradient descent and Nesterov's accelerated gradient on a
+    periodic one-constant bulk from a random start (the comparison of Fig. 2,
+    at L^3), each for the same wall-clock budget on the FP32 form: the
+    residual |F|/sqrt(N) and the energy against time, and the time each
+    method needs to bring |F|/sqrt(N) below 1e-2, 1e-3, 1e-4."""
+    from paper_1911_07045_b300 import lqmin
+    cfg = dict(shape=(L, L, L), L1=synth.L1_5CB, L2=0.0, L3=0.0, objects=[])
+    runs = {
+        "fire": lqmin.fire_params(**dict(synth.FIRE_DEFAULTS, max_iter=10 ** 12, force_tol=0.0)),
+        "fire_dtmax_0.05": lqmin.fire_params(**dict(synth.FIRE_DEFAULTS, dt_max=0.05,
+                                                    max_iter=10 ** 12, force_tol=0.0)),
+        # steps near the stability limit of the stiffest mode: eta lam < 2
+        # (GD), < 2 (1 + mu) / (1 + 2 mu) (Nesterov), lam ~ 3 L1 x 12 = 84
+        "gd_eta_0.02": lqmin.descent_params(lqmin.LQ_MIN_GD, 0.02, max_iter=10 ** 12, force_tol=0.0),
+        "nesterov_eta_0.012_mu_0.9": lqmin.descent_params(lqmin.LQ_MIN_NESTEROV, 0.012, momentum=0.9,
+                                                          max_iter=10 ** 12, force_tol=0.0),
+    }
+    out = {"workload": f"{L}^3 periodic bulk, one constant, random directors (seed 1), FP32 form, "
+                       f"{seconds} s each", "methods": {}}
+    for name, p in runs.items():
+        s = lqmin.solver_for(cfg, precision=lqmin.LQ_FP32_BULK_FP64_RED)
+        s.init_random_uniaxial(1)
+        r = s.step(p, 1)
+        t0 = time.perf_counter()
+        trace, reach = [], {}
+        chunk, it = 16, 1
+        while True:
+            r = s.step(p, chunk)
+            it += chunk
+            t = time.perf_counter() - t0
+            rms = r.rms_force
+            trace.append([round(t, 3), it, rms, s.energy()[0]])
+            for thr in (1e-2, 1e-3, 1e-4):
+                if rms < thr and str(thr) not in reach:
+                    reach[str(thr)] = round(t, 3)
+            if t > seconds or r.fire_status != lqmin.FIRE_RUNNING or not np.isfinite(rms):
+                break
+            chunk = min(chunk * 2, 1024)
+        out["methods"][name] = {"seconds_to_rms_force": reach, "iterations": it,
+                                "status": int(r.fire_status),
+                                "final_rms_force": trace[-1][2], "final_energy": trace[-1][3],
+                                "trace": trace[:: max(1, len(trace) // 12)] + [trace[-1]]}
+        s.close()
+    return out
+
+
 def cpu_baseline(L_sample=128, steps=6):
     """The oracle as it stands, on the host cores: FIRE iterations on a
     L_sample^3 lattice with the same structure (colloids scaled by L/512,
@@ -375,6 +422,8 @@ def main_ours(args, dist: Dist):
         line["batched"] = run_batch(args.batch_steps)
     if dist.world == 1 and args.serving_requests > 0:
         line["served"] = run_serving(args.serving_requests, args.serving_rate)
+    if dist.world == 1 and args.minimizers > 0:
+        line["minimizers"] = run_minimizers(args.minimizer_size, args.minimizers)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if not all(f["ok"] for f in forms.values()):
@@ -426,6 +475,9 @@ def main(argv=None):
     ap.add_argument("--batch-steps", type=int, default=50)
     ap.add_argument("--serving-requests", type=int, default=8)
     ap.add_argument("--serving-rate", type=float, default=20.0)
+    ap.add_argument("--minimizers", type=float, default=0.0,
+                    help="seconds per method of the FIRE / GD / Nesterov comparison (0: skip)")
+    ap.add_argument("--minimizer-size", type=int, default=250)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
