@@ -66,7 +66,9 @@ class _Model(C.Structure):
                 ("periodic", C.c_int * 3),
                 ("A", C.c_double), ("B", C.c_double), ("C", C.c_double),
                 ("L1", C.c_double), ("L2", C.c_double), ("L3", C.c_double),
-                ("S0", C.c_double)]
+                ("S0", C.c_double), ("L4", C.c_double), ("L6", C.c_double),
+                ("H", C.c_double * 3), ("mu0_dchi", C.c_double),
+                ("E", C.c_double * 3), ("eps0_deps", C.c_double)]
 
 
 class _AnchorSpec(C.Structure):
@@ -170,12 +172,14 @@ class Oracle:
     """
 
     def __init__(self, shape, A, B, C_, L1, L2=0.0, L3=0.0, periodic=(1, 1, 1),
-                 objects=(), S0=None):
+                 objects=(), S0=None, L4=0.0, L6=0.0, H=(0.0, 0.0, 0.0), mu0_dchi=0.0,
+                 E=(0.0, 0.0, 0.0), eps0_deps=0.0):
         self.nx, self.ny, self.nz = (int(s) for s in shape)
         self.N = self.nx * self.ny * self.nz
         self.S0 = uniaxial_s0(A, B, C_) if S0 is None else float(S0)
         self.model = _Model(self.nx, self.ny, self.nz, (C.c_int * 3)(*periodic),
-                            A, B, C_, L1, L2, L3, self.S0)
+                            A, B, C_, L1, L2, L3, self.S0, L4, L6, (C.c_double * 3)(*H),
+                            mu0_dchi, (C.c_double * 3)(*E), eps0_deps)
         self._keep = []
         objs = (_Object * max(1, len(objects)))()
         for o, spec in zip(objs, objects):

@@ -86,14 +86,23 @@ static void to_q5(double G[3][3], double out[5]) {
 
 /* ---- bulk, Eq. (fphase) ------------------------------------------------ */
 
+/* the external-field coupling tensor: f_ext = -(1/3) sum_ab K_ab Q_ab with
+   K = mu0_dchi H H^T + eps0_deps E E^T */
+static void field_tensor(const orc_model *m, double K[3][3]) {
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) K[a][b] = m->mu0_dchi * m->H[a] * m->H[b] + m->eps0_deps * m->E[a] * m->E[b];
+}
+
 static double bulk_energy(const orc_model *m, double Q[3][3]) {
-    double trQ2 = 0.0, trQ3 = 0.0;
+    double trQ2 = 0.0, trQ3 = 0.0, ext = 0.0, K[3][3];
+    field_tensor(m, K);
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
             trQ2 += Q[a][b] * Q[b][a];
             for (int c = 0; c < 3; ++c) trQ3 += Q[a][b] * Q[b][c] * Q[c][a];
+            ext += K[a][b] * Q[a][b];
         }
-    return m->A / 2.0 * trQ2 + m->B / 3.0 * trQ3 + m->C / 4.0 * trQ2 * trQ2;
+    return m->A / 2.0 * trQ2 + m->B / 3.0 * trQ3 + m->C / 4.0 * trQ2 * trQ2 - ext / 3.0;
 }
 
 /* dF/dQ_ab of Eq. (fphase): A Q + B Q.Q + C tr(Q^2) Q */
@@ -107,6 +116,10 @@ static void bulk_grad(const orc_model *m, double Q[3][3], double G[3][3]) {
             for (int c = 0; c < 3; ++c) QQ += Q[a][c] * Q[c][b];
             G[a][b] = m->A * Q[a][b] + m->B * QQ + m->C * trQ2 * Q[a][b];
         }
+    double K[3][3];
+    field_tensor(m, K);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) G[a][b] -= K[a][b] / 3.0;
 }
 
 /* ---- anchoring (boundary free energy) ---------------------------------- */
@@ -231,29 +244,61 @@ static void fd_tensor(const double *q, int64_t N, int64_t i, const fd_choices *c
     }
 }
 
-/* Eq. (fdistortionFull), L1, L2, L3 terms, Einstein summation written out */
-static double distortion_density(const orc_model *m, double d[3][3][3]) {
-    double e1 = 0.0, e2 = 0.0, e3 = 0.0;
+/* Levi-Civita symbol */
+static double levi(int i, int j, int k) {
+    return (double)((i - j) * (j - k) * (k - i)) / 2.0;
+}
+
+/* Eq. (fdistortionFull), Einstein summation written out, with Q the site's
+   tensor (it multiplies the L4 and L6 terms):
+   L1/2 d_ijk d_ijk + L2/2 d_ijj d_ikk + L3/2 d_ikj d_ijk
+   + L4/2 eps_lik Q_lj d_ijk + L6/2 Q_lk d_ijl d_ijk,   d_ijk = dQ_ij/dx_k */
+static double distortion_density(const orc_model *m, double Q[3][3], double d[3][3][3]) {
+    double e1 = 0.0, e2 = 0.0, e3 = 0.0, e4 = 0.0, e6 = 0.0;
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j)
             for (int k = 0; k < 3; ++k) {
                 e1 += d[i][j][k] * d[i][j][k];
                 e2 += d[i][j][j] * d[i][k][k];
                 e3 += d[i][k][j] * d[i][j][k];
+                for (int l = 0; l < 3; ++l) {
+                    e4 += levi(l, i, k) * Q[l][j] * d[i][j][k];
+                    e6 += Q[l][k] * d[i][j][l] * d[i][j][k];
+                }
             }
-    return m->L1 / 2.0 * e1 + m->L2 / 2.0 * e2 + m->L3 / 2.0 * e3;
+    return m->L1 / 2.0 * e1 + m->L2 / 2.0 * e2 + m->L3 / 2.0 * e3 + m->L4 / 2.0 * e4 +
+           m->L6 / 2.0 * e6;
 }
 
 /* derivative of the density above with respect to d[a][b][c] */
-static void distortion_ddens(const orc_model *m, double d[3][3][3], double g[3][3][3]) {
+static void distortion_ddens(const orc_model *m, double Q[3][3], double d[3][3][3],
+                             double g[3][3][3]) {
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b)
             for (int c = 0; c < 3; ++c) {
-                double div = 0.0;
+                double div = 0.0, chi = 0.0, cub = 0.0;
                 for (int j = 0; j < 3; ++j) div += d[a][j][j];
+                for (int l = 0; l < 3; ++l) {
+                    chi += levi(l, a, c) * Q[l][b];
+                    cub += Q[c][l] * d[a][b][l];
+                }
                 g[a][b][c] = m->L1 * d[a][b][c] + (b == c ? m->L2 * div : 0.0) +
-                             m->L3 * d[a][c][b];
+                             m->L3 * d[a][c][b] + m->L4 / 2.0 * chi + m->L6 * cub;
             }
+}
+
+/* derivative of the density above with respect to the site's own Q_ab
+   (through the L4 and L6 prefactors) */
+static void distortion_dQ(const orc_model *m, double d[3][3][3], double gq[3][3]) {
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double chi = 0.0, cub = 0.0;
+            for (int i = 0; i < 3; ++i)
+                for (int k = 0; k < 3; ++k) chi += levi(a, i, k) * d[i][b][k];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) cub += d[i][j][a] * d[i][j][b];
+            gq[a][b] = m->L4 / 2.0 * chi + m->L6 / 2.0 * cub;
+        }
 }
 
 /* list every combination (s_x, s_y, s_z) of allowed differences; an axis
@@ -290,7 +335,7 @@ void orc_site_energy(const orc_model *m, const orc_geometry *g, const double *q,
     double sum = 0.0, d[3][3][3];
     for (int t = 0; t < nc; ++t) {
         fd_tensor(q, N, i, &ch, s[t], d);
-        sum += distortion_density(m, d);
+        sum += distortion_density(m, Q, d);
     }
     parts[1] = sum / nc;
 
@@ -363,7 +408,8 @@ static void site_force(const orc_model *m, const orc_geometry *g, const double *
         int s[8][3];
         int nc = list_combos(&ch, s);
         double inv = 1.0 / nc;
-        double d[3][3][3], dd[3][3][3];
+        double d[3][3][3], dd[3][3][3], Qi[3][3];
+        qmat(q, N, i, Qi);
         for (int u = 0; u < nc; ++u) {
             /* coefficient of Q(j) in the difference along each axis */
             double coef[3];
@@ -381,10 +427,17 @@ static void site_force(const orc_model *m, const orc_geometry *g, const double *
             }
             if (!any) continue;
             fd_tensor(q, N, i, &ch, s[u], d);
-            distortion_ddens(m, d, dd);
+            distortion_ddens(m, Qi, d, dd);
             for (int a = 0; a < 3; ++a)
                 for (int b = 0; b < 3; ++b)
                     for (int k = 0; k < 3; ++k) G[a][b] += inv * coef[k] * dd[a][b][k];
+            if (i == j) {
+                /* the site's own Q multiplies the L4 and L6 terms */
+                double gq[3][3];
+                distortion_dQ(m, d, gq);
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) G[a][b] += inv * gq[a][b];
+            }
         }
     }
 

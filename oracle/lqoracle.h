@@ -29,6 +29,11 @@ typedef struct {
     double A, B, C;           /* bulk constants, Eq. (fphase) */
     double L1, L2, L3;        /* distortion constants, Eq. (fdistortionFull) */
     double S0;                /* degree of order used by the anchoring terms */
+    double L4, L6;            /* chiral and cubic terms of Eq. (fdistortionFull) */
+    /* external fields (section II, external fields free energy):
+       -(1/3) mu0_dchi H.Q.H - (1/3) eps0_deps E.Q.E, counted with the bulk */
+    double H[3], mu0_dchi;
+    double E[3], eps0_deps;
 } orc_model;
 
 /* anchoring kinds, boundary free energy of section II */

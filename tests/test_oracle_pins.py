@@ -607,3 +607,130 @@ def test_nesterov_without_momentum_is_gradient_descent(oracle_mod):
     g = o.descent(q, oracle_mod.GD, 0.02, max_steps=25, force_tol=0.0)
     n = o.descent(q, oracle_mod.NESTEROV, 0.02, mu=0.0, max_steps=25, force_tol=0.0)
     assert np.array_equal(g["x"], n["x"]) and np.array_equal(g["F"], n["F"])
+
+
+# ---- chiral L4, cubic L6 and external fields (Eq. fdistortionFull, section II) ----
+
+EXTRA = dict(L4=0.7, L6=0.9, H=(0.3, -0.2, 0.5), mu0_dchi=1.3, E=(0.1, 0.4, 0.2), eps0_deps=-0.6)
+
+
+def _twist_helix(L, k, S):
+    """Uniaxial Q at order S with n = (cos kz, sin kz, 0), all sites."""
+    z = np.repeat(np.arange(L[2]), L[0] * L[1]).astype(float)
+    n = np.stack([np.cos(k * z), np.sin(k * z), np.zeros_like(z)])
+    return synth.uniaxial_q(n, S)
+
+
+@pytest.mark.parametrize("m", [1, 2, 5])
+def test_twist_helix_energy_with_chiral_and_cubic_terms(oracle_mod, m):
+    """A twist helix along z on a periodic lattice: every site sees the same
+    averaged differences (Q(z+1) - Q(z-1)) / 2 and squares, so per site
+      L1:  (9 S^2 / 8) L1 (1 - cos 2k)
+      L4:  (9 S^2 / 16) L4 sin 2k     (eps_lik Q_lj dQ_ij/dz, only k = z)
+      L6:  L6/2 Q_zz <|dQ/dz|^2> = -(9 L6 S^3 / 16) (1 - cos 2k)
+    and the L2, L3 terms vanish (Q_iz = 0 for i != z, Q_zz constant)."""
+    shape = (2, 3, 24)
+    k = 2 * math.pi * m / shape[2]
+    S = 0.53
+    o = oracle_mod.Oracle(shape, A, B, C, 2.32, 0.5, 0.3, L4=0.7, L6=0.9)
+    _, parts = o.energy(_twist_helix(shape, k, S))
+    per = (9 * S ** 2 / 8 * 2.32 * (1 - math.cos(2 * k)) + 9 * S ** 2 / 16 * 0.7 * math.sin(2 * k)
+           - 9 * 0.9 * S ** 3 / 16 * (1 - math.cos(2 * k)))
+    assert abs(parts[1] - o.N * per) < 1e-12 * o.N
+
+
+def test_chiral_term_picks_a_handedness(oracle_mod):
+    """L4 < 0 favours the helix with k > 0, L4 > 0 the other; the lattice
+    energy of the twist helix is lowest at tan 2k = -L4 / (2 L1) (from the
+    closed form above with L6 = 0)."""
+    shape = (1, 1, 120)
+    for L4 in (-0.5, 0.5):
+        o = oracle_mod.Oracle(shape, 0.0, 0.0, 0.0, 2.32, L4=L4)
+        ks = 2 * math.pi * np.arange(-6, 7) / shape[2]
+        E = [o.energy(_twist_helix(shape, k, 0.5))[1][1] for k in ks]
+        kbest = ks[int(np.argmin(E))]
+        kstar = -0.5 * math.atan(L4 / (2 * 2.32))
+        assert np.sign(kbest) == np.sign(kstar)
+        assert abs(kbest - kstar) <= math.pi / shape[2]
+
+
+def test_field_energy_and_alignment(oracle_mod):
+    """Uniaxial limit of the field term: -(1/2) S mu0_dchi (H.n)^2 + const;
+    minimising a single site aligns the director with H for mu0_dchi > 0 and
+    turns it perpendicular for mu0_dchi < 0."""
+    H = np.array([0.6, 0.0, 0.8])
+    for chi in (2.0, -2.0):
+        o = oracle_mod.Oracle((1, 1, 1), A, B, C, 2.32, H=tuple(H), mu0_dchi=chi)
+        qpar = synth.uniaxial_q(H[:, None], o.S0)
+        nperp = np.array([0.8, 0.0, -0.6])
+        qper = synth.uniaxial_q(nperp[:, None], o.S0)
+        dE = o.energy(qpar)[0] - o.energy(qper)[0]
+        assert abs(dE - (-0.5 * o.S0 * chi * 1.0)) < 1e-13
+        q0 = synth.uniaxial_q(np.array([[0.3], [0.9], [0.3]]) / math.sqrt(0.99), o.S0)
+        r = o.descent(q0, oracle_mod.NESTEROV, 0.05, mu=0.5, force_tol=1e-12, max_steps=200000,
+                      max_iter=200000)
+        assert r["status"] == oracle_mod.CONVERGED
+        Qf = full_Q(r["y"])[0]
+        # the largest-eigenvalue axis: along H for chi > 0, perpendicular for chi < 0
+        w, V = np.linalg.eigh(Qf)
+        nmax = V[:, int(np.argmax(w))]
+        assert (abs(np.dot(nmax, H)) > 1 - 1e-6) if chi > 0 else (abs(np.dot(nmax, H)) < 1e-6)
+
+
+EXTRA_GEOMS = ["sphere_nd_3c", "fg_walls_open_y", "custom_open_x", "tiny_2cube"]
+
+
+@pytest.mark.parametrize("name", EXTRA_GEOMS)
+def test_force_is_minus_gradient_with_chiral_cubic_and_fields(oracle_mod, name):
+    gdef = GEOMS[name]
+    o = oracle_mod.Oracle(gdef["shape"], A, B, C, *gdef["L"], periodic=gdef["periodic"],
+                          objects=gdef["objects"], **EXTRA)
+    q = rand_q(o.N, 6)
+    F = o.force(q)
+    sim = o.simulated()
+    assert np.all(F[:, ~sim] == 0)
+    rng = np.random.default_rng(5)
+    h = 1e-5
+    for _ in range(25):
+        i = int(rng.choice(np.nonzero(sim)[0]))
+        c = int(rng.integers(5))
+        vals = []
+        for s in (+1, -1, +2, -2):
+            qq = q.copy()
+            qq[c, i] += s * h
+            vals.append(o.energy(qq)[0])
+        fd = -(8 * (vals[0] - vals[1]) - (vals[2] - vals[3])) / (12 * h)
+        assert abs(fd - F[c, i]) < 1e-7 * max(1.0, abs(F[c, i])), (i, c, fd, F[c, i])
+
+
+def test_chiral_energy_is_odd_under_reflection(oracle_mod):
+    """Mirroring x -> -x (lattice and Q -> M Q M) flips the sign of the L4
+    energy and keeps every other term: eps_lik is a pseudotensor."""
+    L = 6
+    M = np.diag([-1.0, 1.0, 1.0])
+    q = rand_q(L ** 3, 9)
+    idx = np.arange(L ** 3)
+    x, y, z = idx % L, (idx // L) % L, idx // (L * L)
+    j = ((-x) % L) + L * (y + L * z)
+    qm = np.zeros_like(q)
+    qm[:, j] = comps(np.einsum("ab,nbc,dc->nad", M, full_Q(q), M))
+    base = oracle_mod.Oracle((L, L, L), A, B, C, 2.32, 0.5, 0.3, L6=0.9)
+    chi = oracle_mod.Oracle((L, L, L), A, B, C, 2.32, 0.5, 0.3, L4=0.7, L6=0.9)
+    e4 = chi.energy(q)[1][1] - base.energy(q)[1][1]
+    e4m = chi.energy(qm)[1][1] - base.energy(qm)[1][1]
+    assert abs(e4) > 1e-3
+    assert abs(e4 + e4m) < 1e-11 * abs(e4)
+    assert abs(base.energy(q)[0] - base.energy(qm)[0]) < 1e-11 * abs(base.energy(q)[0])
+
+
+@pytest.mark.parametrize("rot", ["z90", "x90"])
+def test_cubic_rotation_invariance_with_chiral_and_cubic_terms(oracle_mod, rot):
+    R = {"z90": np.array([[0, -1, 0], [1, 0, 0], [0, 0, 1]]),
+         "x90": np.array([[1, 0, 0], [0, 0, -1], [0, 1, 0]])}[rot]
+    L = 6
+    objects = [dict(type="sphere", c=(3.0, 2.0, 3.0), R=1.2, anchor=HOM(5.3))]
+    o = oracle_mod.Oracle((L, L, L), A, B, C, 2.32, 0.5, 0.3, objects=objects, L4=0.7, L6=0.9)
+    q = rand_q(o.N, 10)
+    qr, objr = _lattice_rotation(L, R, q, objects)
+    orr = oracle_mod.Oracle((L, L, L), A, B, C, 2.32, 0.5, 0.3, objects=objr, L4=0.7, L6=0.9)
+    assert np.allclose(o.energy(q)[1], orr.energy(qr)[1], rtol=1e-12, atol=1e-12)
