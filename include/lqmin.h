@@ -69,15 +69,22 @@ typedef struct {
 } lq_lattice;
 
 /* Material constants in lattice units.  Bulk A, B, C: Eq. (fphase).
-   Distortion L1, L2, L3: Eq. (fdistortionFull); L4 and L6 must be 0.
-   n_constants = 1 uses the one-constant form Eq. (fd1) (L2 = L3 = 0
-   required), 3 the L1/L2/L3 form.  S0 <= 0 selects Eq. (S0def) from A, B, C;
-   it sets the preferred order of the anchoring terms. */
+   Distortion L1, L2, L3, the chiral L4 and the cubic L6 term:
+   Eq. (fdistortionFull), each averaged over the allowed one-sided
+   differences like the others.  n_constants = 1 uses the one-constant form
+   Eq. (fd1) (L2 = L3 = L4 = L6 = 0 required), 3 the full form.  S0 <= 0
+   selects Eq. (S0def) from A, B, C; it sets the preferred order of the
+   anchoring terms.  External fields (section II): the density
+   -(1/3) mu0_dchi H.Q.H - (1/3) eps0_deps E.Q.E (mu0 dchi and eps0 deps the
+   anisotropic couplings, in lattice units), reported with the bulk energy;
+   all zero for none. */
 typedef struct {
     double A, B, C;
     double L1, L2, L3, L4, L6;
     int n_constants;
     double S0;
+    double H[3], mu0_dchi;
+    double E[3], eps0_deps;
 } lq_material;
 
 /* Anchoring of a surface, section II (boundary free energy):

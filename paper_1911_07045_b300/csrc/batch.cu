@@ -28,6 +28,7 @@ struct lq_batch {
     cudaStream_t stream = nullptr;
     int ty = 0, zchunk = 0;           // tiling; zchunk 0 = each lattice's own
     int idx32 = 1;                    // every lattice indexed in 32 bits
+    int form = 0;                     // kernel form: 0 one-, 1 three-constant, 2 with L4 / L6
     bool tables_ok = false;
     int cap = 0;                      // lattices the device arrays hold
     // device tables
@@ -131,7 +132,7 @@ lq_status build_items(lq_batch *b, int ty, int zc_all, bool shadow) {
 }
 
 int persistent_grid(lq_batch *b, int ty) {
-    int per = fire_batch_blocks_per_sm(b->fp32, b->three, ty, b->idx32);
+    int per = fire_batch_blocks_per_sm(b->fp32, b->form, ty, b->idx32);
     return std::max(1, per) * b->nsm;
 }
 
@@ -161,7 +162,7 @@ lq_status ensure_graph(lq_batch *b) {
     BK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int t = 0; t < kk && e == cudaSuccess; ++t)
-        e = launch_fire_batch(b->fp32, b->three, b->ty, b->idx32, b->args, b->items, b->nitems, grid, b->stream);
+        e = launch_fire_batch(b->fp32, b->form, b->ty, b->idx32, b->args, b->items, b->nitems, grid, b->stream);
     if (e == cudaSuccess) e = batch_running(b->states, (int)b->solvers.size(), b->running, b->stream);
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -222,7 +223,8 @@ lq_status batch_new(int device, int fp32, int three, lq_batch **out) {
     cudaError_t e = cudaSuccess;
     for (int ty : {4, 8})
         for (int i32 : {0, 1})
-            if (e == cudaSuccess) e = prepare_fire_batch(fp32, three, ty, i32);
+            for (int form : {three ? 1 : 0, three ? 2 : 0})
+                if (e == cudaSuccess) e = prepare_fire_batch(fp32, form, ty, i32);
     if (e == cudaSuccess) e = cudaMalloc(&b->running, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMallocHost(&b->running_host, sizeof(unsigned int));
     if (e != cudaSuccess) {
@@ -249,8 +251,11 @@ lq_status batch_set_members(lq_batch *b, lq_solver *const *solvers, int n) {
     b->solvers.assign(solvers, solvers + n);
     b->sites = 0;
     b->idx32 = 1;
-    for (int l = 0; l < n; ++l)
+    b->form = b->three ? 1 : 0;
+    for (int l = 0; l < n; ++l) {
         if (!step_index32(solvers[l]->L.N)) b->idx32 = 0;
+        if (solvers[l]->ext) b->form = 2;
+    }
     if (n > b->cap) {
         cudaFree(b->args); cudaFree(b->shadow_args); cudaFree(b->shadow); cudaFree(b->states);
         b->args = b->shadow_args = nullptr; b->shadow = nullptr; b->states = nullptr;
@@ -287,7 +292,7 @@ lq_status batch_round(lq_batch *b, int k, unsigned int *running) {
     if (!b->tables_ok) return bfail(b, LQ_EINVAL, "batch tables are not built");
     int grid = persistent_grid(b, b->ty);
     for (int t = 0; t < k; ++t)
-        BK(launch_fire_batch(b->fp32, b->three, b->ty, b->idx32, b->args, b->items, b->nitems, grid, b->stream));
+        BK(launch_fire_batch(b->fp32, b->form, b->ty, b->idx32, b->args, b->items, b->nitems, grid, b->stream));
     BK(batch_running(b->states, (int)b->solvers.size(), b->running, b->stream));
     BK(cudaMemcpyAsync(b->running_host, b->running, sizeof(unsigned int), cudaMemcpyDeviceToHost, b->stream));
     BK(cudaStreamSynchronize(b->stream));
@@ -369,14 +374,14 @@ lq_status lq_batch_autotune(lq_batch *b, const lq_fire_params *p, int launches, 
             for (int l = 0; l < n; ++l)
                 cudaMemcpyAsync(b->shadow + l, b->solvers[l]->st, sizeof(FireDev), cudaMemcpyDeviceToDevice,
                                 b->stream);
-            cudaError_t e = launch_fire_batch(b->fp32, b->three, ty, b->idx32, b->shadow_args, b->items, b->nitems,
+            cudaError_t e = launch_fire_batch(b->fp32, b->form, ty, b->idx32, b->shadow_args, b->items, b->nitems,
                                               grid, b->stream);
             cudaEventRecord(e0, b->stream);
             for (int t = 0; t < launches && e == cudaSuccess; ++t) {
                 for (int l = 0; l < n; ++l)   // every timed launch starts from the same state
                     cudaMemcpyAsync(b->shadow + l, b->solvers[l]->st, sizeof(FireDev),
                                     cudaMemcpyDeviceToDevice, b->stream);
-                e = launch_fire_batch(b->fp32, b->three, ty, b->idx32, b->shadow_args, b->items, b->nitems, grid,
+                e = launch_fire_batch(b->fp32, b->form, ty, b->idx32, b->shadow_args, b->items, b->nitems, grid,
                                       b->stream);
             }
             cudaEventRecord(e1, b->stream);
@@ -412,7 +417,7 @@ lq_status lq_batch_step(lq_batch *b, const lq_fire_params *p, int64_t n, lq_resu
     int grid = persistent_grid(b, b->ty);
     for (int64_t t = 0; t < full; ++t) BK(cudaGraphLaunch(b->gexec, b->stream));
     for (int64_t t = 0; t < rest; ++t)
-        BK(launch_fire_batch(b->fp32, b->three, b->ty, b->idx32, b->args, b->items, b->nitems, grid, b->stream));
+        BK(launch_fire_batch(b->fp32, b->form, b->ty, b->idx32, b->args, b->items, b->nitems, grid, b->stream));
     BK(cudaStreamSynchronize(b->stream));
     return collect(b, out, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
 }

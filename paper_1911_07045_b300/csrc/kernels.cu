@@ -425,7 +425,8 @@ __device__ __forceinline__ void load5(const QS *q, long long N, long long i, dou
 // T: arithmetic type of the form (selects the record layout); QS: Q storage
 template <typename T, typename QS>
 __global__ void k_energy(LatticeDev L, Geometry g, const QS *q, double A, double B, double C,
-                         double L1, double L2, double L3, double S0, double *partials) {
+                         double L1, double L2, double L3, double S0, EnergyExtra ex,
+                         double *partials) {
     double eb = 0.0, ed = 0.0, ea = 0.0;
     const long long N = L.N;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
@@ -443,6 +444,9 @@ __global__ void k_energy(LatticeDev L, Geometry g, const QS *q, double A, double
             double det = a * (d * f - e * e) - b * (b * f - e * c) + c * (b * e - d * c);
             // tr Q^3 = 3 det Q for a traceless Q
             eb += A / 2.0 * tr2 + B / 3.0 * (3.0 * det) + C / 4.0 * tr2 * tr2;
+            // external fields: -(1/3) K:Q
+            const double *K = ex.K;
+            eb -= (K[0] * a + K[3] * d + K[5] * f + 2.0 * (K[1] * b + K[2] * c + K[4] * e)) / 3.0;
         }
         // distortion: factorised average over allowed differences
         double mk[3][5], sqF[3], squ[3];
@@ -482,6 +486,29 @@ __global__ void k_energy(LatticeDev L, Geometry g, const QS *q, double A, double
                 }
                 f += L2 / 2.0 * t2 + L3 / 2.0 * t3;
             }
+        if (ex.L4 != 0.0 || ex.L6 != 0.0) {
+            // chiral: L4/2 eps_lik Q_lj m_k[ij]; cubic: L6/2 (Q_kk <|D_k|^2>
+            // + sum_{l != k} Q_lk m_l . m_k)
+            double f4 = 0.0, f6 = 0.0;
+            for (int l = 0; l < 3; ++l)
+                for (int i2 = 0; i2 < 3; ++i2)
+                    for (int k = 0; k < 3; ++k) {
+                        int e3 = (l - i2) * (i2 - k) * (k - l) / 2;
+                        if (!e3) continue;
+                        for (int j = 0; j < 3; ++j) f4 += e3 * sym(q0, l, j) * sym(mk[k], i2, j);
+                    }
+            for (int k = 0; k < 3; ++k) {
+                f6 += sym(q0, k, k) * sqF[k];
+                for (int l = 0; l < 3; ++l) {
+                    if (l == k) continue;
+                    double dot = 0.0;
+                    for (int a2 = 0; a2 < 3; ++a2)
+                        for (int b2 = 0; b2 < 3; ++b2) dot += sym(mk[l], a2, b2) * sym(mk[k], a2, b2);
+                    f6 += sym(q0, l, k) * dot;
+                }
+            }
+            f += ex.L4 / 2.0 * f4 + ex.L6 / 2.0 * f6;
+        }
         ed += f;
         // anchoring
         if (m & M_ANCH) {
@@ -550,13 +577,16 @@ __global__ void k_sum_partials3(const double *partials, int n, double *out3) {
 
 cudaError_t energy_parts(const LatticeDev &L, const Geometry &g, const void *q, int fp32,
                          double A, double B, double C, double L1, double L2, double L3, double S0,
-                         double *partials, int max_blocks, double *out3, cudaStream_t s) {
+                         const EnergyExtra &ex, double *partials, int max_blocks, double *out3,
+                         cudaStream_t s) {
     int nb = blocks_for(L.N, 256);
     if (nb > max_blocks) nb = max_blocks;
     if (fp32)
-        k_energy<float, int><<<nb, 256, 0, s>>>(L, g, (const int *)q, A, B, C, L1, L2, L3, S0, partials);
+        k_energy<float, int><<<nb, 256, 0, s>>>(L, g, (const int *)q, A, B, C, L1, L2, L3, S0, ex,
+                                                 partials);
     else
-        k_energy<double, double><<<nb, 256, 0, s>>>(L, g, (const double *)q, A, B, C, L1, L2, L3, S0, partials);
+        k_energy<double, double><<<nb, 256, 0, s>>>(L, g, (const double *)q, A, B, C, L1, L2, L3, S0,
+                                                    ex, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_sum_partials3<<<1, 256, 0, s>>>(partials, nb, out3);

@@ -15,6 +15,8 @@ struct StepLaunch {
     Geometry g;
     LatticeDev L;
     double A, B, C, L1, L2, L3, S0;
+    double L4, L6, fext[5];
+    int ext;                  // the chiral / cubic terms are on (three-constant form)
     FireDev *st;
     double *partials;
     int zchunk, force_only, fp32, three;
@@ -34,13 +36,14 @@ cudaError_t launch_fire_step(const StepLaunch &sl, cudaStream_t stream);
 // true when the state arrays of a lattice of N sites are indexed in 32 bits
 bool step_index32(long long N);
 
-// batched steps (tile 32 x ty, ty in {4, 8}; idx32: every lattice of the
-// batch indexed in 32 bits)
+// batched steps (tile 32 x ty, ty in {4, 8}; form 0 one-constant, 1
+// three-constant, 2 with the chiral / cubic terms; idx32: every lattice of
+// the batch indexed in 32 bits)
 size_t step_args_bytes(int fp32);
 void step_args_pack(const StepLaunch &sl, void *out);   // host memory, step_args_bytes()
-cudaError_t prepare_fire_batch(int fp32, int three, int ty, int idx32);
-int fire_batch_blocks_per_sm(int fp32, int three, int ty, int idx32);
-cudaError_t launch_fire_batch(int fp32, int three, int ty, int idx32, const void *dev_args,
+cudaError_t prepare_fire_batch(int fp32, int form, int ty, int idx32);
+int fire_batch_blocks_per_sm(int fp32, int form, int ty, int idx32);
+cudaError_t launch_fire_batch(int fp32, int form, int ty, int idx32, const void *dev_args,
                               const WorkItem *items, int nitems, int grid, cudaStream_t stream);
 // running[0] = number of lattices whose FIRE status is still running
 cudaError_t batch_running(FireDev *const *states, int n, unsigned int *running, cudaStream_t s);
@@ -91,9 +94,16 @@ cudaError_t count_simulated(const LatticeDev &L, const uint8_t *mask, unsigned l
                             cudaStream_t s);
 
 // readback
+// chiral and cubic constants and the field tensor K (xx, xy, xz, yy, yz, zz)
+// of the energy readback
+struct EnergyExtra {
+    double L4, L6;
+    double K[6];
+};
 cudaError_t energy_parts(const LatticeDev &L, const Geometry &g, const void *q, int fp32,
                          double A, double B, double C, double L1, double L2, double L3, double S0,
-                         double *partials, int max_blocks, double *out3, cudaStream_t s);
+                         const EnergyExtra &ex, double *partials, int max_blocks, double *out3,
+                         cudaStream_t s);
 cudaError_t order_field(const LatticeDev &L, const uint8_t *mask, const void *q, int fp32,
                         double *S_out, cudaStream_t s);
 

@@ -22,6 +22,10 @@
 namespace lq {
 namespace {
 
+struct double6 {
+    double v[6];   // symmetric tensor: xx, xy, xz, yy, yz, zz
+};
+
 constexpr int NOALLOC_MAX_NZ = 4096;
 constexpr int NOALLOC_THREADS = 256;
 constexpr int NOALLOC_MAX_DEVICES = 64;
@@ -53,8 +57,8 @@ __device__ __forceinline__ long long step_site(int nx, int ny, int nz, const int
 // averaged-difference distortion density (Eq. fdistortionFull) of its sites
 __global__ void __launch_bounds__(NOALLOC_THREADS)
 k_plane_energy(int nx, int ny, int nz, int px, int py, int pz, double A, double B, double C,
-               double L1, double L2, double L3, const double *q, const uint8_t *mask,
-               double *plane_sums) {
+               double L1, double L2, double L3, double L4, double L6, double6 K, const double *q,
+               const uint8_t *mask, double *plane_sums) {
     const int z = blockIdx.x;
     const long long N = (long long)nx * ny * nz;
     const int per[3] = {px, py, pz};
@@ -70,6 +74,8 @@ k_plane_energy(int nx, int ny, int nz, int px, int py, int pz, double A, double 
         double tr2 = a * a + d * d + f * f + 2.0 * (b * b + c3 * c3 + e * e);
         double det = a * (d * f - e * e) - b * (b * f - e * c3) + c3 * (b * e - d * c3);
         eb += A / 2.0 * tr2 + B * det + C / 4.0 * tr2 * tr2;   // tr Q^3 = 3 det Q
+        // external fields, -(1/3) K:Q
+        eb -= (K.v[0] * a + K.v[3] * d + K.v[5] * f + 2.0 * (K.v[1] * b + K.v[2] * c3 + K.v[4] * e)) / 3.0;
         double mk[3][5], sqF[3], squ[3];
         for (int k = 0; k < 3; ++k) {
             int fo = (m & m_fwd(k)) ? 1 : 0, bo = (m & m_bwd(k)) ? 1 : 0;
@@ -104,6 +110,29 @@ k_plane_energy(int nx, int ny, int nz, int px, int py, int pz, double A, double 
                 }
                 fd += L2 / 2.0 * t2 + L3 / 2.0 * t3;
             }
+        if (L4 != 0.0 || L6 != 0.0) {
+            // chiral L4/2 eps_lik Q_lj m_k[ij], cubic L6/2 (Q_kk <|D_k|^2>
+            // + sum_{l != k} Q_lk m_l . m_k)
+            double f4 = 0.0, f6 = 0.0;
+            for (int l = 0; l < 3; ++l)
+                for (int i2 = 0; i2 < 3; ++i2)
+                    for (int k = 0; k < 3; ++k) {
+                        int e3 = (l - i2) * (i2 - k) * (k - l) / 2;
+                        if (!e3) continue;
+                        for (int j = 0; j < 3; ++j) f4 += e3 * sym(q0, l, j) * sym(mk[k], i2, j);
+                    }
+            for (int k = 0; k < 3; ++k) {
+                f6 += sym(q0, k, k) * sqF[k];
+                for (int l = 0; l < 3; ++l) {
+                    if (l == k) continue;
+                    double dot = 0.0;
+                    for (int a2 = 0; a2 < 3; ++a2)
+                        for (int b2 = 0; b2 < 3; ++b2) dot += sym(mk[l], a2, b2) * sym(mk[k], a2, b2);
+                    f6 += sym(q0, l, k) * dot;
+                }
+            }
+            fd += L4 / 2.0 * f4 + L6 / 2.0 * f6;
+        }
         ed += fd;
     }
     __shared__ double sh[2][NOALLOC_THREADS];
@@ -185,10 +214,19 @@ extern "C" lq_status lq_energy_noalloc(const lq_lattice *lat, const lq_material 
     double *scratch = scratch_for_current_device(&st);
     if (!scratch) return st;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    double6 K;
+    {
+        double Kf[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                Kf[a][b] = mat->mu0_dchi * mat->H[a] * mat->H[b] + mat->eps0_deps * mat->E[a] * mat->E[b];
+        const double v[6] = {Kf[0][0], Kf[0][1], Kf[0][2], Kf[1][1], Kf[1][2], Kf[2][2]};
+        for (int t = 0; t < 6; ++t) K.v[t] = v[t];
+    }
     k_plane_energy<<<lat->nz, NOALLOC_THREADS, 0, s>>>(
         lat->nx, lat->ny, lat->nz, lat->periodic[0] ? 1 : 0, lat->periodic[1] ? 1 : 0,
-        lat->periodic[2] ? 1 : 0, mat->A, mat->B, mat->C, mat->L1, mat->L2, mat->L3, q_dev,
-        mask_dev, scratch);
+        lat->periodic[2] ? 1 : 0, mat->A, mat->B, mat->C, mat->L1, mat->L2, mat->L3, mat->L4,
+        mat->L6, K, q_dev, mask_dev, scratch);
     if (cudaGetLastError() != cudaSuccess) return LQ_ECUDA;
     k_sum_planes<<<1, NOALLOC_THREADS, 0, s>>>(scratch, lat->nz, parts_dev);
     if (cudaGetLastError() != cudaSuccess) return LQ_ECUDA;

@@ -77,6 +77,22 @@ int auto_zchunk(const lq_solver *s) {
 
 int effective_zchunk(const lq_solver *s) { return s->zchunk > 0 ? s->zchunk : auto_zchunk(s); }
 
+// the force of the external fields, the same at every site: f_ext =
+// -(1/3) K:Q with K = mu0_dchi H H^T + eps0_deps E E^T, so F = (1/3) J^T K
+void field_tensor(const lq_material &m, double K[3][3]) {
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) K[a][b] = m.mu0_dchi * m.H[a] * m.H[b] + m.eps0_deps * m.E[a] * m.E[b];
+}
+void field_force(const lq_material &m, double f[5]) {
+    double K[3][3];
+    field_tensor(m, K);
+    f[0] = (K[0][0] - K[2][2]) / 3.0;
+    f[1] = 2.0 * K[0][1] / 3.0;
+    f[2] = 2.0 * K[0][2] / 3.0;
+    f[3] = (K[1][1] - K[2][2]) / 3.0;
+    f[4] = 2.0 * K[1][2] / 3.0;
+}
+
 StepLaunch make_launch(lq_solver *s, int force_only) {
     StepLaunch sl;
     for (int b = 0; b < 2; ++b) { sl.q[b] = s->q[b]; sl.v[b] = s->v[b]; sl.F[b] = s->F[b]; }
@@ -89,12 +105,15 @@ StepLaunch make_launch(lq_solver *s, int force_only) {
     sl.L = s->L;
     sl.A = s->mat.A; sl.B = s->mat.B; sl.C = s->mat.C;
     sl.L1 = s->mat.L1; sl.L2 = s->mat.L2; sl.L3 = s->mat.L3; sl.S0 = s->S0;
+    sl.L4 = s->mat.L4; sl.L6 = s->mat.L6;
+    field_force(s->mat, sl.fext);
     sl.st = s->st;
     sl.partials = s->partials;
     sl.zchunk = effective_zchunk(s);
     sl.force_only = force_only;
     sl.fp32 = s->fp32;
     sl.three = s->three;
+    sl.ext = s->ext;
     return sl;
 }
 
@@ -414,10 +433,9 @@ lq_status lq_create(const lq_lattice *lat, const lq_material *mat, int precision
     *out = nullptr;
     if (lat->nx <= 0 || lat->ny <= 0 || lat->nz <= 0) return fail(s, LQ_EINVAL, "lattice sizes must be positive");
     if (lat->spacing != 1.0) return fail(s, LQ_EINVAL, "spacing must be 1 (lattice units)");
-    if (mat->L4 != 0.0 || mat->L6 != 0.0) return fail(s, LQ_EINVAL, "L4 and L6 terms are not supported");
     if (mat->n_constants != 1 && mat->n_constants != 3) return fail(s, LQ_EINVAL, "n_constants must be 1 or 3");
-    if (mat->n_constants == 1 && (mat->L2 != 0.0 || mat->L3 != 0.0))
-        return fail(s, LQ_EINVAL, "one-constant form needs L2 = L3 = 0");
+    if (mat->n_constants == 1 && (mat->L2 != 0.0 || mat->L3 != 0.0 || mat->L4 != 0.0 || mat->L6 != 0.0))
+        return fail(s, LQ_EINVAL, "one-constant form needs L2 = L3 = L4 = L6 = 0");
     if (precision != LQ_FP64 && precision != LQ_FP32_BULK_FP64_RED) return fail(s, LQ_EINVAL, "bad precision");
     double disc = mat->B * mat->B - 24.0 * mat->A * mat->C;
     double S0 = mat->S0;
@@ -443,6 +461,7 @@ lq_status lq_create(const lq_lattice *lat, const lq_material *mat, int precision
     }
     s->fp32 = precision == LQ_FP32_BULK_FP64_RED;
     s->three = mat->n_constants == 3;
+    s->ext = s->three && (mat->L4 != 0.0 || mat->L6 != 0.0);
     s->esize = s->fp32 ? sizeof(float) : sizeof(double);
     s->L.nx = lat->nx; s->L.ny = lat->ny; s->L.nz = lat->nz;
     s->L.px = lat->periodic[0] ? 1 : 0; s->L.py = lat->periodic[1] ? 1 : 0;
@@ -671,8 +690,11 @@ lq_status lq_energy(lq_solver *s, double *total, double parts[3]) {
     r = ensure_partials(s);
     if (r != LQ_OK) return r;
     Geometry g{s->mask, s->row_start, s->rec_x, s->recs};
+    double Kf[3][3];
+    field_tensor(s->mat, Kf);
+    EnergyExtra ex{s->mat.L4, s->mat.L6, {Kf[0][0], Kf[0][1], Kf[0][2], Kf[1][1], Kf[1][2], Kf[2][2]}};
     CK(energy_parts(s->L, g, s->q[s->cur], s->fp32, s->mat.A, s->mat.B, s->mat.C, s->mat.L1,
-                    s->mat.L2, s->mat.L3, s->S0, s->partials, s->partials_cap, s->out3, s->stream));
+                    s->mat.L2, s->mat.L3, s->S0, ex, s->partials, s->partials_cap, s->out3, s->stream));
     double h[3];
     CK(cudaMemcpyAsync(h, s->out3, sizeof h, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));

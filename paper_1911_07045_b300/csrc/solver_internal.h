@@ -29,6 +29,7 @@ struct lq_solver {
     cudaStream_t stream = nullptr;
     bool own_stream = false;        // created by lq_create when given NULL
     int fp32 = 0, three = 0;
+    int ext = 0;                    // chiral / cubic terms on (three-constant form)
     lq::LatticeDev L{};
     lq_material mat{};
     double S0 = 0;

@@ -67,6 +67,9 @@ struct StepArgs {
     Geometry g;
     LatticeDev L;
     T A, B, C, L1, L2, L3, S0;
+    T L4, L6;                 // chiral and cubic distortion terms (three-constant form)
+    T fext[5];                // force of the external fields (the same at every site)
+    int fields;               // fext is not zero
     FireDev *st;
     double *partials;         // 4 doubles per block
     int zchunk;
@@ -316,6 +319,87 @@ __device__ __forceinline__ void jt_cross(const T *ma, const T *mb, T L2, T L3, T
     o[4] = X[1][2] + X[2][1];
 }
 
+// ---- chiral (L4) and cubic (L6) terms of Eq. (fdistortionFull) -------------
+// Averaged over the allowed differences like the other terms, the density
+// of a site adds  L4/2 eps_lik Q_lj m_k[ij]  +  L6/2 [ sum_k Q_kk <|D_k|^2>
+// + sum_{l != k} Q_lk m_l . m_k ]  (Q the site's tensor, m_k the mean of its
+// allowed differences along k, <|D_k|^2> the mean of their squared norms).
+// Its derivative enters the link flux through X_K (dE/dm_K, below), a
+// diagonal coefficient L6 Q_KK on the squared differences (link_flux), and
+// a local term through the site's own Q (jt_extra_local).
+
+__host__ __device__ constexpr int levi3(int i, int j, int k) {
+    return (i - j) * (j - k) * (k - i) / 2;
+}
+template <int K, typename T>
+__device__ __forceinline__ T qdiag(const T *q) {
+    return K == 0 ? q[0] : (K == 1 ? q[3] : -q[0] - q[3]);
+}
+// Frobenius product of two symmetric traceless tensors given as 5 components
+template <typename T>
+__device__ __forceinline__ T dot5(const T *a, const T *b) {
+    return a[0] * b[0] + a[3] * b[3] + (a[0] + a[3]) * (b[0] + b[3]) +
+           T(2) * (a[1] * b[1] + a[2] * b[2] + a[4] * b[4]);
+}
+// J^T of a general 3x3 matrix
+template <typename T>
+__device__ __forceinline__ void jt_mat(T X[3][3], T *o) {
+    o[0] = X[0][0] - X[2][2];
+    o[1] = X[0][1] + X[1][0];
+    o[2] = X[0][2] + X[2][0];
+    o[3] = X[1][1] - X[2][2];
+    o[4] = X[1][2] + X[2][1];
+}
+// J^T of dE/dm_K from the L4 and L6 terms at a site with tensor q and means
+// ma, mb along the other two axes:  L4/2 eps_{l i K} Q_{l j}
+// + L6 (Q_{a K} m_a[ij] + Q_{b K} m_b[ij])
+template <int K, typename T>
+__device__ __forceinline__ void jt_extra_x(const T *q, const T *ma, const T *mb, T L4, T L6, T *o) {
+    constexpr int a = K == 0 ? 1 : 0;
+    constexpr int b = K == 2 ? 1 : 2;
+    const T qa = sym(q, a, K), qb = sym(q, b, K);
+    T X[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T chi = T(0);
+#pragma unroll
+            for (int l = 0; l < 3; ++l)
+                if (levi3(l, i, K) != 0) chi += T(levi3(l, i, K)) * sym(q, l, j);
+            X[i][j] = T(0.5) * L4 * chi + L6 * (qa * sym(ma, i, j) + qb * sym(mb, i, j));
+        }
+    jt_mat(X, o);
+}
+// J^T of dE/dQ through the site's own tensor: L4/2 sum_{i,k} eps_{a i k}
+// m_k[i b]; L6/2 <|D_k|^2> on (k, k) and L6/2 m_l . m_k on (l, k), l != k
+template <typename T>
+__device__ __forceinline__ void jt_extra_local(const T *mx, const T *my, const T *mz, const T *sq,
+                                               T L4, T L6, T *o) {
+    const T *mk[3] = {mx, my, mz};
+    T G[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            T chi = T(0);
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    if (levi3(a, i, k) != 0) chi += T(levi3(a, i, k)) * sym(mk[k], i, b);
+            G[a][b] = T(0.5) * L4 * chi;
+        }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) G[k][k] += T(0.5) * L6 * sq[k];
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            if (l != k) G[l][k] += T(0.5) * L6 * dot5(mk[l], mk[k]);
+    jt_mat(G, o);
+}
+
 // Shared-memory staging of one block.  A plane slot keeps the drifted Q of
 // the tile and its ring with the five components of a site packed so that a
 // site loads in 2 (fixed point: int4 + int) or 3 (FP64: 2 double2 + double)
@@ -394,12 +478,41 @@ __device__ __forceinline__ void mean_diff(Smem<T, TX, TY> &S, int lx, int ly, in
     }
 }
 
+// mean over the allowed one-sided differences along axis K of their squared
+// norm |D|^2 (the L6 term's <|D_K|^2>)
+template <int K, typename T, int TX, int TY>
+__device__ __forceinline__ T mean_sq(Smem<T, TX, TY> &S, int lx, int ly, int sc, int splus,
+                                     int sminus) {
+    uint8_t m = S.m(sc, lx, ly);
+    const bool f = (m & m_fwd(K)) != 0, b = (m & m_bwd(K)) != 0;
+    using P = Prec<T>;
+    T df[5], db[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        typename P::Q q0 = S.q(sc, c, lx, ly), qf, qb;
+        if (K == 0) { qf = S.q(sc, c, lx + 1, ly); qb = S.q(sc, c, lx - 1, ly); }
+        if (K == 1) { qf = S.q(sc, c, lx, ly + 1); qb = S.q(sc, c, lx, ly - 1); }
+        if (K == 2) { qf = S.q(splus, c, lx, ly); qb = S.q(sminus, c, lx, ly); }
+        df[c] = P::diff(q0, qf);
+        db[c] = P::diff(qb, q0);
+    }
+    T sum = (f ? dot5(df, df) : T(0)) + (b ? dot5(db, db) : T(0));
+    return (f && b) ? T(0.5) * sum : sum;
+}
+
+// the five components of a staged site as values
+template <typename T, int TX, int TY>
+__device__ __forceinline__ void q_at(Smem<T, TX, TY> &S, int slot, int lx, int ly, T *o) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) o[c] = Prec<T>::val(S.q(slot, c, lx, ly));
+}
+
 // flux through the link (a, a + e_K); ma/mb masks, qa/qb drifted Q,
 // xa/xb the J^T X_K cross terms at both ends (three-constant only)
-template <int K, bool THREE, typename T>
+template <int K, bool THREE, bool EXT = false, typename T>
 __device__ __forceinline__ void link_flux(uint8_t ma, uint8_t mb, const typename Prec<T>::Q *qa,
                                           const typename Prec<T>::Q *qb, const T *xa, const T *xb,
-                                          T L1, T L23, T *phi) {
+                                          T L1, T L23, T *phi, T L6 = T(0)) {
     if (!(ma & M_SIM) || !(ma & m_fwd(K))) {
 #pragma unroll
         for (int c = 0; c < 5; ++c) phi[c] = T(0);
@@ -421,6 +534,15 @@ __device__ __forceinline__ void link_flux(uint8_t ma, uint8_t mb, const typename
 #pragma unroll
         for (int c = 0; c < 5; ++c)
             phi[c] = w * (L1 * j1[c] + L23 * j2[c]) + wa * xa[c] + wb * xb[c];
+        if (EXT) {
+            // L6: the squared differences of each end weighted by its Q_KK
+            T va[5], vb[5];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) { va[c] = Prec<T>::val(qa[c]); vb[c] = Prec<T>::val(qb[c]); }
+            const T l6 = L6 * (wa * qdiag<K>(va) + wb * qdiag<K>(vb));
+#pragma unroll
+            for (int c = 0; c < 5; ++c) phi[c] += l6 * j1[c];
+        }
     }
 }
 
@@ -695,12 +817,15 @@ __device__ __forceinline__ void regular_force(Smem<T, TX, TY> &S, int lx, int ly
 // One block's work for one lattice: the tile with origin (bx*TX, by*TY),
 // planes [z0, z1), block number bid of the nblk blocks of that lattice's
 // step (its partial-sum slot).  Shared memory is the caller's.
-template <typename T, bool THREE, int TX, int TY, typename I>
+// FORM: 0 one-constant, 1 three-constant (L1, L2, L3), 2 three-constant
+// with the chiral L4 and cubic L6 terms
+template <typename T, int FORM, int TX, int TY, typename I>
 __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int by, int z0, int z1,
                                           int nblk, int bid, unsigned char *smem_raw, double *red,
                                           int *am_last_p) {
     constexpr int NT = TX * TY;
     constexpr int NSLOT = 5;
+    constexpr bool THREE = FORM >= 1;
     using SM = Smem<T, TX, TY>;
     using P = Prec<T>;
     using QS = typename P::Q;
@@ -828,6 +953,9 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
     __syncthreads();   // the first regularity check reads neighbours' masks
 
     const T L1 = args.L1, L23 = args.L2 + args.L3;
+    // chiral / cubic terms: taken by the general path on every plane
+    constexpr bool ext = FORM == 2;
+    const T L4 = args.L4, L6 = ext ? args.L6 : T(0);
     const T sc_ = T(Stencil<T>::scale);
     const T L1s = L1 * sc_, L23s = L23 * sc_;
     const T L2q = T(0.25) * args.L2 * sc_, L3q = T(0.25) * args.L3 * sc_;
@@ -855,7 +983,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
         if (own) {
             uint8_t a = S.m(sc, lx - 1, ly) & S.m(sc, lx + 1, ly) & S.m(sc, lx, ly - 1) &
                         S.m(sc, lx, ly + 1) & S.m(sp, lx, ly) & S.m(sm, lx, ly) & m0;
-            reg = (m0 & FULL) == FULL && (a & 0xFC) == 0xFC;
+            reg = (m0 & FULL) == FULL && (a & 0xFC) == 0xFC && !ext;
         }
         const I i = (I)z * NXY + (I)gy * (I)L.nx + (I)gx;
         T vold[5], fold[5];
@@ -887,23 +1015,45 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                     mean_diff<0>(S, lx, ly, sc, 0, 0, mx_cur);
                     mean_diff<1>(S, lx, ly, sc, 0, 0, my_cur);
                     jt_cross<2>(mx_cur, my_cur, args.L2, args.L3, xz_cur);
+                    if (ext) {
+                        T qv[5], e[5];
+                        q_at(S, sm, lx, ly, qv);
+                        jt_extra_x<2>(qv, mx, my, L4, L6, e);
+#pragma unroll
+                        for (int c = 0; c < 5; ++c) xz_m[c] += e[c];
+                        q_at(S, sc, lx, ly, qv);
+                        jt_extra_x<2>(qv, mx_cur, my_cur, L4, L6, e);
+#pragma unroll
+                        for (int c = 0; c < 5; ++c) xz_cur[c] += e[c];
+                    }
                 }
                 QS qa[5], qb[5];
 #pragma unroll
                 for (int c = 0; c < 5; ++c) { qa[c] = S.q(sm, c, lx, ly); qb[c] = S.q(sc, c, lx, ly); }
-                link_flux<2, THREE>(S.m(sm, lx, ly), m0, qa, qb, xz_m, xz_cur, L1, L23, phi_zm);
+                link_flux<2, THREE, ext>(S.m(sm, lx, ly), m0, qa, qb, xz_m, xz_cur, L1, L23, phi_zm, L6);
             }
             T xz_nxt[5], mx_nxt[5], my_nxt[5];
             const int xs = z & 1;
             if (THREE) {
                 // cross terms of the tile at plane z
                 if (m0 & M_SIM) {
-                    T mz[5], o[5];
-                    mean_diff<2>(S, lx, ly, sc, sp, sm, mz);
-                    jt_cross<0>(my_cur, mz, args.L2, args.L3, o);
+                    T o[5], e[5], qv[5], mz_cur[5];
+                    mean_diff<2>(S, lx, ly, sc, sp, sm, mz_cur);
+                    if (ext) q_at(S, sc, lx, ly, qv);
+                    jt_cross<0>(my_cur, mz_cur, args.L2, args.L3, o);
+                    if (ext) {
+                        jt_extra_x<0>(qv, my_cur, mz_cur, L4, L6, e);
+#pragma unroll
+                        for (int c = 0; c < 5; ++c) o[c] += e[c];
+                    }
 #pragma unroll
                     for (int c = 0; c < 5; ++c) S.x(xs, 0, c, lx, ly) = o[c];
-                    jt_cross<1>(mx_cur, mz, args.L2, args.L3, o);
+                    jt_cross<1>(mx_cur, mz_cur, args.L2, args.L3, o);
+                    if (ext) {
+                        jt_extra_x<1>(qv, mx_cur, mz_cur, L4, L6, e);
+#pragma unroll
+                        for (int c = 0; c < 5; ++c) o[c] += e[c];
+                    }
 #pragma unroll
                     for (int c = 0; c < 5; ++c) S.x(xs, 1, c, lx, ly) = o[c];
                 }
@@ -915,6 +1065,13 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                         mean_diff<1>(S, sx, sy, sc, sp, sm, my);
                         mean_diff<2>(S, sx, sy, sc, sp, sm, mz);
                         jt_cross<0>(my, mz, args.L2, args.L3, o);
+                        if (ext) {
+                            T qv[5], e[5];
+                            q_at(S, sc, sx, sy, qv);
+                            jt_extra_x<0>(qv, my, mz, L4, L6, e);
+#pragma unroll
+                            for (int c = 0; c < 5; ++c) o[c] += e[c];
+                        }
 #pragma unroll
                         for (int c = 0; c < 5; ++c) S.x(xs, 0, c, sx, sy) = o[c];
                     }
@@ -926,6 +1083,13 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                         mean_diff<0>(S, sx, sy, sc, sp, sm, mx);
                         mean_diff<2>(S, sx, sy, sc, sp, sm, mz);
                         jt_cross<1>(mx, mz, args.L2, args.L3, o);
+                        if (ext) {
+                            T qv[5], e[5];
+                            q_at(S, sc, sx, sy, qv);
+                            jt_extra_x<1>(qv, mx, mz, L4, L6, e);
+#pragma unroll
+                            for (int c = 0; c < 5; ++c) o[c] += e[c];
+                        }
 #pragma unroll
                         for (int c = 0; c < 5; ++c) S.x(xs, 1, c, sx, sy) = o[c];
                     }
@@ -934,6 +1098,13 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                 mean_diff<0>(S, lx, ly, sp, 0, 0, mx_nxt);
                 mean_diff<1>(S, lx, ly, sp, 0, 0, my_nxt);
                 jt_cross<2>(mx_nxt, my_nxt, args.L2, args.L3, xz_nxt);
+                if (ext) {
+                    T qv[5], e[5];
+                    q_at(S, sp, lx, ly, qv);
+                    jt_extra_x<2>(qv, mx_nxt, my_nxt, L4, L6, e);
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) xz_nxt[c] += e[c];
+                }
                 __syncthreads();
             }
             QS q0[5];
@@ -945,8 +1116,8 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                 QS qb[5];
 #pragma unroll
                 for (int c = 0; c < 5; ++c) qb[c] = S.q(sp, c, lx, ly);
-                link_flux<2, THREE>(m0, S.m(sp, lx, ly), q0, qb, xz_cur, THREE ? xz_nxt : xz_cur, L1,
-                                    L23, phi_zp);
+                link_flux<2, THREE, ext>(m0, S.m(sp, lx, ly), q0, qb, xz_cur, THREE ? xz_nxt : xz_cur, L1,
+                                    L23, phi_zp, L6);
             }
             if (own) {
                 T grad[5];
@@ -960,7 +1131,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                     qn[c] = S.q(sc, c, lx - 1, ly);
                     if (THREE) { xa[c] = S.x(xs, 0, c, lx - 1, ly); xb[c] = S.x(xs, 0, c, lx, ly); }
                 }
-                link_flux<0, THREE>(S.m(sc, lx - 1, ly), m0, qn, q0, xa, xb, L1, L23, phi);
+                link_flux<0, THREE, ext>(S.m(sc, lx - 1, ly), m0, qn, q0, xa, xb, L1, L23, phi, L6);
 #pragma unroll
                 for (int c = 0; c < 5; ++c) grad[c] += phi[c];
                 // (x, x+1)
@@ -969,7 +1140,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                     qn[c] = S.q(sc, c, lx + 1, ly);
                     if (THREE) { xa[c] = xb[c]; xb[c] = S.x(xs, 0, c, lx + 1, ly); }
                 }
-                link_flux<0, THREE>(m0, S.m(sc, lx + 1, ly), q0, qn, xa, xb, L1, L23, phi);
+                link_flux<0, THREE, ext>(m0, S.m(sc, lx + 1, ly), q0, qn, xa, xb, L1, L23, phi, L6);
 #pragma unroll
                 for (int c = 0; c < 5; ++c) grad[c] -= phi[c];
                 // (y-1, y)
@@ -978,7 +1149,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                     qn[c] = S.q(sc, c, lx, ly - 1);
                     if (THREE) { xa[c] = S.x(xs, 1, c, lx, ly - 1); xb[c] = S.x(xs, 1, c, lx, ly); }
                 }
-                link_flux<1, THREE>(S.m(sc, lx, ly - 1), m0, qn, q0, xa, xb, L1, L23, phi);
+                link_flux<1, THREE, ext>(S.m(sc, lx, ly - 1), m0, qn, q0, xa, xb, L1, L23, phi, L6);
 #pragma unroll
                 for (int c = 0; c < 5; ++c) grad[c] += phi[c];
                 // (y, y+1)
@@ -987,9 +1158,19 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                     qn[c] = S.q(sc, c, lx, ly + 1);
                     if (THREE) { xa[c] = xb[c]; xb[c] = S.x(xs, 1, c, lx, ly + 1); }
                 }
-                link_flux<1, THREE>(m0, S.m(sc, lx, ly + 1), q0, qn, xa, xb, L1, L23, phi);
+                link_flux<1, THREE, ext>(m0, S.m(sc, lx, ly + 1), q0, qn, xa, xb, L1, L23, phi, L6);
 #pragma unroll
                 for (int c = 0; c < 5; ++c) grad[c] -= phi[c];
+                if (ext) {
+                    // the site's own Q in the chiral and cubic terms
+                    T sq[3] = {mean_sq<0>(S, lx, ly, sc, 0, 0), mean_sq<1>(S, lx, ly, sc, 0, 0),
+                               mean_sq<2>(S, lx, ly, sc, sp, sm)};
+                    T e[5], mz_cur[5];
+                    mean_diff<2>(S, lx, ly, sc, sp, sm, mz_cur);
+                    jt_extra_local(mx_cur, my_cur, mz_cur, sq, L4, L6, e);
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) grad[c] += e[c];
+                }
                 if (!THREE) {
                     T j[5];
                     jt_sym(grad, j);
@@ -1008,6 +1189,10 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
             S.load5(sc, lx, ly, q0);
             q_values(q0, qv);
             bulk_force(qv, args.A, args.B, args.C, fb);
+            if (args.fields) {
+#pragma unroll
+                for (int c = 0; c < 5; ++c) fb[c] += args.fext[c];
+            }
             add5(Fd, fb, Fn);
             if (m0 & M_ANCH) {
                 const AnchorRec<T> *r = find_record<T>(args.g, L, gx, gy, z);
@@ -1072,7 +1257,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
 
 
 // one FIRE iteration of one lattice: one block per tile and z chunk
-template <typename T, bool THREE, int TX, int TY, typename I>
+template <typename T, int FORM, int TX, int TY, typename I>
 __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 512 / (TX * TY) : 1)
 fire_step_kernel(StepArgs<T> args) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1082,15 +1267,15 @@ fire_step_kernel(StepArgs<T> args) {
     const int z1 = min(z0 + args.zchunk, args.L.nz);
     const int nblk = gridDim.x * gridDim.y * gridDim.z;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    step_tile<T, THREE, TX, TY, I>(args, blockIdx.x, blockIdx.y, z0, z1, nblk, bid, smem_raw, red,
-                                   &am_last);
+    step_tile<T, FORM, TX, TY, I>(args, blockIdx.x, blockIdx.y, z0, z1, nblk, bid, smem_raw, red,
+                                  &am_last);
 }
 
 // one FIRE iteration of every lattice of a batch: a persistent grid strides
 // over the work items (lattice, tile, z chunk); each lattice keeps its own
 // partial sums, last-block ticket and FIRE state, so a lattice advances
 // exactly as it would alone with the same tile and z chunk
-template <typename T, bool THREE, int TX, int TY, typename I>
+template <typename T, int FORM, int TX, int TY, typename I>
 __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 512 / (TX * TY) : 1)
 fire_batch_kernel(const StepArgs<T> *__restrict__ args, const WorkItem *__restrict__ items,
                   int nitems) {
@@ -1099,8 +1284,8 @@ fire_batch_kernel(const StepArgs<T> *__restrict__ args, const WorkItem *__restri
     __shared__ int am_last;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const WorkItem w = items[it];
-        step_tile<T, THREE, TX, TY, I>(args[w.lattice], w.bx, w.by, w.z0, w.z1, w.nblk, w.bid,
-                                       smem_raw, red, &am_last);
+        step_tile<T, FORM, TX, TY, I>(args[w.lattice], w.bx, w.by, w.z0, w.z1, w.nblk, w.bid,
+                                      smem_raw, red, &am_last);
         __syncthreads();   // shared memory is reused by the next item
     }
 }
@@ -1128,6 +1313,12 @@ static void pack_args(const StepLaunch &sl, StepArgs<T> &a) {
     a.L = sl.L;
     a.A = T(sl.A); a.B = T(sl.B); a.C = T(sl.C);
     a.L1 = T(sl.L1); a.L2 = T(sl.L2); a.L3 = T(sl.L3); a.S0 = T(sl.S0);
+    a.L4 = T(sl.L4); a.L6 = T(sl.L6);
+    a.fields = 0;
+    for (int c = 0; c < 5; ++c) {
+        a.fext[c] = T(sl.fext[c]);
+        a.fields |= sl.fext[c] != 0.0;
+    }
     a.st = sl.st;
     a.partials = sl.partials;
     a.zchunk = sl.zchunk;
@@ -1138,12 +1329,12 @@ static void pack_args(const StepLaunch &sl, StepArgs<T> &a) {
 // than 2^32 elements (5 N < 2^32, N < 858,993,459 sites, about 950^3)
 bool step_index32(long long N) { return 5 * N < (1LL << 32); }
 
-template <typename T, bool THREE, int TX, int TY, typename I>
+template <typename T, int FORM, int TX, int TY, typename I>
 static cudaError_t launch_impl(const StepLaunch &sl, cudaStream_t stream) {
     StepArgs<T> a;
     pack_args<T>(sl, a);
-    size_t smem = step_smem_bytes<T, THREE, TX, TY>();
-    auto kern = fire_step_kernel<T, THREE, TX, TY, I>;
+    size_t smem = step_smem_bytes<T, (FORM >= 1), TX, TY>();
+    auto kern = fire_step_kernel<T, FORM, TX, TY, I>;
     dim3 grid = step_grid(sl.L, sl.zchunk, TX, TY);
     kern<<<grid, TX * TY, smem, stream>>>(a);
     return cudaGetLastError();
@@ -1161,56 +1352,55 @@ void step_tile(int fp32, int three, int *tx, int *ty) {
     *ty = fp32 ? 4 : 8;
 }
 
-// calls F::template run<T, THREE, TY, I>() for the form, tile height and
-// index width of a launch
-template <int TY, typename F>
-static auto dispatch_ty(int fp32, int three, bool idx32, F &&f) {
-    if (fp32) {
-        if (three) return idx32 ? f.template run<float, true, TY, unsigned>() : f.template run<float, true, TY, long long>();
-        return idx32 ? f.template run<float, false, TY, unsigned>() : f.template run<float, false, TY, long long>();
-    }
-    if (three) return idx32 ? f.template run<double, true, TY, unsigned>() : f.template run<double, true, TY, long long>();
-    return idx32 ? f.template run<double, false, TY, unsigned>() : f.template run<double, false, TY, long long>();
+// calls F::template run<T, FORM, TY, I>() for the precision, distortion form
+// (0 one-constant, 1 three-constant, 2 with chiral / cubic terms), tile
+// height and index width of a launch
+template <typename T, int TY, typename F>
+static auto dispatch_form(int form, bool idx32, F &&f) {
+    if (form == 2) return idx32 ? f.template run<T, 2, TY, unsigned>() : f.template run<T, 2, TY, long long>();
+    if (form == 1) return idx32 ? f.template run<T, 1, TY, unsigned>() : f.template run<T, 1, TY, long long>();
+    return idx32 ? f.template run<T, 0, TY, unsigned>() : f.template run<T, 0, TY, long long>();
 }
 template <typename F>
-static auto dispatch(int fp32, int three, int ty, bool idx32, F &&f) {
-    return ty == 4 ? dispatch_ty<4>(fp32, three, idx32, f) : dispatch_ty<8>(fp32, three, idx32, f);
+static auto dispatch(int fp32, int form, int ty, bool idx32, F &&f) {
+    if (fp32) return ty == 4 ? dispatch_form<float, 4>(form, idx32, f) : dispatch_form<float, 8>(form, idx32, f);
+    return ty == 4 ? dispatch_form<double, 4>(form, idx32, f) : dispatch_form<double, 8>(form, idx32, f);
 }
-// the single-lattice kernel: each form at its own tile height (step_tile)
+// the single-lattice kernel: each precision at its own tile height (step_tile)
 template <typename F>
-static auto dispatch_single(int fp32, int three, bool idx32, F &&f) {
-    if (fp32) {
-        if (three) return idx32 ? f.template run<float, true, 4, unsigned>() : f.template run<float, true, 4, long long>();
-        return idx32 ? f.template run<float, false, 4, unsigned>() : f.template run<float, false, 4, long long>();
-    }
-    if (three) return idx32 ? f.template run<double, true, 8, unsigned>() : f.template run<double, true, 8, long long>();
-    return idx32 ? f.template run<double, false, 8, unsigned>() : f.template run<double, false, 8, long long>();
+static auto dispatch_single(int fp32, int form, bool idx32, F &&f) {
+    if (fp32) return dispatch_form<float, 4>(form, idx32, f);
+    return dispatch_form<double, 8>(form, idx32, f);
 }
 
 struct PrepareStep {
-    template <typename T, bool THREE, int TY, typename I>
+    template <typename T, int FORM, int TY, typename I>
     cudaError_t run() {
-        return cudaFuncSetAttribute(fire_step_kernel<T, THREE, 32, TY, I>,
+        return cudaFuncSetAttribute(fire_step_kernel<T, FORM, 32, TY, I>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)step_smem_bytes<T, THREE, 32, TY>());
+                                    (int)step_smem_bytes<T, (FORM >= 1), 32, TY>());
     }
 };
 
 cudaError_t prepare_fire_step(int fp32, int three) {
-    cudaError_t e = dispatch_single(fp32, three, true, PrepareStep{});
-    if (e != cudaSuccess) return e;
-    return dispatch_single(fp32, three, false, PrepareStep{});
+    cudaError_t e = cudaSuccess;
+    const int forms[2] = {three ? 1 : 0, three ? 2 : 0};
+    for (int form : forms)
+        for (bool i32 : {true, false})
+            if (e == cudaSuccess) e = dispatch_single(fp32, form, i32, PrepareStep{});
+    return e;
 }
 
 struct LaunchStep {
     const StepLaunch &sl;
     cudaStream_t stream;
-    template <typename T, bool THREE, int TY, typename I>
-    cudaError_t run() { return launch_impl<T, THREE, 32, TY, I>(sl, stream); }
+    template <typename T, int FORM, int TY, typename I>
+    cudaError_t run() { return launch_impl<T, FORM, 32, TY, I>(sl, stream); }
 };
 
 cudaError_t launch_fire_step(const StepLaunch &sl, cudaStream_t stream) {
-    return dispatch_single(sl.fp32, sl.three, step_index32(sl.L.N), LaunchStep{sl, stream});
+    const int form = sl.three ? (sl.ext ? 2 : 1) : 0;
+    return dispatch_single(sl.fp32, form, step_index32(sl.L.N), LaunchStep{sl, stream});
 }
 
 // ---- batched launches ----------------------------------------------------------
@@ -1223,20 +1413,20 @@ void step_args_pack(const StepLaunch &sl, void *out) {
 }
 
 struct PrepareBatch {
-    template <typename T, bool THREE, int TY, typename I>
+    template <typename T, int FORM, int TY, typename I>
     cudaError_t run() {
-        return cudaFuncSetAttribute(fire_batch_kernel<T, THREE, 32, TY, I>,
+        return cudaFuncSetAttribute(fire_batch_kernel<T, FORM, 32, TY, I>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)step_smem_bytes<T, THREE, 32, TY>());
+                                    (int)step_smem_bytes<T, (FORM >= 1), 32, TY>());
     }
 };
 
 struct BlocksBatch {
-    template <typename T, bool THREE, int TY, typename I>
+    template <typename T, int FORM, int TY, typename I>
     int run() {
         int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fire_batch_kernel<T, THREE, 32, TY, I>,
-                                                      32 * TY, step_smem_bytes<T, THREE, 32, TY>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fire_batch_kernel<T, FORM, 32, TY, I>,
+                                                      32 * TY, step_smem_bytes<T, (FORM >= 1), 32, TY>());
         return nb;
     }
 };
@@ -1246,25 +1436,26 @@ struct LaunchBatch {
     const WorkItem *items;
     int nitems, grid;
     cudaStream_t stream;
-    template <typename T, bool THREE, int TY, typename I>
+    template <typename T, int FORM, int TY, typename I>
     cudaError_t run() {
-        fire_batch_kernel<T, THREE, 32, TY, I><<<grid, 32 * TY, step_smem_bytes<T, THREE, 32, TY>(), stream>>>(
-            static_cast<const StepArgs<T> *>(args), items, nitems);
+        fire_batch_kernel<T, FORM, 32, TY, I><<<grid, 32 * TY, step_smem_bytes<T, (FORM >= 1), 32, TY>(),
+                                                stream>>>(static_cast<const StepArgs<T> *>(args), items,
+                                                          nitems);
         return cudaGetLastError();
     }
 };
 
-cudaError_t prepare_fire_batch(int fp32, int three, int ty, int idx32) {
-    return dispatch(fp32, three, ty, idx32 != 0, PrepareBatch{});
+cudaError_t prepare_fire_batch(int fp32, int form, int ty, int idx32) {
+    return dispatch(fp32, form, ty, idx32 != 0, PrepareBatch{});
 }
 
-int fire_batch_blocks_per_sm(int fp32, int three, int ty, int idx32) {
-    return dispatch(fp32, three, ty, idx32 != 0, BlocksBatch{});
+int fire_batch_blocks_per_sm(int fp32, int form, int ty, int idx32) {
+    return dispatch(fp32, form, ty, idx32 != 0, BlocksBatch{});
 }
 
-cudaError_t launch_fire_batch(int fp32, int three, int ty, int idx32, const void *dev_args,
+cudaError_t launch_fire_batch(int fp32, int form, int ty, int idx32, const void *dev_args,
                               const WorkItem *items, int nitems, int grid, cudaStream_t stream) {
-    return dispatch(fp32, three, ty, idx32 != 0, LaunchBatch{dev_args, items, nitems, grid, stream});
+    return dispatch(fp32, form, ty, idx32 != 0, LaunchBatch{dev_args, items, nitems, grid, stream});
 }
 
 __global__ void k_batch_running(FireDev *const *states, int n, unsigned int *running) {

@@ -55,7 +55,9 @@ class Lattice(C.Structure):
 class Material(C.Structure):
     _fields_ = [("A", C.c_double), ("B", C.c_double), ("C", C.c_double), ("L1", C.c_double),
                 ("L2", C.c_double), ("L3", C.c_double), ("L4", C.c_double), ("L6", C.c_double),
-                ("n_constants", C.c_int), ("S0", C.c_double)]
+                ("n_constants", C.c_int), ("S0", C.c_double),
+                ("H", C.c_double * 3), ("mu0_dchi", C.c_double),
+                ("E", C.c_double * 3), ("eps0_deps", C.c_double)]
 
 
 class Anchoring(C.Structure):
@@ -193,15 +195,18 @@ class Solver:
     """One lattice on the current CUDA device (see ``lq_create``)."""
 
     def __init__(self, shape, A, B, C_, L1, L2=0.0, L3=0.0, periodic=(1, 1, 1), precision=LQ_FP64,
-                 stream=None, n_constants=None, S0=0.0):
+                 stream=None, n_constants=None, S0=0.0, L4=0.0, L6=0.0, H=(0.0, 0.0, 0.0),
+                 mu0_dchi=0.0, E=(0.0, 0.0, 0.0), eps0_deps=0.0):
         lib = load()
         nx, ny, nz = (int(v) for v in shape)
         self.shape = (nx, ny, nz)
         self.N = nx * ny * nz
         lat = Lattice(nx, ny, nz, 1.0, (C.c_int * 3)(*[int(bool(p)) for p in periodic]))
         if n_constants is None:
-            n_constants = 1 if (L2 == 0.0 and L3 == 0.0) else 3
-        mat = Material(A, B, C_, L1, L2, L3, 0.0, 0.0, n_constants, S0)
+            n_constants = 1 if (L2 == 0.0 and L3 == 0.0 and L4 == 0.0 and L6 == 0.0) else 3
+        mat = Material(A, B, C_, L1, L2, L3, L4, L6, n_constants, S0,
+                       (C.c_double * 3)(*[float(v) for v in H]), float(mu0_dchi),
+                       (C.c_double * 3)(*[float(v) for v in E]), float(eps0_deps))
         h = C.c_void_p()
         st = lib.lq_create(C.byref(lat), C.byref(mat), int(precision),
                            C.c_void_p(stream) if stream else None, C.byref(h))

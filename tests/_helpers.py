@@ -17,14 +17,17 @@ def need_gpu():
 
 
 def make_pair(oracle_mod, shape, L=(2.32, 0.0, 0.0), objects=(), periodic=(1, 1, 1),
-              precision=0, A=synth.A_5CB, B=synth.B_5CB, C=synth.C_5CB, zchunk=0):
+              precision=0, A=synth.A_5CB, B=synth.B_5CB, C=synth.C_5CB, zchunk=0, **extra):
+    """CUDA solver and oracle on the same lattice, material and objects;
+    ``extra``: L4, L6, H, mu0_dchi, E, eps0_deps."""
     from paper_1911_07045_b300 import lqmin
     L1, L2, L3 = L
-    s = lqmin.Solver(shape, A, B, C, L1, L2, L3, periodic=periodic, precision=precision)
+    s = lqmin.Solver(shape, A, B, C, L1, L2, L3, periodic=periodic, precision=precision, **extra)
     s.add_objects(list(objects))
     if zchunk:
         s.set_zchunk(zchunk)
-    o = oracle_mod.Oracle(shape, A, B, C, L1, L2, L3, periodic=periodic, objects=list(objects))
+    o = oracle_mod.Oracle(shape, A, B, C, L1, L2, L3, periodic=periodic, objects=list(objects),
+                          **extra)
     return s, o
 
 
