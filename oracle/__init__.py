@@ -23,7 +23,7 @@ _HDR = os.path.join(_HERE, "lqoracle.h")
 _LIB = os.path.join(_HERE, "liblqoracle.so")
 
 ND_HOMEOTROPIC, ND_ORIENTED, FG_PLANAR = 0, 1, 2
-WALL, SPHERE, SITES, ANCHORED = 0, 1, 2, 3
+WALL, SPHERE, SITES, ANCHORED, DROPLET, SPHEROCYLINDER = 0, 1, 2, 3, 4, 5
 RUNNING, CONVERGED, MAXITER, DIVERGED = 0, 1, 2, 3
 
 
@@ -80,7 +80,7 @@ class _Object(C.Structure):
                 ("c", C.c_double * 3), ("R", C.c_double),
                 ("n", C.c_int64), ("xyz", C.POINTER(C.c_int32)),
                 ("per_site", C.POINTER(_AnchorSpec)),
-                ("anch", _AnchorSpec)]
+                ("anch", _AnchorSpec), ("c2", C.c_double * 3)]
 
 
 class _Anchor(C.Structure):
@@ -184,7 +184,7 @@ class Oracle:
         objs = (_Object * max(1, len(objects)))()
         for o, spec in zip(objs, objects):
             t = spec["type"]
-            if t in ("wall", "sphere", "sites"):
+            if t in ("wall", "sphere", "sites", "droplet", "spherocylinder"):
                 kind, W, dr = spec.get("anchor", (ND_HOMEOTROPIC, 0.0, (0, 0, 1)))
                 o.anch = _AnchorSpec(kind, W, (C.c_double * 3)(*dr))
             if t == "wall":
@@ -192,6 +192,13 @@ class Oracle:
             elif t == "sphere":
                 o.type, o.R = SPHERE, spec["R"]
                 o.c = (C.c_double * 3)(*spec["c"])
+            elif t == "droplet":
+                o.type, o.R = DROPLET, spec["R"]
+                o.c = (C.c_double * 3)(*spec["c"])
+            elif t == "spherocylinder":
+                o.type, o.R = SPHEROCYLINDER, spec["R"]
+                o.c = (C.c_double * 3)(*spec["c"])
+                o.c2 = (C.c_double * 3)(*spec["c2"])
             elif t in ("sites", "anchored"):
                 xyz = np.ascontiguousarray(spec["xyz"], dtype=np.int32).reshape(-1, 3)
                 self._keep.append(xyz)

@@ -495,6 +495,24 @@ typedef struct {
     int32_t *listed; /* SITES / ANCHORED: per-site list position, -1 if absent */
 } obj_aux;
 
+/* offset of site c from the nearest point of the segment o->c .. o->c2:
+   d = site - midpoint (minimum image), a = c2 - c, nearest point at
+   midpoint + t a with t = clamp(d.a / a.a, -1/2, 1/2) */
+static void capsule_offset(const orc_model *m, const orc_object *o, const int c[3], double r[3]) {
+    double d[3], a[3], aa = 0.0, da = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double mid = (o->c[k] + o->c2[k]) * 0.5;
+        d[k] = disp(m, k, c[k] - mid);
+        a[k] = o->c2[k] - o->c[k];
+        aa += a[k] * a[k];
+        da += d[k] * a[k];
+    }
+    double t = aa > 0.0 ? da / aa : 0.0;
+    if (t < -0.5) t = -0.5;
+    if (t > 0.5) t = 0.5;
+    for (int k = 0; k < 3; ++k) r[k] = d[k] - t * a[k];
+}
+
 static int in_object(const orc_model *m, const orc_object *o, const obj_aux *ax,
                      int64_t i) {
     int c[3];
@@ -510,6 +528,19 @@ static int in_object(const orc_model *m, const orc_object *o, const obj_aux *ax,
         return r2 <= o->R * o->R;
     }
     case ORC_SITES: return ax->listed[i] >= 0;
+    case ORC_DROPLET: {
+        double r2 = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            double d = disp(m, k, c[k] - o->c[k]);
+            r2 += d * d;
+        }
+        return r2 > o->R * o->R;
+    }
+    case ORC_SPHEROCYLINDER: {
+        double r[3];
+        capsule_offset(m, o, c, r);
+        return r[0] * r[0] + r[1] * r[1] + r[2] * r[2] <= o->R * o->R;
+    }
     default: return 0;
     }
 }
@@ -608,8 +639,10 @@ int orc_build_geometry(const orc_model *m, const orc_object *objs, int nobj,
         coords(m, i, c);
         if (ob->type == ORC_WALL) {
             normal[ob->axis] = 1.0;
-        } else if (ob->type == ORC_SPHERE) {
+        } else if (ob->type == ORC_SPHERE || ob->type == ORC_DROPLET) {
             for (int k = 0; k < 3; ++k) normal[k] = disp(m, k, c[k] - ob->c[k]);
+        } else if (ob->type == ORC_SPHEROCYLINDER) {
+            capsule_offset(m, ob, c, normal);
         } else if (ob->type == ORC_SITES) {
             for (int k = 0; k < 3; ++k) normal[k] = sp->dir[k];
         } else {

@@ -39,7 +39,8 @@ typedef struct {
 /* anchoring kinds, boundary free energy of section II */
 enum { ORC_ND_HOMEOTROPIC = 0, ORC_ND_ORIENTED = 1, ORC_FG_PLANAR = 2 };
 /* object kinds */
-enum { ORC_WALL = 0, ORC_SPHERE = 1, ORC_SITES = 2, ORC_ANCHORED = 3 };
+enum { ORC_WALL = 0, ORC_SPHERE = 1, ORC_SITES = 2, ORC_ANCHORED = 3, ORC_DROPLET = 4,
+       ORC_SPHEROCYLINDER = 5 };
 
 typedef struct { int kind; double W; double dir[3]; } orc_anchor_spec;
 
@@ -51,7 +52,12 @@ typedef struct {
     const int32_t *xyz;       /* SITES / ANCHORED: 3*n coordinates */
     const orc_anchor_spec *per_site; /* ANCHORED: n specs */
     orc_anchor_spec anch;     /* WALL / SPHERE / SITES: anchoring of the surface */
+    double c2[3];             /* SPHEROCYLINDER: second end of the axis segment (c the first) */
 } orc_object;
+/* DROPLET: the nematic fills the ball |x - c| <= R (minimum image along
+   periodic axes); every site outside is an object site; surface normal
+   x - c.  SPHEROCYLINDER: object sites within R of the segment c..c2 (a
+   capsule, Fig. 3); normal from the nearest point of the segment. */
 
 /* resolved per-site anchoring record */
 typedef struct {

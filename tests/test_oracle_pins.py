@@ -460,6 +460,106 @@ def test_geometry_sphere_and_walls(oracle_mod):
     assert np.array_equal(np.sort(sites), np.nonzero((touched & sim).ravel())[0])
 
 
+def _face_touched(obj):
+    """Sites with a face neighbour in ``obj`` (periodic rolls; [z, y, x] arrays)."""
+    t = np.zeros_like(obj)
+    for ax in range(3):
+        for sh in (1, -1):
+            t |= np.roll(obj, sh, axis=ax)
+    return t
+
+
+def _segment_distance_sampled(P, p0, p1, shape, periodic, n=801):
+    """Distance of the points P (m, 3) to the segment p0..p1 over all periodic
+    images, by sampling the segment at n points (an independent route to the
+    nearest point) -- returns the distance and the offset to the sampled
+    nearest point."""
+    ts = np.linspace(0.0, 1.0, n)
+    seg = np.asarray(p0)[None, :] + ts[:, None] * (np.asarray(p1) - np.asarray(p0))[None, :]
+    L = np.asarray(shape, dtype=float)
+    best = np.full(len(P), np.inf)
+    off = np.zeros((len(P), 3))
+    shifts = [[-1, 0, 1] if p else [0] for p in periodic]
+    for img in np.array(np.meshgrid(*shifts)).reshape(3, -1).T:
+        d = P[:, None, :] + img * L - seg[None, :, :]
+        r = np.sqrt((d * d).sum(2))
+        k = r.argmin(1)
+        rk = r[np.arange(len(P)), k]
+        better = rk < best
+        best[better] = rk[better]
+        off[better] = d[np.arange(len(P)), k][better]
+    return best, off
+
+
+def test_geometry_droplet_is_the_complement_of_a_sphere(oracle_mod):
+    """A droplet (Fig. 3) of radius R about c fills exactly the sites a sphere
+    of the same c and R removes, wrapping across periodic faces; its boundary
+    sites are the ball's sites with a face neighbour outside, anchored along
+    the radius."""
+    L = 14
+    for c, R in (((6.5, 7.0, 6.2), 5.3), ((1.0, 7.0, 12.5), 4.5)):
+        drop = oracle_mod.Oracle((L, L, L), A, B, C, 1.0, objects=[
+            dict(type="droplet", c=c, R=R, anchor=HOM(2.0))])
+        sph = oracle_mod.Oracle((L, L, L), A, B, C, 1.0, objects=[
+            dict(type="sphere", c=c, R=R, anchor=HOM(2.0))])
+        assert np.array_equal(drop.simulated(), ~sph.simulated())
+        sim = drop.simulated().reshape(L, L, L)
+        assert abs(sim.sum() - 4 / 3 * np.pi * R ** 3) < 0.15 * 4 / 3 * np.pi * R ** 3
+        sites, kind, W, q0, nu = drop.records()
+        assert np.array_equal(np.sort(sites), np.nonzero((_face_touched(~sim) & sim).ravel())[0])
+        for s, qq in zip(sites, q0):
+            x, y, z = s % L, (s // L) % L, s // (L * L)
+            d = np.array([x - c[0], y - c[1], z - c[2]])
+            d -= L * np.round(d / L)
+            assert np.allclose(qq, synth.uniaxial_q((d / np.linalg.norm(d))[:, None], drop.S0)[:, 0],
+                               atol=1e-14)
+    # a droplet larger than the lattice's inscribed ball's diagonal is the bulk
+    big = oracle_mod.Oracle((6, 5, 4), A, B, C, 1.0, objects=[
+        dict(type="droplet", c=(3.0, 2.0, 2.0), R=5.0, anchor=HOM(2.0))])
+    assert big.simulated().all() and len(big.records()[0]) == 0
+
+
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 1, 0)])
+def test_geometry_spherocylinder_against_sampled_segment(oracle_mod, periodic):
+    """Object sites of a spherocylinder (Fig. 3) are the sites within R of its
+    axis segment, found here by sampling the segment over all periodic
+    images; boundary normals point from the nearest axis point to the site."""
+    shape = (20, 13, 11)
+    p0, p1, R = (4.3, 5.1, 4.0), (14.6, 8.2, 6.7), 2.6
+    o = oracle_mod.Oracle(shape, A, B, C, 1.0, periodic=periodic, objects=[
+        dict(type="spherocylinder", c=p0, c2=p1, R=R, anchor=HOM(2.0))])
+    nx, ny, nz = shape
+    zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    P = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], 1).astype(float)
+    dist, off = _segment_distance_sampled(P, p0, p1, shape, periodic)
+    sim = o.simulated()
+    clear = np.abs(dist - R) > 1e-3
+    assert clear.sum() > 0.95 * len(P)
+    assert np.array_equal(sim[clear], (dist > R)[clear])
+    assert 0.7 * (np.pi * R * R * np.linalg.norm(np.subtract(p1, p0)) + 4 / 3 * np.pi * R ** 3) \
+        < (~sim).sum() < 1.3 * (np.pi * R * R * np.linalg.norm(np.subtract(p1, p0)) +
+                                4 / 3 * np.pi * R ** 3)
+    sites, kind, W, q0, nu = o.records()
+    assert len(sites) > 50
+    for s, qq in zip(sites, q0):
+        n = off[s] / np.linalg.norm(off[s])
+        ref = synth.uniaxial_q(n[:, None], o.S0)[:, 0]
+        assert np.abs(qq - ref).max() < 2e-3
+
+
+def test_geometry_spherocylinder_of_zero_length_is_a_sphere(oracle_mod):
+    shape = (13, 12, 11)
+    for c, R in (((6.0, 5.5, 5.2), 3.3), ((0.5, 11.0, 5.0), 2.8)):
+        a = oracle_mod.Oracle(shape, A, B, C, 1.0, objects=[
+            dict(type="spherocylinder", c=c, c2=c, R=R, anchor=(2, 1.5, (0.0, 0.0, 1.0)))])
+        b = oracle_mod.Oracle(shape, A, B, C, 1.0, objects=[
+            dict(type="sphere", c=c, R=R, anchor=(2, 1.5, (0.0, 0.0, 1.0)))])
+        assert np.array_equal(a.simulated(), b.simulated())
+        ra, rb = a.records(), b.records()
+        for u, v in zip(ra, rb):
+            assert np.array_equal(u, v)
+
+
 # ---- FIRE ---------------------------------------------------------------------------------
 
 FP = dict(dt0=0.1, dt_max=0.25, alpha0=0.2, f_alpha=0.5, f_inc=2.0, f_dec=0.5, n_min=2,
