@@ -156,7 +156,8 @@ typedef struct {
    lq_precision.
    Allocates the device state: 2 x (q, v, F) buffers, 1-byte site masks and
    the FIRE reduction scratch.  LQ_EINVAL for non-positive sizes, spacing
-   != 1, L4/L6 != 0, or n_constants not 1 or 3. */
+   != 1, n_constants not 1 or 3, L2..L6 != 0 with n_constants 1, or A, B, C
+   without a nematic minimum (when S0 <= 0). */
 lq_status lq_create(const lq_lattice *lattice, const lq_material *material,
                     int precision, void *cuda_stream, lq_solver **out);
 /* Free all device and host memory of the solver (NULL is accepted). */
@@ -176,6 +177,20 @@ lq_status lq_add_wall(lq_solver *s, int axis, int plane, const lq_anchoring *a);
    are object sites; boundary normal (x - c)/|x - c|. */
 lq_status lq_add_sphere(lq_solver *s, const double c[3], double radius,
                         const lq_anchoring *a);
+/* Droplet (Fig. 3, the confining shell of a drop): every site with
+   |x - c|^2 > R^2 (minimum image) is an object site, so the liquid crystal
+   fills the ball; boundary normal (x - c)/|x - c|, pointing out of the drop.
+   LQ_EINVAL for radius <= 0. */
+lq_status lq_add_droplet(lq_solver *s, const double c[3], double radius,
+                         const lq_anchoring *a);
+/* Spherocylinder (Fig. 3): sites within distance R of the segment p0..p1
+   are object sites; boundary normal x - p*, p* the nearest point of the
+   segment.  Distances are taken from the segment's midpoint with the
+   minimum image along periodic axes, so the object must fit in the box
+   (|p1 - p0|/2 + R below half the period).  p0 == p1 is a sphere.
+   LQ_EINVAL for radius < 0. */
+lq_status lq_add_spherocylinder(lq_solver *s, const double p0[3], const double p1[3],
+                                double radius, const lq_anchoring *a);
 /* Custom object: the n listed sites (xyz[3*t..3*t+2]) become object sites;
    their simulated face neighbours take anchoring a (dir used as normal).
    Sites outside the lattice are ignored. */
@@ -186,6 +201,65 @@ lq_status lq_add_object_sites(lq_solver *s, int64_t n, const int32_t *xyz,
    When several objects claim a boundary site, the first one added wins. */
 lq_status lq_add_anchored_sites(lq_solver *s, int64_t n, const int32_t *xyz,
                                 const lq_anchoring *per_site);
+/* Custom boundary text (section VI: objects made of arbitrary site sets,
+   each boundary site with its own homeotropic or planar anchoring, read
+   from a prepared text file).  The format of this library:
+     - '#' starts a comment; blank lines are skipped; tokens are separated
+       by blanks;
+     - a block "object <anchoring> <W> [dx dy dz]" ... "end" lists object
+       sites, one "x y z" per line; their simulated face neighbours take the
+       anchoring (as lq_add_object_sites, dir = (dx, dy, dz), default
+       (0, 0, 1));
+     - a block "boundary" ... "end" lists anchored sites, one
+       "x y z <anchoring> <W> dx dy dz" per line (as lq_add_anchored_sites);
+     - <anchoring> is homeotropic | oriented | planar (or 0 | 1 | 2, the
+       lq_anchor_kind values); W >= 0.
+   Blocks become objects in file order.  The whole text is checked before
+   anything is added: on any error nothing changes and the message names
+   the line.  lq_boundary_check parses without a solver (no device work)
+   and reports the number of blocks and of site lines; err (errlen bytes,
+   may be NULL) receives the message. */
+lq_status lq_boundary_check(const char *text, int64_t *n_blocks, int64_t *n_sites,
+                            char *err, size_t errlen);
+lq_status lq_add_boundary_text(lq_solver *s, const char *text);
+/* The same read from a file (LQ_EINVAL if it cannot be read). */
+lq_status lq_load_boundary_file(lq_solver *s, const char *path);
+/* Objects added so far (their index order is the order of addition). */
+lq_status lq_object_count(lq_solver *s, int *n);
+/* Move object `index` by shift (section VI: objects repositioned and the
+   liquid crystal re-minimised).  Spheres, droplets and spherocylinders move
+   by any shift; walls by whole planes along their axis (other components
+   ignored); site lists by whole lattice vectors, wrapping periodic axes.
+   Sites the object leaves become simulated with Q = 0; sites it covers
+   become object sites.  The minimiser restarts at the next step. */
+lq_status lq_move_object(lq_solver *s, int index, const double shift[3]);
+/* Remove every object (Q on the freed sites is 0). */
+lq_status lq_clear_objects(lq_solver *s);
+/* Change the material constants of a live solver (section VI: energy terms
+   changed between minimisations).  Same rules as lq_create; Q is kept, the
+   anchoring targets follow the new S0 and the minimiser restarts at the
+   next step. */
+lq_status lq_set_material(lq_solver *s, const lq_material *material);
+/* A new solver (on cuda_stream, NULL = its own) with the same lattice,
+   material, precision, objects and current Q as src. */
+lq_status lq_clone(lq_solver *src, void *cuda_stream, lq_solver **out);
+/* Potential-of-mean-force sweep (section VI): for each k < n a clone of
+   base with object `index` moved by shifts[3k..3k+2] starts from base's
+   current Q (freed sites 0), and all n are minimised together in one batch
+   (lq_batch_minimize; n results with the energy at the minimum).  base is
+   not modified.  Returns what lq_batch_minimize returns. */
+lq_status lq_pmf_sweep(lq_solver *base, int index, int n, const double *shifts,
+                       const lq_fire_params *p, lq_result *out);
+/* Dipolar start about a homeotropic colloid (section IV.A, the dipolar
+   initial condition after Lubensky et al.): a radial hedgehog at c and a
+   hyperbolic hedgehog at h = c + rd a (a = axis / |axis|, also the far-field
+   director), n tilted from a by theta_c - theta_h, the polar angles of the
+   site about a seen from c and from h (minimum image of x - c, w = u - rd a);
+   Q = 3/2 S (n n - I/3) on simulated sites, S <= 0 selecting S0; n = a
+   where the angles are undefined.  Resets the minimiser.  LQ_EINVAL for a
+   zero axis or rd <= 0. */
+lq_status lq_init_dipolar(lq_solver *s, const double c[3], const double axis[3], double rd,
+                          double S);
 /* Number of simulated sites and of sites carrying an anchoring record
    (builds the geometry if it changed). */
 lq_status lq_geometry_info(lq_solver *s, int64_t *n_simulated, int64_t *n_anchored);
@@ -277,15 +351,17 @@ lq_status lq_batch_minimize(lq_batch *b, const lq_fire_params *p, lq_result *out
 /* ---- serving: continuous batching of minimisation requests -------------------------- */
 
 /* An object of a request, the same objects lq_add_* take (section V). */
-enum { LQ_OBJ_WALL = 0, LQ_OBJ_SPHERE = 1, LQ_OBJ_SITES = 2, LQ_OBJ_ANCHORED = 3 };
+enum { LQ_OBJ_WALL = 0, LQ_OBJ_SPHERE = 1, LQ_OBJ_SITES = 2, LQ_OBJ_ANCHORED = 3,
+       LQ_OBJ_DROPLET = 4, LQ_OBJ_SPHEROCYLINDER = 5 };
 typedef struct {
     int type;                       /* LQ_OBJ_* */
     int axis, plane;                /* wall */
-    double c[3], R;                 /* sphere */
-    lq_anchoring anch;              /* wall, sphere, object sites */
+    double c[3], R;                 /* sphere, droplet (centre, radius); spherocylinder (end, radius) */
+    lq_anchoring anch;              /* wall, sphere, droplet, spherocylinder, object sites */
     int64_t n;                      /* site lists: number of sites */
     const int32_t *xyz;             /* site lists: 3n coordinates */
     const lq_anchoring *per_site;   /* anchored sites: n records */
+    double c2[3];                   /* spherocylinder: the other end of its axis */
 } lq_object;
 
 /* One minimisation (section V: set up a lattice and objects, start from a

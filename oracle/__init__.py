@@ -4,7 +4,8 @@ TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
 and the CPU-baseline leg of ``bench.py``; never by the product package.  It
 shares no code with the CUDA path.  The arithmetic lives in ``lqoracle.c``
 (see its header for the paper passages each routine follows); this module
-only marshals numpy arrays through ctypes.
+marshals numpy arrays through ctypes, except for the dipolar initial
+condition (``dipolar_director``), written here in numpy.
 
 Every function is pinned by the ``-m "not gpu"`` tests in ``tests/`` against
 closed forms, invariants, hand-derived values and finite differences.
@@ -166,6 +167,8 @@ class Oracle:
     ``objects`` is a list of dicts, in the order the objects were added:
       {"type": "wall", "axis": k, "plane": p, "anchor": (kind, W, dir)}
       {"type": "sphere", "c": (x, y, z), "R": r, "anchor": (kind, W, dir)}
+      {"type": "droplet", "c": (x, y, z), "R": r, "anchor": ...}   (fills the ball)
+      {"type": "spherocylinder", "c": p0, "c2": p1, "R": r, "anchor": ...}
       {"type": "sites", "xyz": int array (n, 3), "anchor": (kind, W, dir)}
       {"type": "anchored", "xyz": int array (n, 3), "kinds": (n,), "W": (n,), "dirs": (n, 3)}
     ``S0`` defaults to Eq. (S0def) of the bulk constants.
@@ -175,6 +178,8 @@ class Oracle:
                  objects=(), S0=None, L4=0.0, L6=0.0, H=(0.0, 0.0, 0.0), mu0_dchi=0.0,
                  E=(0.0, 0.0, 0.0), eps0_deps=0.0):
         self.nx, self.ny, self.nz = (int(s) for s in shape)
+        self.shape = (self.nx, self.ny, self.nz)
+        self.periodic = tuple(int(bool(p)) for p in periodic)
         self.N = self.nx * self.ny * self.nz
         self.S0 = uniaxial_s0(A, B, C_) if S0 is None else float(S0)
         self.model = _Model(self.nx, self.ny, self.nz, (C.c_int * 3)(*periodic),
@@ -321,6 +326,52 @@ class Oracle:
 
 
 GD, NESTEROV = 1, 2
+
+
+def dipolar_director(u, axis, rd):
+    """Director of the dipolar configuration about a homeotropic colloid
+    (section IV.A, the dipolar start after Lubensky et al.), at offsets u
+    (m, 3) from the colloid centre: a radial hedgehog at the centre and a
+    hyperbolic hedgehog at h = rd a on the axis a.  With theta_c and
+    theta_h the polar angles (about a) of the point seen from the centre
+    and from h, the director is tilted from a by psi = theta_c - theta_h
+    toward the point's radial direction away from the axis:
+    n = cos(psi) a + sin(psi) e_rho.  Far away theta_c ~ theta_h and n -> a;
+    near the centre n ~ u/|u| (radial); near h, n is the hyperbolic
+    hedgehog's reflection of w/|w| through the axis."""
+    a = np.asarray(axis, dtype=np.float64)
+    a = a / np.linalg.norm(a)
+    u = np.atleast_2d(np.asarray(u, dtype=np.float64))
+    w = u - rd * a[None, :]
+    ua, wa = u @ a, w @ a
+    perp = u - ua[:, None] * a[None, :]
+    rho = np.linalg.norm(perp, axis=1)
+    theta_c = np.arctan2(rho, ua)
+    theta_h = np.arctan2(rho, wa)
+    psi = theta_c - theta_h
+    e_rho = np.zeros_like(perp)
+    nz = rho > 0
+    e_rho[nz] = perp[nz] / rho[nz, None]
+    return np.cos(psi)[:, None] * a[None, :] + np.sin(psi)[:, None] * e_rho
+
+
+def dipolar_q(oracle, c, axis, rd, S):
+    """Q = 3/2 S (n n - I/3) of ``dipolar_director`` on the oracle's
+    simulated sites (offsets by the minimum image along periodic axes),
+    zero on object sites; (5, N) like every Q field here."""
+    nx, ny, nz = oracle.shape
+    i = np.arange(oracle.N)
+    xyz = np.stack([i % nx, (i // nx) % ny, i // (nx * ny)], axis=1).astype(np.float64)
+    u = xyz - np.asarray(c, dtype=np.float64)[None, :]
+    for k, n in enumerate((nx, ny, nz)):
+        if oracle.periodic[k]:
+            u[:, k] -= n * np.floor(u[:, k] / n + 0.5)
+    d = dipolar_director(u, axis, rd)
+    q = np.stack([1.5 * S * (d[:, 0] * d[:, 0] - 1.0 / 3.0), 1.5 * S * d[:, 0] * d[:, 1],
+                  1.5 * S * d[:, 0] * d[:, 2], 1.5 * S * (d[:, 1] * d[:, 1] - 1.0 / 3.0),
+                  1.5 * S * d[:, 1] * d[:, 2]])
+    q[:, ~oracle.simulated()] = 0.0
+    return q
 
 
 def fire_params(dt0=1e-3, dt_max=1e-2, alpha0=0.99, f_alpha=0.99, f_inc=1.1, f_dec=0.5,

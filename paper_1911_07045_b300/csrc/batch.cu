@@ -45,6 +45,7 @@ struct lq_batch {
     cudaGraphExec_t gexec = nullptr;
     int graph_k = 0;
     long long sites = 0;
+    std::vector<unsigned long long> gens;   // members' generations the tables were built from
     std::string err;
 };
 
@@ -65,7 +66,7 @@ lq_status bfail(lq_batch *b, lq_status st, const char *msg, cudaError_t e = cuda
             return bfail(b, e_ == cudaErrorMemoryAllocation ? LQ_ENOMEM : LQ_ECUDA, #call, e_); \
     } while (0)
 
-void drop_graph(lq_batch *b) {
+void drop_batch_graph(lq_batch *b) {
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
     b->graph_k = 0;
@@ -128,6 +129,10 @@ lq_status build_items(lq_batch *b, int ty, int zc_all, bool shadow) {
     BK(cudaMemcpyAsync(shadow ? b->shadow_args : b->args, host.data(), host.size(),
                        cudaMemcpyHostToDevice, b->stream));
     BK(cudaStreamSynchronize(b->stream));
+    if (!shadow) {
+        b->gens.resize(b->solvers.size());
+        for (size_t l = 0; l < b->solvers.size(); ++l) b->gens[l] = b->solvers[l]->gen;
+    }
     return LQ_OK;
 }
 
@@ -138,7 +143,7 @@ int persistent_grid(lq_batch *b, int ty) {
 
 lq_status set_tiling(lq_batch *b, int ty, int zc) {
     if (b->tables_ok && b->ty == ty && b->zchunk == zc) return LQ_OK;
-    drop_graph(b);
+    drop_batch_graph(b);
     b->tables_ok = false;
     if (!b->solvers.empty()) {
         lq_status r = build_items(b, ty, zc, false);
@@ -156,7 +161,7 @@ lq_status ensure_graph(lq_batch *b) {
     long long k = (1LL << 24) / std::max(1LL, b->sites);
     int kk = (int)std::max(1LL, std::min(64LL, k));
     if (b->gexec && b->graph_k == kk) return LQ_OK;
-    drop_graph(b);
+    drop_batch_graph(b);
     int grid = persistent_grid(b, b->ty);
     cudaGraph_t g = nullptr;
     BK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
@@ -189,6 +194,15 @@ lq_status prepare_run(lq_batch *b, const lq_fire_params *p, bool reset) {
         }
         if (r != LQ_OK) return bfail(b, r, s->err.c_str());
         cudaStreamSynchronize(s->stream);
+    }
+    // a member whose geometry or material changed since the tables were
+    // built: its records moved, its form may differ -- rebuild the tables
+    bool stale = b->gens.size() != b->solvers.size();
+    for (size_t l = 0; l < b->solvers.size() && !stale; ++l) stale = b->gens[l] != b->solvers[l]->gen;
+    if (stale) {
+        std::vector<lq_solver *> members = b->solvers;
+        lq_status r = batch_set_members(b, members.data(), (int)members.size());
+        if (r != LQ_OK) return r;
     }
     return LQ_OK;
 }
@@ -246,7 +260,7 @@ lq_status batch_set_members(lq_batch *b, lq_solver *const *solvers, int n) {
             solvers[l]->three != b->three)
             return bfail(b, LQ_EINVAL, "one device, one precision, one distortion form per batch");
     cudaSetDevice(b->device);
-    drop_graph(b);
+    drop_batch_graph(b);
     b->tables_ok = false;
     b->solvers.assign(solvers, solvers + n);
     b->sites = 0;
@@ -326,7 +340,7 @@ void lq_batch_destroy(lq_batch *b) {
     if (!b) return;
     cudaSetDevice(b->device);
     if (b->stream) cudaStreamSynchronize(b->stream);
-    drop_graph(b);
+    drop_batch_graph(b);
     cudaFree(b->args); cudaFree(b->shadow_args); cudaFree(b->shadow); cudaFree(b->items);
     cudaFree(b->partials); cudaFree(b->states); cudaFree(b->running);
     if (b->running_host) cudaFreeHost(b->running_host);
@@ -397,7 +411,7 @@ lq_status lq_batch_autotune(lq_batch *b, const lq_fire_params *p, int launches, 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->tables_ok = false;   // force the rebuild of the real tables
-    drop_graph(b);
+    drop_batch_graph(b);
     lq_status r2 = set_tiling(b, bty, bzc);
     if (r != LQ_OK) return r;
     if (best_ms) *best_ms = best;

@@ -47,16 +47,42 @@ __device__ __forceinline__ double min_image(double d, int n, int periodic) {
     return d;
 }
 
+// |d|^2 summed in x, y, z order with every product rounded (no contraction),
+// so that sites on an object's surface are classified like the host geometry
+__device__ __forceinline__ double norm2_rn(double dx, double dy, double dz) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// offset of site (x, y, z) from the nearest point of the segment o.c .. o.c2:
+// d = site - midpoint (minimum image), a = c2 - c, nearest point at
+// midpoint + t a with t = clamp(d.a / a.a, -1/2, 1/2)
+__device__ void capsule_offset(const LatticeDev &L, const GeoObjDev &o, int x, int y, int z, double r[3]) {
+    double m[3];
+    for (int k = 0; k < 3; ++k) m[k] = __dmul_rn(__dadd_rn(o.c[k], o.c2[k]), 0.5);
+    double d[3] = {min_image(x - m[0], L.nx, L.px), min_image(y - m[1], L.ny, L.py),
+                   min_image(z - m[2], L.nz, L.pz)};
+    double a[3] = {o.c2[0] - o.c[0], o.c2[1] - o.c[1], o.c2[2] - o.c[2]};
+    double aa = norm2_rn(a[0], a[1], a[2]);
+    double da = __dadd_rn(__dadd_rn(__dmul_rn(d[0], a[0]), __dmul_rn(d[1], a[1])), __dmul_rn(d[2], a[2]));
+    double t = aa > 0.0 ? __ddiv_rn(da, aa) : 0.0;
+    t = fmin(fmax(t, -0.5), 0.5);
+    for (int k = 0; k < 3; ++k) r[k] = __dadd_rn(d[k], -__dmul_rn(t, a[k]));
+}
+
 __device__ bool obj_contains(const LatticeDev &L, const GeoObjDev &o, int x, int y, int z) {
     if (o.type == 0) {
         int c = o.axis == 0 ? x : (o.axis == 1 ? y : z);
         return c == o.plane;
     }
-    if (o.type == 1) {
-        double dx = min_image(x - o.c[0], L.nx, L.px);
-        double dy = min_image(y - o.c[1], L.ny, L.py);
-        double dz = min_image(z - o.c[2], L.nz, L.pz);
-        return dx * dx + dy * dy + dz * dz <= o.R * o.R;
+    if (o.type == 1 || o.type == 4) {   // sphere; droplet = everything outside the ball
+        double r2 = norm2_rn(min_image(x - o.c[0], L.nx, L.px), min_image(y - o.c[1], L.ny, L.py),
+                             min_image(z - o.c[2], L.nz, L.pz));
+        return o.type == 1 ? r2 <= o.R * o.R : r2 > o.R * o.R;
+    }
+    if (o.type == 5) {   // spherocylinder: within R of its axis segment
+        double r[3];
+        capsule_offset(L, o, x, y, z, r);
+        return norm2_rn(r[0], r[1], r[2]) <= o.R * o.R;
     }
     return false;
 }
@@ -68,7 +94,10 @@ __global__ void k_owner(LatticeDev L, const GeoObjDev *objs, int nobj, int *owne
         site_xyz(L, i, x, y, z);
         int o = NO_OWNER;
         for (int t = 0; t < nobj; ++t)
-            if (objs[t].type <= 1 && obj_contains(L, objs[t], x, y, z)) { o = t; break; }
+            if ((objs[t].type <= 1 || objs[t].type >= 4) && obj_contains(L, objs[t], x, y, z)) {
+                o = t;
+                break;
+            }
         owner[i] = o;
     }
 }
@@ -166,10 +195,12 @@ __global__ void k_fill(LatticeDev L, const uint8_t *mask, const int *owner,
             double nrm[3] = {0.0, 0.0, 0.0};
             if (o.type == 0) {
                 nrm[o.axis] = 1.0;
-            } else if (o.type == 1) {
+            } else if (o.type == 1 || o.type == 4) {
                 nrm[0] = min_image(x - o.c[0], L.nx, L.px);
                 nrm[1] = min_image(y - o.c[1], L.ny, L.py);
                 nrm[2] = min_image(z - o.c[2], L.nz, L.pz);
+            } else if (o.type == 5) {
+                capsule_offset(L, o, x, y, z, nrm);
             } else {
                 if (o.type == 3) sp = o.per_site[pos];
                 nrm[0] = sp.dir[0]; nrm[1] = sp.dir[1]; nrm[2] = sp.dir[2];
@@ -390,6 +421,54 @@ cudaError_t init_random_uniaxial(const LatticeDev &L, const uint8_t *mask, unsig
                                  double S, void *q, int fp32, cudaStream_t s) {
     if (fp32) k_random_uniaxial<int><<<blocks_for(L.N, 256), 256, 0, s>>>(L, mask, seed, S, (int *)q);
     else k_random_uniaxial<double><<<blocks_for(L.N, 256), 256, 0, s>>>(L, mask, seed, S, (double *)q);
+    return cudaGetLastError();
+}
+
+// Dipolar start about a colloid at c with far-field director a (unit): a
+// radial hedgehog at c superposed on a hyperbolic hedgehog at h = c + rd a,
+// director tilt psi = theta_c - theta_h from a (polar angles of the site
+// seen from c and from h).  With u = x - c, u_a = u.a, w_a = u_a - rd and
+// u_perp = u - u_a a, the angle difference expands to
+//   n = ((u_a w_a + |u_perp|^2) a - rd u_perp) / (|u| |w|),
+// a unit vector; at c and at h, where it is undefined, n = a.
+template <typename T>
+__global__ void k_dipolar(LatticeDev L, const uint8_t *mask, double3 c, double3 a, double rd, double S,
+                          T *q) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L.N;
+         i += (long long)gridDim.x * blockDim.x) {
+        double qq[5] = {0, 0, 0, 0, 0};
+        if (mask[i] & M_SIM) {
+            int x, y, z;
+            site_xyz(L, i, x, y, z);
+            double u0 = min_image(x - c.x, L.nx, L.px), u1 = min_image(y - c.y, L.ny, L.py),
+                   u2 = min_image(z - c.z, L.nz, L.pz);
+            double ua = u0 * a.x + u1 * a.y + u2 * a.z;
+            double p0 = u0 - ua * a.x, p1 = u1 - ua * a.y, p2 = u2 - ua * a.z;
+            double rho2 = p0 * p0 + p1 * p1 + p2 * p2;
+            double wa = ua - rd;
+            double den = sqrt((ua * ua + rho2) * (wa * wa + rho2));
+            double n0 = a.x, n1 = a.y, n2 = a.z;
+            if (den > 0.0) {
+                double ca = (ua * wa + rho2) / den, cp = -rd / den;
+                n0 = ca * a.x + cp * p0;
+                n1 = ca * a.y + cp * p1;
+                n2 = ca * a.z + cp * p2;
+            }
+            qq[0] = 1.5 * S * (n0 * n0 - 1.0 / 3.0);
+            qq[1] = 1.5 * S * n0 * n1;
+            qq[2] = 1.5 * S * n0 * n2;
+            qq[3] = 1.5 * S * (n1 * n1 - 1.0 / 3.0);
+            qq[4] = 1.5 * S * n1 * n2;
+        }
+        for (int k = 0; k < 5; ++k) store_q(q, k * L.N + i, qq[k]);
+    }
+}
+
+cudaError_t init_dipolar(const LatticeDev &L, const uint8_t *mask, const double c[3], const double a[3],
+                         double rd, double S, void *q, int fp32, cudaStream_t s) {
+    double3 cc = make_double3(c[0], c[1], c[2]), aa = make_double3(a[0], a[1], a[2]);
+    if (fp32) k_dipolar<int><<<blocks_for(L.N, 256), 256, 0, s>>>(L, mask, cc, aa, rd, S, (int *)q);
+    else k_dipolar<double><<<blocks_for(L.N, 256), 256, 0, s>>>(L, mask, cc, aa, rd, S, (double *)q);
     return cudaGetLastError();
 }
 

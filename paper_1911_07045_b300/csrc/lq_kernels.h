@@ -55,9 +55,11 @@ struct AnchorSpecDev {
     double dir[3];
 };
 struct GeoObjDev {
-    int type;                 // 0 wall, 1 sphere, 2 object sites, 3 anchored sites
+    int type;                 // 0 wall, 1 sphere, 2 object sites, 3 anchored sites,
+                              // 4 droplet (outside a ball), 5 spherocylinder
     int axis, plane;
     double c[3], R;
+    double c2[3];             // spherocylinder: second end of the axis segment
     AnchorSpecDev spec;
     const int32_t *xyz;       // device copy of a site list
     long long n;
@@ -90,6 +92,10 @@ cudaError_t mixed_velocity(const void *v, const void *F, const FireDev *st, doub
                            long long n, int fp32, cudaStream_t s);
 cudaError_t init_random_uniaxial(const LatticeDev &L, const uint8_t *mask, unsigned long long seed,
                                  double S, void *q, int fp32, cudaStream_t s);
+// dipolar start about a colloid (centre c, unit far-field axis a, hyperbolic
+// hedgehog at c + rd a), Q = 3/2 S (n n - I/3) on simulated sites
+cudaError_t init_dipolar(const LatticeDev &L, const uint8_t *mask, const double c[3], const double a[3],
+                         double rd, double S, void *q, int fp32, cudaStream_t s);
 cudaError_t count_simulated(const LatticeDev &L, const uint8_t *mask, unsigned long long *out,
                             cudaStream_t s);
 

@@ -100,6 +100,8 @@ lq_status start_solve(lq_server *sv, Active &a) {
         switch (o.type) {
         case LQ_OBJ_WALL: st = lq_add_wall(a.s, o.axis, o.plane, &o.anch); break;
         case LQ_OBJ_SPHERE: st = lq_add_sphere(a.s, o.c, o.R, &o.anch); break;
+        case LQ_OBJ_DROPLET: st = lq_add_droplet(a.s, o.c, o.R, &o.anch); break;
+        case LQ_OBJ_SPHEROCYLINDER: st = lq_add_spherocylinder(a.s, o.c, o.c2, o.R, &o.anch); break;
         case LQ_OBJ_SITES: st = lq_add_object_sites(a.s, o.n, o.xyz, &o.anch); break;
         case LQ_OBJ_ANCHORED: st = lq_add_anchored_sites(a.s, o.n, o.xyz, o.per_site); break;
         default: st = LQ_EINVAL;

@@ -142,6 +142,8 @@ void drop_graph(lq_solver *s) {
 
 lq_status build_geometry(lq_solver *s) {
     if (!s->geom_dirty) return LQ_OK;
+    drop_graph(s);   // captured launches hold the record tables freed below
+    ++s->gen;
     const LatticeDev &L = s->L;
     cudaStream_t st = s->stream;
     int nobj = (int)s->objects.size();
@@ -157,7 +159,7 @@ lq_status build_geometry(lq_solver *s) {
         GeoObjDev &d = hobj[o];
         memset(&d, 0, sizeof d);
         d.type = h.type; d.axis = h.axis; d.plane = h.plane;
-        for (int k = 0; k < 3; ++k) d.c[k] = h.c[k];
+        for (int k = 0; k < 3; ++k) { d.c[k] = h.c[k]; d.c2[k] = h.c2[k]; }
         d.R = h.R;
         d.spec.kind = h.anch.kind; d.spec.W = h.anch.W;
         for (int k = 0; k < 3; ++k) d.spec.dir[k] = h.anch.dir[k];
@@ -400,6 +402,32 @@ lq_status check_solver(lq_solver *s) {
     return LQ_OK;
 }
 
+const char *validate_material(const lq_material *m, double *S0) {
+    if (m->n_constants != 1 && m->n_constants != 3) return "n_constants must be 1 or 3";
+    if (m->n_constants == 1 && (m->L2 != 0.0 || m->L3 != 0.0 || m->L4 != 0.0 || m->L6 != 0.0))
+        return "one-constant form needs L2 = L3 = L4 = L6 = 0";
+    double disc = m->B * m->B - 24.0 * m->A * m->C;
+    double s0 = m->S0;
+    if (!(s0 > 0)) {
+        if (!(m->C > 0) || disc < 0) return "no nematic minimum for these A, B, C";
+        s0 = (-m->B + std::sqrt(disc)) / (6.0 * m->C);  // Eq. (S0def)
+    }
+    *S0 = s0;
+    return nullptr;
+}
+
+lq_status add_object(lq_solver *s, HostObject &&o) {
+    if (o.type != 3) {
+        const lq_anchoring &a = o.anch;
+        if (a.kind < 0 || a.kind > 2 || !(a.W >= 0)) return fail(s, LQ_EINVAL, "bad anchoring");
+    }
+    if (s->objects.size() >= 0x7ffffff0u) return fail(s, LQ_EINVAL, "too many objects");
+    s->objects.push_back(std::move(o));
+    s->geom_dirty = true;
+    s->fire_ready = false;
+    return LQ_OK;
+}
+
 lq_status copy_out_state(lq_solver *s, const void *src, double *out, bool is_q = false) {
     size_t n = 5 * (size_t)s->L.N;
     if (s->fp32) {
@@ -433,16 +461,9 @@ lq_status lq_create(const lq_lattice *lat, const lq_material *mat, int precision
     *out = nullptr;
     if (lat->nx <= 0 || lat->ny <= 0 || lat->nz <= 0) return fail(s, LQ_EINVAL, "lattice sizes must be positive");
     if (lat->spacing != 1.0) return fail(s, LQ_EINVAL, "spacing must be 1 (lattice units)");
-    if (mat->n_constants != 1 && mat->n_constants != 3) return fail(s, LQ_EINVAL, "n_constants must be 1 or 3");
-    if (mat->n_constants == 1 && (mat->L2 != 0.0 || mat->L3 != 0.0 || mat->L4 != 0.0 || mat->L6 != 0.0))
-        return fail(s, LQ_EINVAL, "one-constant form needs L2 = L3 = L4 = L6 = 0");
+    double S0 = 0;
+    if (const char *why = validate_material(mat, &S0)) return fail(s, LQ_EINVAL, "%s", why);
     if (precision != LQ_FP64 && precision != LQ_FP32_BULK_FP64_RED) return fail(s, LQ_EINVAL, "bad precision");
-    double disc = mat->B * mat->B - 24.0 * mat->A * mat->C;
-    double S0 = mat->S0;
-    if (!(S0 > 0)) {
-        if (!(mat->C > 0) || disc < 0) return fail(s, LQ_EINVAL, "no nematic minimum for these A, B, C");
-        S0 = (-mat->B + std::sqrt(disc)) / (6.0 * mat->C);  // Eq. (S0def)
-    }
     long long N = (long long)lat->nx * lat->ny * lat->nz;
     if ((long long)lat->ny * lat->nz + 1 > 0x7fffffffLL) return fail(s, LQ_EINVAL, "lattice too large");
 
@@ -513,18 +534,6 @@ void lq_destroy(lq_solver *s) {
     delete s;
 }
 
-static lq_status add_object(lq_solver *s, HostObject &&o) {
-    if (o.type != 3) {
-        const lq_anchoring &a = o.anch;
-        if (a.kind < 0 || a.kind > 2 || !(a.W >= 0)) return fail(s, LQ_EINVAL, "bad anchoring");
-    }
-    if (s->objects.size() >= 0x7ffffff0u) return fail(s, LQ_EINVAL, "too many objects");
-    s->objects.push_back(std::move(o));
-    s->geom_dirty = true;
-    s->fire_ready = false;
-    return LQ_OK;
-}
-
 lq_status lq_add_wall(lq_solver *s, int axis, int plane, const lq_anchoring *a) {
     if (check_solver(s)) return LQ_EINVAL;
     if (!a || axis < 0 || axis > 2) return fail(s, LQ_EINVAL, "bad wall");
@@ -539,6 +548,25 @@ lq_status lq_add_sphere(lq_solver *s, const double c[3], double radius, const lq
     HostObject o;
     o.type = 1; o.R = radius; o.anch = *a;
     for (int k = 0; k < 3; ++k) o.c[k] = c[k];
+    return add_object(s, std::move(o));
+}
+
+lq_status lq_add_droplet(lq_solver *s, const double c[3], double radius, const lq_anchoring *a) {
+    if (check_solver(s)) return LQ_EINVAL;
+    if (!a || !c || !(radius > 0)) return fail(s, LQ_EINVAL, "bad droplet");
+    HostObject o;
+    o.type = 4; o.R = radius; o.anch = *a;
+    for (int k = 0; k < 3; ++k) o.c[k] = c[k];
+    return add_object(s, std::move(o));
+}
+
+lq_status lq_add_spherocylinder(lq_solver *s, const double p0[3], const double p1[3], double radius,
+                                const lq_anchoring *a) {
+    if (check_solver(s)) return LQ_EINVAL;
+    if (!a || !p0 || !p1 || !(radius >= 0)) return fail(s, LQ_EINVAL, "bad spherocylinder");
+    HostObject o;
+    o.type = 5; o.R = radius; o.anch = *a;
+    for (int k = 0; k < 3; ++k) { o.c[k] = p0[k]; o.c2[k] = p1[k]; }
     return add_object(s, std::move(o));
 }
 

@@ -13,9 +13,11 @@ namespace lq {
 namespace detail {
 
 struct HostObject {
-    int type;                       // 0 wall, 1 sphere, 2 object sites, 3 anchored sites
+    int type;                       // 0 wall, 1 sphere, 2 object sites, 3 anchored sites,
+                                    // 4 droplet, 5 spherocylinder
     int axis = 0, plane = 0;
     double c[3] = {0, 0, 0}, R = 0;
+    double c2[3] = {0, 0, 0};       // spherocylinder: second end of the axis
     lq_anchoring anch{};
     std::vector<int32_t> xyz;
     std::vector<lq_anchoring> per_site;
@@ -37,6 +39,8 @@ struct lq_solver {
 
     std::vector<lq::detail::HostObject> objects;
     bool geom_dirty = true;
+    unsigned long long gen = 0;     // bumped when device geometry or material change
+                                    // (batches rebuild their kernel arguments)
 
     uint8_t *mask = nullptr;
     int *row_start = nullptr, *rec_x = nullptr;
@@ -65,6 +69,13 @@ namespace lq {
 namespace detail {
 
 lq_status fail(lq_solver *s, lq_status st, const char *fmt, ...);
+lq_status check_solver(lq_solver *s);
+// material checks shared by lq_create and lq_set_material; S0 from Eq. (S0def)
+// unless given; returns a message or nullptr
+const char *validate_material(const lq_material *m, double *S0);
+lq_status add_object(lq_solver *s, HostObject &&o);
+void drop_graph(lq_solver *s);
+lq_status ensure_partials(lq_solver *s);
 int effective_zchunk(const lq_solver *s);
 StepLaunch make_launch(lq_solver *s, int force_only);
 lq_status build_geometry(lq_solver *s);

@@ -30,6 +30,7 @@ LQ_MIN_FIRE, LQ_MIN_GD, LQ_MIN_NESTEROV = 0, 1, 2
 # every symbol include/lqmin.h declares
 EXPORTS = [
     "lq_create", "lq_destroy", "lq_last_error", "lq_create_error", "lq_add_wall", "lq_add_sphere",
+    "lq_add_droplet", "lq_add_spherocylinder",
     "lq_add_object_sites", "lq_add_anchored_sites", "lq_geometry_info", "lq_get_mask", "lq_set_q",
     "lq_set_q_device", "lq_init_random_uniaxial", "lq_get_q", "lq_get_velocity", "lq_get_force",
     "lq_force", "lq_energy", "lq_order_field", "lq_fire_reset", "lq_step", "lq_minimize",
@@ -37,7 +38,9 @@ EXPORTS = [
     "lq_energy_noalloc", "lq_batch_create", "lq_batch_destroy", "lq_batch_last_error",
     "lq_batch_set_tiling", "lq_batch_get_tiling", "lq_batch_autotune", "lq_batch_step",
     "lq_batch_minimize", "lq_server_create", "lq_server_destroy", "lq_server_submit",
-    "lq_server_poll", "lq_server_wait", "lq_server_stats_get",
+    "lq_server_poll", "lq_server_wait", "lq_server_stats_get", "lq_boundary_check",
+    "lq_add_boundary_text", "lq_load_boundary_file", "lq_object_count", "lq_move_object",
+    "lq_clear_objects", "lq_set_material", "lq_clone", "lq_pmf_sweep", "lq_init_dipolar",
 ]
 
 
@@ -84,7 +87,7 @@ class Result(C.Structure):
 class Object(C.Structure):
     _fields_ = [("type", C.c_int), ("axis", C.c_int), ("plane", C.c_int), ("c", C.c_double * 3),
                 ("R", C.c_double), ("anch", Anchoring), ("n", C.c_int64),
-                ("xyz", C.c_void_p), ("per_site", C.c_void_p)]
+                ("xyz", C.c_void_p), ("per_site", C.c_void_p), ("c2", C.c_double * 3)]
 
 
 class Request(C.Structure):
@@ -122,6 +125,9 @@ def load(path: str = LIB_PATH):
         "lq_create_error": (C.c_char_p, []),
         "lq_add_wall": (C.c_int, [S, C.c_int, C.c_int, C.POINTER(Anchoring)]),
         "lq_add_sphere": (C.c_int, [S, C.POINTER(C.c_double), d, C.POINTER(Anchoring)]),
+        "lq_add_droplet": (C.c_int, [S, C.POINTER(C.c_double), d, C.POINTER(Anchoring)]),
+        "lq_add_spherocylinder": (C.c_int, [S, C.POINTER(C.c_double), C.POINTER(C.c_double), d,
+                                            C.POINTER(Anchoring)]),
         "lq_add_object_sites": (C.c_int, [S, i64, p, C.POINTER(Anchoring)]),
         "lq_add_anchored_sites": (C.c_int, [S, i64, p, p]),
         "lq_geometry_info": (C.c_int, [S, C.POINTER(i64), C.POINTER(i64)]),
@@ -158,6 +164,17 @@ def load(path: str = LIB_PATH):
         "lq_server_poll": (C.c_int, [p, C.c_uint64, C.POINTER(Result), p]),
         "lq_server_wait": (C.c_int, [p, C.c_uint64, d, C.POINTER(Result), p]),
         "lq_server_stats_get": (C.c_int, [p, C.POINTER(ServerStats)]),
+        "lq_boundary_check": (C.c_int, [C.c_char_p, C.POINTER(i64), C.POINTER(i64), C.c_char_p,
+                                        C.c_size_t]),
+        "lq_add_boundary_text": (C.c_int, [S, C.c_char_p]),
+        "lq_load_boundary_file": (C.c_int, [S, C.c_char_p]),
+        "lq_object_count": (C.c_int, [S, C.POINTER(C.c_int)]),
+        "lq_move_object": (C.c_int, [S, C.c_int, C.POINTER(C.c_double)]),
+        "lq_clear_objects": (C.c_int, [S]),
+        "lq_set_material": (C.c_int, [S, C.POINTER(Material)]),
+        "lq_clone": (C.c_int, [S, p, C.POINTER(p)]),
+        "lq_pmf_sweep": (C.c_int, [S, C.c_int, C.c_int, p, C.POINTER(FireParams), p]),
+        "lq_init_dipolar": (C.c_int, [S, C.POINTER(C.c_double), C.POINTER(C.c_double), d, d]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -187,6 +204,29 @@ def descent_params(method, step, momentum=0.0, max_iter=10 ** 9, force_tol=1e-9,
                        wall_timeout_s=wall_timeout_s, method=method, momentum=momentum)
 
 
+def material(A, B, C_, L1, L2=0.0, L3=0.0, n_constants=None, S0=0.0, L4=0.0, L6=0.0,
+             H=(0.0, 0.0, 0.0), mu0_dchi=0.0, E=(0.0, 0.0, 0.0), eps0_deps=0.0) -> Material:
+    """lq_material; n_constants None picks 1 when L2..L6 are all zero."""
+    if n_constants is None:
+        n_constants = 1 if (L2 == 0.0 and L3 == 0.0 and L4 == 0.0 and L6 == 0.0) else 3
+    return Material(A, B, C_, L1, L2, L3, L4, L6, n_constants, S0,
+                    (C.c_double * 3)(*[float(v) for v in H]), float(mu0_dchi),
+                    (C.c_double * 3)(*[float(v) for v in E]), float(eps0_deps))
+
+
+def boundary_check(text):
+    """Parse boundary text (see ``lq_add_boundary_text``) without a solver:
+    (number of blocks, number of site lines); raises LqError with the
+    message naming the line."""
+    lib = load()
+    nb, ns = C.c_int64(), C.c_int64()
+    err = C.create_string_buffer(256)
+    st = lib.lq_boundary_check(text.encode(), C.byref(nb), C.byref(ns), err, len(err))
+    if st != LQ_OK:
+        raise LqError(st, err.value.decode())
+    return nb.value, ns.value
+
+
 def anchoring(kind, W, dir=(0.0, 0.0, 1.0)) -> Anchoring:
     return Anchoring(int(kind), float(W), (C.c_double * 3)(*[float(v) for v in dir]))
 
@@ -202,11 +242,7 @@ class Solver:
         self.shape = (nx, ny, nz)
         self.N = nx * ny * nz
         lat = Lattice(nx, ny, nz, 1.0, (C.c_int * 3)(*[int(bool(p)) for p in periodic]))
-        if n_constants is None:
-            n_constants = 1 if (L2 == 0.0 and L3 == 0.0 and L4 == 0.0 and L6 == 0.0) else 3
-        mat = Material(A, B, C_, L1, L2, L3, L4, L6, n_constants, S0,
-                       (C.c_double * 3)(*[float(v) for v in H]), float(mu0_dchi),
-                       (C.c_double * 3)(*[float(v) for v in E]), float(eps0_deps))
+        mat = material(A, B, C_, L1, L2, L3, n_constants, S0, L4, L6, H, mu0_dchi, E, eps0_deps)
         h = C.c_void_p()
         st = lib.lq_create(C.byref(lat), C.byref(mat), int(precision),
                            C.c_void_p(stream) if stream else None, C.byref(h))
@@ -215,6 +251,24 @@ class Solver:
         self.h = h
         self.lib = lib
         self.precision = precision
+
+    @classmethod
+    def _wrap(cls, lib, h, shape, precision):
+        self = cls.__new__(cls)
+        self.lib, self.h, self.shape, self.precision = lib, h, tuple(shape), precision
+        self.N = self.shape[0] * self.shape[1] * self.shape[2]
+        return self
+
+    def clone(self, stream=None):
+        """A new solver with this one's lattice, material, objects and Q."""
+        h = C.c_void_p()
+        self._ck(self.lib.lq_clone(self.h, C.c_void_p(stream) if stream else None, C.byref(h)))
+        return Solver._wrap(self.lib, h, self.shape, self.precision)
+
+    def set_material(self, A, B, C_, L1, L2=0.0, L3=0.0, n_constants=None, S0=0.0, L4=0.0, L6=0.0,
+                     H=(0.0, 0.0, 0.0), mu0_dchi=0.0, E=(0.0, 0.0, 0.0), eps0_deps=0.0):
+        mat = material(A, B, C_, L1, L2, L3, n_constants, S0, L4, L6, H, mu0_dchi, E, eps0_deps)
+        self._ck(self.lib.lq_set_material(self.h, C.byref(mat)))
 
     def close(self):
         if getattr(self, "h", None):
@@ -242,6 +296,17 @@ class Solver:
         cc = (C.c_double * 3)(*[float(v) for v in c])
         self._ck(self.lib.lq_add_sphere(self.h, cc, float(R), C.byref(a)))
 
+    def add_droplet(self, c, R, kind=ND_HOMEOTROPIC, W=0.0, dir=(0, 0, 1)):
+        a = anchoring(kind, W, dir)
+        cc = (C.c_double * 3)(*[float(v) for v in c])
+        self._ck(self.lib.lq_add_droplet(self.h, cc, float(R), C.byref(a)))
+
+    def add_spherocylinder(self, p0, p1, R, kind=ND_HOMEOTROPIC, W=0.0, dir=(0, 0, 1)):
+        a = anchoring(kind, W, dir)
+        c0 = (C.c_double * 3)(*[float(v) for v in p0])
+        c1 = (C.c_double * 3)(*[float(v) for v in p1])
+        self._ck(self.lib.lq_add_spherocylinder(self.h, c0, c1, float(R), C.byref(a)))
+
     def add_object_sites(self, xyz, kind=ND_HOMEOTROPIC, W=0.0, dir=(0, 0, 1)):
         xyz = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
         a = anchoring(kind, W, dir)
@@ -268,6 +333,12 @@ class Solver:
             elif t == "sphere":
                 k, W, d = o.get("anchor", (ND_HOMEOTROPIC, 0.0, (0, 0, 1)))
                 self.add_sphere(o["c"], o["R"], k, W, d)
+            elif t == "droplet":
+                k, W, d = o.get("anchor", (ND_HOMEOTROPIC, 0.0, (0, 0, 1)))
+                self.add_droplet(o["c"], o["R"], k, W, d)
+            elif t == "spherocylinder":
+                k, W, d = o.get("anchor", (ND_HOMEOTROPIC, 0.0, (0, 0, 1)))
+                self.add_spherocylinder(o["c"], o["c2"], o["R"], k, W, d)
             elif t == "sites":
                 k, W, d = o.get("anchor", (ND_HOMEOTROPIC, 0.0, (0, 0, 1)))
                 self.add_object_sites(o["xyz"], k, W, d)
@@ -275,6 +346,53 @@ class Solver:
                 self.add_anchored_sites(o["xyz"], o["kinds"], o["W"], o["dirs"])
             else:
                 raise ValueError(t)
+
+    def add_boundary_text(self, text):
+        self._ck(self.lib.lq_add_boundary_text(self.h, text.encode()))
+
+    def load_boundary_file(self, path):
+        self._ck(self.lib.lq_load_boundary_file(self.h, os.fsencode(path)))
+
+    def object_count(self):
+        n = C.c_int()
+        self._ck(self.lib.lq_object_count(self.h, C.byref(n)))
+        return n.value
+
+    def move_object(self, index, shift):
+        sh = (C.c_double * 3)(*[float(v) for v in shift])
+        self._ck(self.lib.lq_move_object(self.h, int(index), sh))
+
+    def clear_objects(self):
+        self._ck(self.lib.lq_clear_objects(self.h))
+
+    def pmf_sweep(self, index, shifts, params: FireParams):
+        """Minimise one clone per shift of object ``index`` in one batch;
+        returns (status, results) with each result's energy at its minimum."""
+        sh = np.ascontiguousarray(shifts, dtype=np.float64).reshape(-1, 3)
+        out = (Result * len(sh))()
+        st = self._ck(self.lib.lq_pmf_sweep(self.h, int(index), len(sh), _ptr(sh), C.byref(params),
+                                            C.cast(out, C.c_void_p)),
+                      ok=(LQ_OK, LQ_ENOTCONVERGED, LQ_ETIMEOUT, LQ_EDIVERGED))
+        return st, list(out)
+
+    def pmf_scan(self, index, shifts, params: FireParams):
+        """Move object ``index`` by each shift in turn (cumulative) and
+        re-minimise from the previous minimum; returns the results."""
+        out = []
+        for sh in np.asarray(shifts, dtype=np.float64).reshape(-1, 3):
+            self.move_object(index, sh)
+            out.append(self.minimize(params))
+        return out
+
+    def init_dipolar(self, c, axis=(0.0, 0.0, 1.0), rd=None, R=None, S=0.0):
+        """Dipolar start (see ``lq_init_dipolar``); rd defaults to 1.25 R."""
+        if rd is None:
+            if R is None:
+                raise ValueError("give rd or the colloid radius R")
+            rd = 1.25 * float(R)
+        cc = (C.c_double * 3)(*[float(v) for v in c])
+        aa = (C.c_double * 3)(*[float(v) for v in axis])
+        self._ck(self.lib.lq_init_dipolar(self.h, cc, aa, float(rd), float(S)))
 
     def geometry_info(self):
         a, b = C.c_int64(), C.c_int64()
@@ -418,7 +536,8 @@ class Batch:
         return st, list(out)
 
 
-OBJ_TYPES = {"wall": 0, "sphere": 1, "sites": 2, "anchored": 3}
+OBJ_TYPES = {"wall": 0, "sphere": 1, "sites": 2, "anchored": 3, "droplet": 4,
+             "spherocylinder": 5}
 
 
 class Server:
@@ -463,9 +582,11 @@ class Server:
                 o.anch = anchoring(*spec["anchor"])
             if spec["type"] == "wall":
                 o.axis, o.plane = spec["axis"], spec["plane"]
-            elif spec["type"] == "sphere":
+            elif spec["type"] in ("sphere", "droplet", "spherocylinder"):
                 o.c = (C.c_double * 3)(*spec["c"])
                 o.R = spec["R"]
+                if spec["type"] == "spherocylinder":
+                    o.c2 = (C.c_double * 3)(*spec["c2"])
             else:
                 xyz = np.ascontiguousarray(spec["xyz"], dtype=np.int32).reshape(-1, 3)
                 keep.append(xyz)

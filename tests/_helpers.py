@@ -79,6 +79,19 @@ CASES = {
                                            xyz=[[10, 4, 4], [10, 5, 4], [11, 5, 4], [11, 5, 5]],
                                            anchor=(1, 3.0, (0.6, 0.0, 0.8))),
                                       dict(type="wall", axis=1, plane=0, anchor=HOM(1.0))]),
+    "droplet_nd_1c": dict(shape=(30, 28, 26), L=(2.32, 0.0, 0.0),
+                          objects=[dict(type="droplet", c=(14.5, 13.8, 12.6), R=11.0,
+                                        anchor=HOM())]),
+    "spherocylinder_fg_3c": dict(shape=(40, 26, 24), L=(2.32, 0.5, 0.3),
+                                 objects=[dict(type="wall", axis=2, plane=0, anchor=HOM(1.0)),
+                                          dict(type="spherocylinder", c=(10.0, 12.5, 11.0),
+                                               c2=(29.0, 14.0, 12.5), R=4.5, anchor=PLANAR())]),
+    "droplet_with_rod_open_3c": dict(shape=(28, 26, 24), L=(1.7, 0.9, -0.4), periodic=(0, 0, 0),
+                                     objects=[dict(type="spherocylinder", c=(9.0, 10.0, 8.5),
+                                                   c2=(18.0, 15.0, 14.5), R=2.2,
+                                                   anchor=(1, 2.0, (0.3, 0.4, 0.866))),
+                                              dict(type="droplet", c=(13.5, 12.5, 11.5), R=11.2,
+                                                   anchor=HOM(3.0))]),
     "tiny_1x1x1": dict(shape=(1, 1, 1), L=(2.32, 0.5, 0.3), objects=[]),
     "tiny_2x3x1_open": dict(shape=(2, 3, 1), L=(2.32, 0.5, 0.3), periodic=(0, 1, 0), objects=[]),
     "chain_open": dict(shape=(5, 1, 1), L=(1.3, 0.5, 0.3), periodic=(0, 1, 1), objects=[]),

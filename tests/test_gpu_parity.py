@@ -76,7 +76,8 @@ def test_force_and_energy_fp64(oracle_mod, name, zchunk):
 
 
 @pytest.mark.parametrize("name", ["walls_nd_3c", "sphere_walls_fg_3c", "bulk1c_ragged",
-                                  "custom_open_x_3c"])
+                                  "custom_open_x_3c", "spherocylinder_fg_3c",
+                                  "droplet_with_rod_open_3c"])
 def test_force_fp32_form(oracle_mod, name):
     c = CASES[name]
     per = c.get("periodic", (1, 1, 1))

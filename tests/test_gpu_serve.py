@@ -37,6 +37,10 @@ def requests():
             dict(type="wall", axis=2, plane=0, anchor=hom),
             dict(type="wall", axis=2, plane=15, anchor=PLANAR())], seed=14),
         dict(shape=(28, 36, 20), L1=2.32, objects=[], seed=15),
+        dict(shape=(26, 24, 24), L1=2.32,
+             objects=[dict(type="spherocylinder", c=(9.0, 11.0, 10.0), c2=(15.0, 13.0, 13.0),
+                           R=2.0, anchor=PLANAR()),
+                      dict(type="droplet", c=(12.5, 11.5, 11.5), R=10.5, anchor=hom)], seed=16),
     ]
 
 

@@ -560,6 +560,87 @@ def test_geometry_spherocylinder_of_zero_length_is_a_sphere(oracle_mod):
             assert np.array_equal(u, v)
 
 
+def _degree(field, centre, radius, n_theta=120, n_phi=240):
+    """Topological degree of a unit-vector field on a sphere: the signed
+    solid angle its image sweeps over a triangulated (theta, phi) mesh,
+    divided by 4 pi (outward orientation)."""
+    th = np.linspace(0.0, np.pi, n_theta + 1)
+    ph = np.linspace(0.0, 2 * np.pi, n_phi + 1)
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    pts = np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)], -1)
+    n = field(np.asarray(centre)[None, :] + radius * pts.reshape(-1, 3)).reshape(pts.shape)
+
+    def omega(a, b, c):
+        num = np.einsum("...i,...i", a, np.cross(b, c))
+        den = 1 + np.einsum("...i,...i", a, b) + np.einsum("...i,...i", b, c) + \
+            np.einsum("...i,...i", c, a)
+        return 2 * np.arctan2(num, den)
+
+    a, b = n[:-1, :-1], n[1:, :-1]
+    c, d = n[1:, 1:], n[:-1, 1:]
+    # (theta, phi) increasing is the outward orientation of (e_theta, e_phi)
+    tot = omega(a, b, c).sum() + omega(a, c, d).sum()
+    return tot / (4 * np.pi)
+
+
+def test_degree_routine_on_textbook_fields():
+    radial = lambda x: x / np.linalg.norm(x, axis=1, keepdims=True)
+    assert _degree(radial, (0, 0, 0), 1.0) == pytest.approx(1.0, abs=1e-9)
+    mirror = lambda x: radial(x) * np.array([1.0, 1.0, -1.0])   # reflected in z = 0
+    assert _degree(mirror, (0, 0, 0), 1.0) == pytest.approx(-1.0, abs=1e-9)
+    half_turn = lambda x: radial(x) * np.array([-1.0, -1.0, 1.0])   # rotated by pi about z
+    assert _degree(half_turn, (0, 0, 0), 1.0) == pytest.approx(1.0, abs=1e-9)
+    assert _degree(lambda x: -radial(x), (0, 0, 0), 1.0) == pytest.approx(-1.0, abs=1e-9)
+    uniform = lambda x: np.tile([0.3, 0.4, 0.866], (len(x), 1))
+    assert _degree(uniform, (0, 0, 0), 1.0) == pytest.approx(0.0, abs=1e-9)
+
+
+@pytest.mark.parametrize("axis", [(0, 0, 1), (0.3, -0.5, 0.8)])
+def test_dipolar_director_hedgehog_charges_and_far_field(oracle_mod, axis):
+    """The dipolar start pairs a radial hedgehog at the colloid centre with
+    a hyperbolic hedgehog at rd along the axis, of opposite charges and total
+    charge zero, and is uniform along the axis far away (section IV.A).  As a
+    vector field continuous away from the two points, n ~ -u/|u| near the
+    centre (theta_h ~ pi there: degree -1) and n ~ w/|w| turned by pi about
+    the axis near the defect (degree +1)."""
+    R = 8.0
+    rd = 1.25 * R
+    a = np.asarray(axis, float) / np.linalg.norm(axis)
+    f = lambda x: oracle_mod.dipolar_director(x, axis, rd)
+    assert _degree(f, (0, 0, 0), 0.3 * rd) == pytest.approx(-1.0, abs=1e-6)
+    assert _degree(f, rd * a, 0.3 * rd) == pytest.approx(1.0, abs=1e-6)
+    assert _degree(f, 0.5 * rd * a, 4 * rd) == pytest.approx(0.0, abs=1e-6)
+    # unit vectors; radial on the colloid surface opposite the defect
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=(500, 3)) * 3 * R
+    n = f(x)
+    assert np.allclose(np.linalg.norm(n, axis=1), 1.0, atol=1e-14)
+    assert np.allclose(np.abs(f(-R * a[None, :]) @ a), 1.0, atol=1e-14)
+    # far field: n -> a, the deviation falling like rd / r
+    d = rng.normal(size=(200, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    for r in (1e3 * rd, 1e5 * rd):
+        dev = 1 - f(r * d) @ a
+        assert dev.max() < (2 * rd / r) ** 2
+    # rotating the point about the axis rotates the director with it
+    from scipy.spatial.transform import Rotation
+    rot = Rotation.from_rotvec(0.7 * a).as_matrix()
+    assert np.allclose(f(x @ rot.T), f(x) @ rot.T, atol=1e-12)
+
+
+def test_dipolar_q_is_uniaxial_on_the_lattice(oracle_mod):
+    shape = (24, 22, 20)
+    c, R = (11.5, 10.7, 9.3), 4.0
+    o = oracle_mod.Oracle(shape, A, B, C, 1.0, objects=[
+        dict(type="sphere", c=c, R=R, anchor=HOM(5.0))])
+    q = oracle_mod.dipolar_q(o, c, (0, 0, 1), 1.25 * R, o.S0)
+    sim = o.simulated()
+    assert np.all(q[:, ~sim] == 0)
+    for i in np.nonzero(sim)[0][::97]:
+        ev, _ = oracle_mod.eig_sym3(q[:, i])
+        assert np.allclose(sorted(ev), [-o.S0 / 2, -o.S0 / 2, o.S0], atol=1e-13)
+
+
 # ---- FIRE ---------------------------------------------------------------------------------
 
 FP = dict(dt0=0.1, dt_max=0.25, alpha0=0.2, f_alpha=0.5, f_inc=2.0, f_dec=0.5, n_min=2,
