@@ -149,6 +149,19 @@ typedef struct {
     double seconds;         /* wall time of the call */
 } lq_result;
 
+/* Distortion constants from Frank constants (section II: Eq. (fdistortionFull)
+   reproduces the Frank-Oseen density Eq. (FOfull) in the uniaxial limit):
+   L[0..4] = L1, L2, L3, L4, L6 for splay K1, twist K2, bend K3, saddle-splay
+   K24, chiral wavenumber q0 and order S (all in lattice units):
+     L1 = 2 (K3 - K1 + 3 K2) / (27 S^2),  L2 = 4 (K1 - K24) / (9 S^2),
+     L3 = 4 (K24 - K2) / (9 S^2),         L4 = -8 q0 K2 / (9 S^2),
+     L6 = 4 (K3 - K1) / (27 S^3).
+   K1 = K2 = K3 = K24 = K, q0 = 0 gives the one-constant L1 = 2K / (9 S^2)
+   of Eq. (fd1).  Host arithmetic only.  LQ_EINVAL for S <= 0 or a
+   non-finite input. */
+lq_status lq_frank_to_landau(double K1, double K2, double K3, double K24, double q0, double S,
+                             double L[5]);
+
 /* ---- lifetime ------------------------------------------------------------- */
 
 /* Create a solver for one lattice (section III.B).  cuda_stream is a

@@ -144,6 +144,8 @@ def lib():
         _lib.orc_eig_sym3.argtypes = [p, p, p]
         _lib.orc_order_field.argtypes = [C.POINTER(_Geometry), p, i64, p]
         _lib.orc_num_threads.restype = C.c_int
+        _lib.orc_distortion_density.restype = d
+        _lib.orc_distortion_density.argtypes = [C.POINTER(_Model), p, p]
     return _lib
 
 
@@ -247,6 +249,13 @@ class Oracle:
         assert len(sites) == n
         return sites, kind, W, q0, nu
 
+    def distortion_density(self, Q, d):
+        """Eq. (fdistortionFull) with this oracle's constants at one point:
+        Q (3, 3) and d (3, 3, 3), d[i, j, k] = dQ_ij/dx_k."""
+        Q = np.ascontiguousarray(Q, dtype=np.float64).reshape(9)
+        d = np.ascontiguousarray(d, dtype=np.float64).reshape(27)
+        return lib().orc_distortion_density(C.byref(self.model), _ptr(Q), _ptr(d))
+
     # ---- energy and force --------------------------------------------------
     def _q(self, q):
         q = np.ascontiguousarray(q, dtype=np.float64).reshape(5, self.N)
@@ -326,6 +335,20 @@ class Oracle:
 
 
 GD, NESTEROV = 1, 2
+
+
+def frank_to_landau(K1, K2, K3, K24, q0, S):
+    """Distortion constants of Eq. (fdistortionFull) that reproduce the
+    Frank-Oseen density Eq. (FOfull) in the uniaxial limit at order S
+    (section II, the identifications after Mori et al. 1999): L1 from the
+    splay, twist and bend constants, L2 and L3 from splay, twist and
+    saddle-splay, L4 from the chiral wavenumber q0 with the twist constant,
+    L6 from bend minus splay."""
+    return dict(L1=2.0 / (27.0 * S * S) * (K3 - K1 + 3.0 * K2),
+                L2=4.0 / (9.0 * S * S) * (K1 - K24),
+                L3=4.0 / (9.0 * S * S) * (K24 - K2),
+                L4=-8.0 / (9.0 * S * S) * q0 * K2,
+                L6=4.0 / (27.0 * S ** 3) * (K3 - K1))
 
 
 def dipolar_director(u, axis, rd):

@@ -270,6 +270,16 @@ static double distortion_density(const orc_model *m, double Q[3][3], double d[3]
            m->L6 / 2.0 * e6;
 }
 
+double orc_distortion_density(const orc_model *m, const double *Q9, const double *d27) {
+    double Q[3][3], d[3][3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            Q[i][j] = Q9[3 * i + j];
+            for (int k = 0; k < 3; ++k) d[i][j][k] = d27[(3 * i + j) * 3 + k];
+        }
+    return distortion_density(m, Q, d);
+}
+
 /* derivative of the density above with respect to d[a][b][c] */
 static void distortion_ddens(const orc_model *m, double Q[3][3], double d[3][3][3],
                              double g[3][3][3]) {

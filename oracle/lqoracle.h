@@ -97,6 +97,9 @@ int  orc_build_geometry(const orc_model *m, const orc_object *objs, int nobj,
                         orc_geometry *out);
 void orc_free_geometry(orc_geometry *g);
 
+/* Eq. (fdistortionFull) at one point: Q[3*i+j] = Q_ij, d[(3*i+j)*3+k] =
+   dQ_ij/dx_k (the continuum density, before any lattice differencing) */
+double orc_distortion_density(const orc_model *m, const double *Q9, const double *d27);
 /* free energy density of one site, split as (bulk, distortion, anchoring) */
 void   orc_site_energy(const orc_model *m, const orc_geometry *g,
                        const double *q, int64_t site, double parts[3]);

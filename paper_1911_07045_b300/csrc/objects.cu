@@ -157,6 +157,20 @@ bool parse_boundary(const char *text, Parsed *P) {
 
 extern "C" {
 
+lq_status lq_frank_to_landau(double K1, double K2, double K3, double K24, double q0, double S,
+                             double L[5]) {
+    if (!L || !(S > 0) || !std::isfinite(S) || !std::isfinite(K1) || !std::isfinite(K2) ||
+        !std::isfinite(K3) || !std::isfinite(K24) || !std::isfinite(q0))
+        return LQ_EINVAL;
+    double s2 = S * S;
+    L[0] = 2.0 * (K3 - K1 + 3.0 * K2) / (27.0 * s2);
+    L[1] = 4.0 * (K1 - K24) / (9.0 * s2);
+    L[2] = 4.0 * (K24 - K2) / (9.0 * s2);
+    L[3] = -8.0 * q0 * K2 / (9.0 * s2);
+    L[4] = 4.0 * (K3 - K1) / (27.0 * s2 * S);
+    return LQ_OK;
+}
+
 lq_status lq_set_material(lq_solver *s, const lq_material *mat) {
     if (check_solver(s)) return LQ_EINVAL;
     if (!mat) return fail(s, LQ_EINVAL, "null material");

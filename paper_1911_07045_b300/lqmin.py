@@ -41,6 +41,7 @@ EXPORTS = [
     "lq_server_poll", "lq_server_wait", "lq_server_stats_get", "lq_boundary_check",
     "lq_add_boundary_text", "lq_load_boundary_file", "lq_object_count", "lq_move_object",
     "lq_clear_objects", "lq_set_material", "lq_clone", "lq_pmf_sweep", "lq_init_dipolar",
+    "lq_frank_to_landau",
 ]
 
 
@@ -175,6 +176,7 @@ def load(path: str = LIB_PATH):
         "lq_clone": (C.c_int, [S, p, C.POINTER(p)]),
         "lq_pmf_sweep": (C.c_int, [S, C.c_int, C.c_int, p, C.POINTER(FireParams), p]),
         "lq_init_dipolar": (C.c_int, [S, C.POINTER(C.c_double), C.POINTER(C.c_double), d, d]),
+        "lq_frank_to_landau": (C.c_int, [d, d, d, d, d, d, C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -212,6 +214,16 @@ def material(A, B, C_, L1, L2=0.0, L3=0.0, n_constants=None, S0=0.0, L4=0.0, L6=
     return Material(A, B, C_, L1, L2, L3, L4, L6, n_constants, S0,
                     (C.c_double * 3)(*[float(v) for v in H]), float(mu0_dchi),
                     (C.c_double * 3)(*[float(v) for v in E]), float(eps0_deps))
+
+
+def frank_to_landau(K1, K2, K3, K24, q0, S):
+    """Distortion constants L1, L2, L3, L4, L6 from Frank constants (see
+    ``lq_frank_to_landau``), as a dict of keyword arguments for Solver."""
+    out = (C.c_double * 5)()
+    st = load().lq_frank_to_landau(K1, K2, K3, K24, q0, S, out)
+    if st != LQ_OK:
+        raise LqError(st, "lq_frank_to_landau: S must be positive and inputs finite")
+    return dict(zip(("L1", "L2", "L3", "L4", "L6"), list(out)))
 
 
 def boundary_check(text):

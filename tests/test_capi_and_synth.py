@@ -83,3 +83,17 @@ def test_workload_layouts():
     reqs = synth.serving_requests(count=50)
     assert all(48 <= r["shape"][0] <= 192 and r["shape"][0] % 16 == 0 for r in reqs)
     assert all(b["t_arrival"] > a["t_arrival"] for a, b in zip(reqs, reqs[1:]))
+
+
+def test_frank_helper_equals_the_oracle_mapping(oracle_mod):
+    """lq_frank_to_landau (host arithmetic, callable without a GPU) gives the
+    oracle's identifications of section II."""
+    for K in [(1.3, 0.7, 1.9, 0.45, 0.21, 0.6), (6.0, 3.0, 8.0, 1.0, -0.1, 0.53),
+              (1.0, 1.0, 1.0, 1.0, 0.0, 0.5)]:
+        got = lqmin.frank_to_landau(*K)
+        want = oracle_mod.frank_to_landau(*K)
+        for k in ("L1", "L2", "L3", "L4", "L6"):
+            assert got[k] == pytest.approx(want[k], rel=1e-15, abs=1e-300)
+    for bad in [(1, 1, 1, 1, 0, 0.0), (1, 1, 1, 1, 0, -0.5), (1, float("nan"), 1, 1, 0, 0.5)]:
+        with pytest.raises(lqmin.LqError):
+            lqmin.frank_to_landau(*bad)

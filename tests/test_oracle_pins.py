@@ -915,3 +915,48 @@ def test_cubic_rotation_invariance_with_chiral_and_cubic_terms(oracle_mod, rot):
     qr, objr = _lattice_rotation(L, R, q, objects)
     orr = oracle_mod.Oracle((L, L, L), A, B, C, 2.32, 0.5, 0.3, objects=objr, L4=0.7, L6=0.9)
     assert np.allclose(o.energy(q)[1], orr.energy(qr)[1], rtol=1e-12, atol=1e-12)
+
+
+# ---- Frank constants -> distortion constants ---------------------------------------------
+
+def _frank_oseen_and_q_gradient(n_expr, X, K1, K2, K3, K24, q0, S):
+    """Frank-Oseen density Eq. (FOfull) of a director field written in
+    sympy, and Q = 3/2 S (n n - I/3) with its gradient, as numpy callables."""
+    import sympy as sp
+    x, y, z = X
+    n = n_expr / sp.sqrt(n_expr.dot(n_expr))
+    div = sum(sp.diff(n[i], X[i]) for i in range(3))
+    curl = sp.Matrix([sp.diff(n[2], y) - sp.diff(n[1], z), sp.diff(n[0], z) - sp.diff(n[2], x),
+                      sp.diff(n[1], x) - sp.diff(n[0], y)])
+    bend = sp.Matrix([sum(n[j] * sp.diff(n[i], X[j]) for j in range(3)) for i in range(3)])
+    saddle = sum(sp.diff((bend - n * div)[i], X[i]) for i in range(3))
+    fo = (K1 * div ** 2 + K2 * (n.dot(curl) + q0) ** 2 + K3 * bend.dot(bend) + K24 * saddle) / 2
+    Q = sp.Rational(3, 2) * S * (n * n.T - sp.eye(3) / 3)
+    d = sp.Array([[[sp.diff(Q[i, j], X[k]) for k in range(3)] for j in range(3)] for i in range(3)])
+    return (sp.lambdify(X, fo, "numpy"), sp.lambdify(X, Q, "numpy"), sp.lambdify(X, d, "numpy"))
+
+
+@pytest.mark.parametrize("K", [(1.3, 0.7, 1.9, 0.45, 0.21), (0.6, 0.6, 0.6, 0.6, 0.0),
+                               (1.0, 0.5, 2.0, 0.0, -0.4)])
+def test_frank_mapping_reproduces_the_frank_oseen_density(oracle_mod, K):
+    """With the identifications of section II, the oracle's Eq.
+    (fdistortionFull) at a uniaxial Q equals Eq. (FOfull) pointwise, up to
+    the constant K2 q0^2 / 2, for a smooth twisted, splayed and bent field."""
+    import sympy as sp
+    K1, K2, K3, K24, q0 = K
+    S = 0.6
+    X = sp.symbols("x y z", real=True)
+    x, y, z = X
+    field = sp.Matrix([sp.sin(0.7 * y) + 0.3 * z, 0.5 + 0.4 * x * z,
+                       1 + 0.2 * x + 0.3 * sp.cos(0.9 * y)])
+    fo, Qf, df = _frank_oseen_and_q_gradient(field, X, K1, K2, K3, K24, q0, S)
+    Ls = oracle_mod.frank_to_landau(K1, K2, K3, K24, q0, S)
+    o = oracle_mod.Oracle((2, 2, 2), -1.0, -1.0, 1.0, Ls["L1"], Ls["L2"], Ls["L3"],
+                          L4=Ls["L4"], L6=Ls["L6"])
+    for pt in [(0.3, -0.2, 0.5), (1.1, 0.7, -0.4), (-0.6, 0.2, 0.9), (2.0, -1.5, 0.1)]:
+        want = float(fo(*pt)) - K2 * q0 * q0 / 2
+        got = o.distortion_density(np.array(Qf(*pt), float), np.array(df(*pt), float))
+        assert got == pytest.approx(want, rel=1e-12, abs=1e-14)
+    if K[:4] == (K1,) * 4 and q0 == 0:   # one-constant case, Eq. (fd1)
+        assert Ls["L1"] == pytest.approx(2 * K1 / (9 * S * S), rel=1e-15)
+        assert Ls["L2"] == Ls["L3"] == Ls["L4"] == Ls["L6"] == 0.0
