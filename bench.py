@@ -42,7 +42,7 @@ DESIGN_BYTES = {"fp32": 6 * 5 * 4 + 1, "fp64": 6 * 5 * 8 + 1}
 # dram__bytes_write.sum from one ncu capture of the same kernel on the 256^3
 # case of this workload, divided by its 16,777,216 sites (the traffic of a
 # launch grows with the sites it updates); the bench scales it to its lattice
-DRAM_BYTES_PER_SITE = {"fp32": 2.035370e9 / 256 ** 3, "fp64": 4.200095e9 / 256 ** 3}
+DRAM_BYTES_PER_SITE = {"fp32": 2.035745e9 / 256 ** 3, "fp64": 4.201560e9 / 256 ** 3}
 # FP64 form: bound by the FP64 pipe (2 FP64 operations per clock per SM).
 # FP64 arithmetic operations per site-update of the regular three-constant
 # site (second and mixed differences, distortion and bulk force, drift,
@@ -296,6 +296,103 @@ def run_serving(count: int, rate: float, budget_gb: float = 120.0):
             "site_updates_per_s": st["site_updates"] / wall, "wall_s": wall}
 
 
+def _trace(s, p, seconds, thresholds=(1e-2, 1e-3, 1e-4)):
+    """Run one minimiser for about ``seconds`` of wall clock in growing
+    chunks of steps: a trace of (time, iterations, |F|/sqrt(N), energy) and
+    the time at which |F|/sqrt(N) first fell below each threshold."""
+    r = s.step(p, 1)
+    t0 = time.perf_counter()
+    trace, reach = [], {}
+    chunk, it = 16, 1
+    while True:
+        r = s.step(p, chunk)
+        it += chunk
+        t = time.perf_counter() - t0
+        rms = r.rms_force
+        trace.append([round(t, 3), it, rms, s.energy()[0]])
+        for thr in thresholds:
+            if rms < thr and str(thr) not in reach:
+                reach[str(thr)] = round(t, 3)
+        if t > seconds or r.fire_status != 0 or not np.isfinite(rms):
+            break
+        chunk = min(chunk * 2, 1024)
+    return trace, reach, it, int(r.fire_status)
+
+
+def run_objects(L: int, seconds: float):
+    """Fig. 3: FIRE against gradient descent on the paper's three object
+    geometries (two colloids between plates, a droplet interior, a
+    spherocylinder between planar plates) at L^3 from a random start, each
+    for the same wall-clock budget on the FP32 form.  The energy is reported
+    relative to the lowest energy any run reached on that geometry."""
+    from paper_1911_07045_b300 import lqmin
+    runs = {
+        "fire": lqmin.fire_params(**dict(synth.FIRE_DEFAULTS, max_iter=10 ** 12, force_tol=0.0)),
+        # homeotropic anchoring (6 W = 32 on the stiffest boundary mode) adds to
+        # the bulk's ~84: eta lam < 2 needs eta < 0.017 here, 0.02 diverges
+        "gd_eta_0.015": lqmin.descent_params(lqmin.LQ_MIN_GD, 0.015, max_iter=10 ** 12,
+                                             force_tol=0.0),
+    }
+    out = {"workload": f"Fig. 3 geometries at {L}^3, one constant, random directors (seed 1), "
+                       f"FP32 form, {seconds} s per method", "geometries": {}}
+    for gname, cfg in synth.config_fig3(L).items():
+        res = {}
+        for name, p in runs.items():
+            s = lqmin.solver_for(cfg, precision=lqmin.LQ_FP32_BULK_FP64_RED)
+            s.init_random_uniaxial(1)
+            trace, reach, it, status = _trace(s, p, seconds)
+            res[name] = dict(trace=trace, reach=reach, iterations=it, status=status)
+            s.close()
+        e_min = min(min(t[3] for t in r["trace"]) for r in res.values())
+        g = {}
+        for name, r in res.items():
+            tr = [[t, i, rms, e - e_min] for t, i, rms, e in r["trace"]]
+            g[name] = {"seconds_to_rms_force": r["reach"], "iterations": r["iterations"],
+                       "status": r["status"], "final_rms_force": tr[-1][2],
+                       "final_energy_above_min": tr[-1][3],
+                       "trace_t_it_rms_dE": tr[:: max(1, len(tr) // 12)] + [tr[-1]]}
+        out["geometries"][gname] = {"energy_min": e_min, "methods": g}
+    return out
+
+
+def run_step_scaling(sizes, tol: float, seeds=(1, 2, 3)):
+    """Minimisation steps to a force tolerance against the linear size
+    (section IV.A: about L steps without boundaries, about L^1.5 with a
+    colloid): FIRE from random starts on a periodic one-constant bulk and on
+    the same box with a centred homeotropic colloid of radius L/8, FP32
+    form, until the largest site force is below ``tol``; the median over
+    seeds at each L and the fitted exponent of that median against L."""
+    from paper_1911_07045_b300 import lqmin
+    hom = (0, synth.W_HOMEOTROPIC, (0.0, 0.0, 1.0))
+    p = lqmin.fire_params(**dict(synth.FIRE_DEFAULTS, max_iter=400000, force_tol=tol))
+    out = {"workload": f"periodic L^3, one constant, random directors (seeds {list(seeds)}), "
+                       f"FP32 form, FIRE to max site force < {tol}", "families": {}}
+    for fam in ("bulk", "colloid"):
+        rows = []
+        for L in sizes:
+            objs = [] if fam == "bulk" else [dict(type="sphere", c=((L - 1) / 2.0,) * 3, R=L / 8.0,
+                                                  anchor=hom)]
+            its, secs, conv = [], [], True
+            for seed in seeds:
+                s = lqmin.solver_for(dict(shape=(L, L, L), L1=synth.L1_5CB, L2=0.0, L3=0.0,
+                                          objects=objs), precision=lqmin.LQ_FP32_BULK_FP64_RED)
+                s.init_random_uniaxial(seed)
+                st, r = s.minimize(p)
+                its.append(int(r.iterations))
+                secs.append(round(r.seconds, 3))
+                conv = conv and r.fire_status == 1
+                s.close()
+            rows.append(dict(L=L, iterations=its, median=float(np.median(its)), seconds=secs,
+                             converged=conv))
+        ok = [w for w in rows if w["converged"]]
+        slope = None
+        if len(ok) >= 3:
+            slope = float(np.polyfit(np.log([w["L"] for w in ok]),
+                                     np.log([w["median"] for w in ok]), 1)[0])
+        out["families"][fam] = {"runs": rows, "fitted_exponent": slope}
+    return out
+
+
 def run_minimizers(L: int, seconds: float):
     """FIRE against gradient descent and Nesterov's accelerated gradient on a
     periodic one-constant bulk from a random start (the comparison of Fig. 2,
@@ -319,24 +416,9 @@ def run_minimizers(L: int, seconds: float):
     for name, p in runs.items():
         s = lqmin.solver_for(cfg, precision=lqmin.LQ_FP32_BULK_FP64_RED)
         s.init_random_uniaxial(1)
-        r = s.step(p, 1)
-        t0 = time.perf_counter()
-        trace, reach = [], {}
-        chunk, it = 16, 1
-        while True:
-            r = s.step(p, chunk)
-            it += chunk
-            t = time.perf_counter() - t0
-            rms = r.rms_force
-            trace.append([round(t, 3), it, rms, s.energy()[0]])
-            for thr in (1e-2, 1e-3, 1e-4):
-                if rms < thr and str(thr) not in reach:
-                    reach[str(thr)] = round(t, 3)
-            if t > seconds or r.fire_status != lqmin.FIRE_RUNNING or not np.isfinite(rms):
-                break
-            chunk = min(chunk * 2, 1024)
+        trace, reach, it, status = _trace(s, p, seconds)
         out["methods"][name] = {"seconds_to_rms_force": reach, "iterations": it,
-                                "status": int(r.fire_status),
+                                "status": status,
                                 "final_rms_force": trace[-1][2], "final_energy": trace[-1][3],
                                 "trace": trace[:: max(1, len(trace) // 12)] + [trace[-1]]}
         s.close()
@@ -424,6 +506,11 @@ def main_ours(args, dist: Dist):
         line["served"] = run_serving(args.serving_requests, args.serving_rate)
     if dist.world == 1 and args.minimizers > 0:
         line["minimizers"] = run_minimizers(args.minimizer_size, args.minimizers)
+    if dist.world == 1 and args.objects > 0:
+        line["objects_fig3"] = run_objects(args.minimizer_size, args.objects)
+    if dist.world == 1 and args.step_scaling:
+        line["step_scaling"] = run_step_scaling([int(v) for v in args.step_scaling.split(",")],
+                                                args.step_scaling_tol)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if not all(f["ok"] for f in forms.values()):
@@ -478,6 +565,11 @@ def main(argv=None):
     ap.add_argument("--minimizers", type=float, default=0.0,
                     help="seconds per method of the FIRE / GD / Nesterov comparison (0: skip)")
     ap.add_argument("--minimizer-size", type=int, default=250)
+    ap.add_argument("--objects", type=float, default=0.0,
+                    help="seconds per method of the Fig. 3 object-geometry comparison (0: skip)")
+    ap.add_argument("--step-scaling", default="",
+                    help="comma-separated edges L of the steps-to-tolerance study (empty: skip)")
+    ap.add_argument("--step-scaling-tol", type=float, default=1e-5)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

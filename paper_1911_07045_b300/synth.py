@@ -186,6 +186,35 @@ def config_large(L: int = 512, seed: int = 3):
                 tol=1e-8)
 
 
+def config_fig3(L: int = 250):
+    """The three geometries of Fig. 3 at L^3, one-constant elasticity,
+    periodic box with plates at z = 0 and z = L-1 where present (sizes are
+    not printed in the paper: colloid radius L/10, droplet radius 0.48 L,
+    spherocylinder of radius L/12 and axis length 0.4 L along x):
+      two_colloids  two homeotropic colloids between homeotropic plates;
+      droplet       the interior of a homeotropic droplet;
+      rod_plates    a homeotropic spherocylinder between planar-degenerate
+                    plates."""
+    hom = (ND_HOMEOTROPIC, W_HOMEOTROPIC, (0.0, 0.0, 1.0))
+    pla = (FG_PLANAR, W_PLANAR, (0.0, 0.0, 1.0))
+    h = (L - 1) / 2.0
+    walls = lambda a: [dict(type="wall", axis=2, plane=0, anchor=a),
+                       dict(type="wall", axis=2, plane=L - 1, anchor=a)]
+    R = L / 10.0
+    return {
+        "two_colloids": dict(shape=(L, L, L), L1=L1_5CB, L2=0.0, L3=0.0,
+                             objects=walls(hom) + [
+                                 dict(type="sphere", c=(h - 1.6 * R, h, h), R=R, anchor=hom),
+                                 dict(type="sphere", c=(h + 1.6 * R, h, h), R=R, anchor=hom)]),
+        "droplet": dict(shape=(L, L, L), L1=L1_5CB, L2=0.0, L3=0.0,
+                        objects=[dict(type="droplet", c=(h, h, h), R=0.48 * L, anchor=hom)]),
+        "rod_plates": dict(shape=(L, L, L), L1=L1_5CB, L2=0.0, L3=0.0,
+                           objects=walls(pla) + [
+                               dict(type="spherocylinder", c=(h - 0.2 * L, h, h),
+                                    c2=(h + 0.2 * L, h, h), R=L / 12.0, anchor=hom)]),
+    }
+
+
 def config_batch(seed: int = 4, count: int = 64):
     """Independent cubic lattices, edge uniform in {32, 48, 64, 96, 128}, each
     with 0-3 homeotropic colloids of radius U[6, 16] (periodic box, no walls),
