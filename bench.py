@@ -48,6 +48,9 @@ DRAM_BYTES_PER_SITE = {"fp32": 2.035745e9 / 256 ** 3, "fp64": 4.201560e9 / 256 *
 # site (second and mixed differences, distortion and bulk force, drift,
 # mixing, kick, reductions), counted from the kernel's arithmetic
 FP64_OPS_PER_SITE = 220
+# the same for a one-constant site: the stencil is 15 second differences (add
+# + FMA), 10 adds for the three-axis sums and 8 scalings (48 instead of 120)
+FP64_OPS_PER_SITE_1C = 148
 FP64_OPS_PER_CLK_SM = 2
 N_SM = 148
 
@@ -176,11 +179,15 @@ class ClockSampler:
 # ---- our arm ------------------------------------------------------------------------
 
 def run_form(precision: str, L: int, steps: int, warmup: int, dist: Dist, sampler_gpu: int):
+    """One precision form on the L^3 workload; a "_1c" suffix runs the same
+    geometry with one-constant elasticity (L2 = L3 = 0)."""
     import torch
     from paper_1911_07045_b300 import lqmin
     cfg = synth.config_large(L)
+    if precision.endswith("_1c"):
+        cfg = dict(cfg, L2=0.0, L3=0.0)
     stream = torch.cuda.Stream()
-    prec = lqmin.LQ_FP32_BULK_FP64_RED if precision == "fp32" else lqmin.LQ_FP64
+    prec = lqmin.LQ_FP32_BULK_FP64_RED if precision.startswith("fp32") else lqmin.LQ_FP64
     s = lqmin.solver_for(cfg, precision=prec, stream=stream.cuda_stream)
     nsim, nrec = s.geometry_info()
     s.init_random_uniaxial(cfg["seed"])
@@ -454,7 +461,7 @@ def main_ours(args, dist: Dist):
     for prec in args.precision.split(","):
         # the FP64 form is ~13x slower: a tenth of the steps keeps its timed
         # region about as long as the FP32 form's
-        k = args.steps if prec == "fp32" else max(3, args.steps // 10)
+        k = args.steps if prec.startswith("fp32") else max(3, args.steps // 10)
         forms[prec] = run_form(prec, args.size, k, args.warmup, dist, dist.local)
     head = "fp32" if "fp32" in forms else next(iter(forms))
     h = forms[head]
@@ -462,22 +469,26 @@ def main_ours(args, dist: Dist):
     # device time per launch (CUDA events around the timed launches)
     rl = {}
     for k, f in forms.items():
-        traffic = DRAM_BYTES_PER_SITE[k] * f["N"]
-        if k == "fp32":
-            ach = ALG_BYTES[k] * f["N"] / f["per_launch_s"] / 1e9
+        base = k.split("_")[0]    # the one-constant forms move the same state bytes
+        traffic = DRAM_BYTES_PER_SITE[base] * f["N"]
+        if base == "fp32":
+            ach = ALG_BYTES[base] * f["N"] / f["per_launch_s"] / 1e9
             rl[k] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(ach / peak, 4), "traffic": round(traffic),
                      "dram_gbs": round(traffic / f["per_launch_s"] / 1e9, 1),
                      "dram_frac": round(traffic / f["per_launch_s"] / 1e9 / peak, 4),
-                     "design_bytes_per_site": DESIGN_BYTES[k], "alg_bytes_per_site": ALG_BYTES[k],
+                     "design_bytes_per_site": DESIGN_BYTES[base], "alg_bytes_per_site": ALG_BYTES[base],
                      "peak_kind": peak_kind + " (HBM copy)"}
+            if k != base:
+                rl[k]["traffic_from"] = "three-constant capture (same state bytes)"
         else:
             # FP64 pipe: derived peak = SMs x ops/clock x maximum SM clock
             fp64_peak = N_SM * FP64_OPS_PER_CLK_SM * (f["clocks"].get("sm_max_mhz") or 2032.0) * 1e6 / 1e9
-            ach = FP64_OPS_PER_SITE * f["N"] / f["per_launch_s"] / 1e9
+            ops = FP64_OPS_PER_SITE if k == base else FP64_OPS_PER_SITE_1C
+            ach = ops * f["N"] / f["per_launch_s"] / 1e9
             rl[k] = {"bound": "alu", "achieved": round(ach, 1), "peak": round(fp64_peak, 1),
                      "unit": "G FP64 op/s", "frac": round(ach / fp64_peak, 4),
-                     "traffic": round(traffic), "ops_per_site": FP64_OPS_PER_SITE,
+                     "traffic": round(traffic), "ops_per_site": ops,
                      "hbm_frac": round(traffic / f["per_launch_s"] / 1e9 / peak, 4),
                      "peak_kind": "derived: 148 SMs x 2 FP64 ops/clock x max SM clock"}
     line = {
@@ -557,7 +568,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=512)
-    ap.add_argument("--precision", default="fp32,fp64")
+    ap.add_argument("--precision", default="fp32,fp64,fp32_1c,fp64_1c")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=50)
     ap.add_argument("--serving-requests", type=int, default=8)
