@@ -450,6 +450,12 @@ lq_status lq_energy_noalloc(const lq_lattice *lattice, const lq_material *materi
 
 /* Number of z planes one thread block marches through (0 = automatic). */
 lq_status lq_set_zchunk(lq_solver *s, int zchunk);
+/* Element-index width of the step kernels: 0 = automatic (32-bit indices
+   while 5 N < 2^32, i.e. below about 950^3 sites, 64-bit beyond), 64 = the
+   64-bit instantiation on any lattice (the code path of the largest
+   lattices, for testing it on small ones; results are identical).
+   LQ_EINVAL for other values. */
+lq_status lq_set_index_width(lq_solver *s, int bits);
 /* Bytes of device memory held by the solver. */
 size_t lq_device_bytes(const lq_solver *s);
 

@@ -267,7 +267,7 @@ lq_status batch_set_members(lq_batch *b, lq_solver *const *solvers, int n) {
     b->idx32 = 1;
     b->form = b->three ? 1 : 0;
     for (int l = 0; l < n; ++l) {
-        if (!step_index32(solvers[l]->L.N)) b->idx32 = 0;
+        if (!step_index32(solvers[l]->L.N) || solvers[l]->idx64) b->idx32 = 0;
         if (solvers[l]->ext) b->form = 2;
     }
     if (n > b->cap) {

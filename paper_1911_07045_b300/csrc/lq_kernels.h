@@ -20,6 +20,7 @@ struct StepLaunch {
     FireDev *st;
     double *partials;
     int zchunk, force_only, fp32, three;
+    int idx64;                // 64-bit element indices even where 32 bits would do
 };
 
 // one block's share of a batched step: lattice, tile, z range, and its

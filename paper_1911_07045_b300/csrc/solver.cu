@@ -114,6 +114,7 @@ StepLaunch make_launch(lq_solver *s, int force_only) {
     sl.fp32 = s->fp32;
     sl.three = s->three;
     sl.ext = s->ext;
+    sl.idx64 = s->idx64;
     return sl;
 }
 
@@ -907,6 +908,16 @@ lq_status lq_set_zchunk(lq_solver *s, int zchunk) {
     s->zchunk = zchunk;
     drop_graph(s);
     return ensure_partials(s);
+}
+
+lq_status lq_set_index_width(lq_solver *s, int bits) {
+    if (check_solver(s)) return LQ_EINVAL;
+    if (bits != 0 && bits != 64) return fail(s, LQ_EINVAL, "index width must be 0 (automatic) or 64");
+    if (s->fire_ready) { lq_status r = sync_state(s); if (r != LQ_OK) return r; }
+    s->idx64 = bits == 64;
+    ++s->gen;          // batches pick their kernel instantiation again
+    drop_graph(s);
+    return LQ_OK;
 }
 
 size_t lq_device_bytes(const lq_solver *s) { return s ? s->bytes : 0; }

@@ -58,6 +58,7 @@ struct lq_solver {
     int cur = 0;                    // buffer holding the state (host view)
     bool fire_ready = false;
     int zchunk = 0;                 // 0 = automatic
+    int idx64 = 0;                  // 64-bit element indices forced (lq_set_index_width)
 
     cudaGraphExec_t gexec = nullptr;
     int graph_k = 0;

@@ -1400,7 +1400,7 @@ struct LaunchStep {
 
 cudaError_t launch_fire_step(const StepLaunch &sl, cudaStream_t stream) {
     const int form = sl.three ? (sl.ext ? 2 : 1) : 0;
-    return dispatch_single(sl.fp32, form, step_index32(sl.L.N), LaunchStep{sl, stream});
+    return dispatch_single(sl.fp32, form, step_index32(sl.L.N) && !sl.idx64, LaunchStep{sl, stream});
 }
 
 // ---- batched launches ----------------------------------------------------------

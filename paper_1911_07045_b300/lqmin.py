@@ -41,7 +41,7 @@ EXPORTS = [
     "lq_server_poll", "lq_server_wait", "lq_server_stats_get", "lq_boundary_check",
     "lq_add_boundary_text", "lq_load_boundary_file", "lq_object_count", "lq_move_object",
     "lq_clear_objects", "lq_set_material", "lq_clone", "lq_pmf_sweep", "lq_init_dipolar",
-    "lq_frank_to_landau",
+    "lq_frank_to_landau", "lq_set_index_width",
 ]
 
 
@@ -177,6 +177,7 @@ def load(path: str = LIB_PATH):
         "lq_pmf_sweep": (C.c_int, [S, C.c_int, C.c_int, p, C.POINTER(FireParams), p]),
         "lq_init_dipolar": (C.c_int, [S, C.POINTER(C.c_double), C.POINTER(C.c_double), d, d]),
         "lq_frank_to_landau": (C.c_int, [d, d, d, d, d, d, C.POINTER(C.c_double)]),
+        "lq_set_index_width": (C.c_int, [S, C.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -488,6 +489,9 @@ class Solver:
 
     def set_zchunk(self, z):
         self._ck(self.lib.lq_set_zchunk(self.h, int(z)))
+
+    def set_index_width(self, bits):
+        self._ck(self.lib.lq_set_index_width(self.h, int(bits)))
 
     def device_bytes(self):
         return self.lib.lq_device_bytes(self.h)

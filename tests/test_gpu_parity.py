@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from _helpers import CASES, HOM, PLANAR, force_rel_err, make_pair, need_gpu, rand_q
-from paper_1911_07045_b300 import synth
+from paper_1911_07045_b300 import lqmin, synth
 
 pytestmark = pytest.mark.gpu
 
@@ -132,3 +132,81 @@ def test_empty_lattice_all_object_sites(oracle_mod):
     s.set_q(rand_q(12, 1))
     assert np.all(s.force() == 0)
     assert s.energy()[0] == 0.0
+
+
+@pytest.mark.parametrize("name", ["bulk3c_ragged", "sphere_walls_fg_3c", "custom_open_x_3c",
+                                  "droplet_with_rod_open_3c", "sphere_nd_1c"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_index64_kernels_equal_index32(oracle_mod, name, prec):
+    """The 64-bit-index instantiation of the step kernels (the path of
+    lattices above about 950^3 sites) computes exactly what the 32-bit one
+    does: forced on small lattices, forces and FIRE trajectories agree bit
+    for bit, and with the oracle."""
+    c = CASES[name]
+    per = c.get("periodic", (1, 1, 1))
+    pair = [make_pair(oracle_mod, c["shape"], c["L"], c["objects"], per, precision=prec)
+            for _ in range(2)]
+    (a, o), (b, _) = pair
+    b.set_index_width(64)
+    q = rand_q(o.N, 23)
+    if prec == 1:
+        q = np.round(q * 2.0 ** 28) / 2.0 ** 28
+    for s in (a, b):
+        s.set_q(q)
+    Fa, Fb = a.force(), b.force()
+    assert np.array_equal(Fa, Fb)
+    tol = FORCE_TOL_FP64 if prec == 0 else FORCE_TOL_FP32
+    assert force_rel_err(Fb, o.force(q), o.simulated()) < tol
+    p = lqmin.fire_params(**dict(synth.FIRE_DEFAULTS, max_iter=10 ** 6, force_tol=1e-14))
+    ra, rb = a.step(p, 150), b.step(p, 150)
+    assert ra.iterations == rb.iterations == 150 and ra.max_force == rb.max_force
+    assert np.array_equal(a.get_q(), b.get_q())
+    with pytest.raises(lqmin.LqError):
+        b.set_index_width(32)
+
+
+def test_index64_member_in_a_batch():
+    """A batch with a member forced to 64-bit indices runs the 64-bit batch
+    kernel for all; one-constant members still advance bit for bit as alone."""
+    shape = (40, 26, 22)
+    mk = lambda: lqmin.Solver(shape, synth.A_5CB, synth.B_5CB, synth.C_5CB, 2.32,
+                              precision=lqmin.LQ_FP32_BULK_FP64_RED)
+    alone, mixed = [mk(), mk()], [mk(), mk()]
+    for lst in (alone, mixed):
+        lst[0].add_objects([dict(type="sphere", c=(20.0, 13.0, 11.0), R=5.0, anchor=HOM())])
+        for k, s in enumerate(lst):
+            s.set_q(synth.random_uniaxial_q(shape, 70 + k))
+    mixed[1].set_index_width(64)
+    batch = lqmin.Batch(mixed)
+    p = lqmin.fire_params(**dict(synth.FIRE_DEFAULTS, max_iter=10 ** 6, force_tol=1e-14))
+    res = batch.step(p, 33)
+    for a, m, rb in zip(alone, mixed, res):
+        a.set_zchunk(batch.tiling()[1])
+        ra = a.step(p, 33)
+        assert ra.iterations == rb.iterations == 33
+        assert np.array_equal(a.get_q(), m.get_q())
+    batch.close()
+
+
+def test_empty_and_zero_length_inputs():
+    """Empty site lists and boundary text, zero steps, and a lattice with no
+    simulated site at all: nothing changes, nothing divides by zero."""
+    shape = (10, 9, 8)
+    s = lqmin.Solver(shape, synth.A_5CB, synth.B_5CB, synth.C_5CB, 2.32)
+    s.add_object_sites(np.zeros((0, 3), np.int32))
+    s.add_anchored_sites(np.zeros((0, 3), np.int32), [], [], np.zeros((0, 3)))
+    s.add_boundary_text("# nothing here\n")
+    assert s.object_count() == 2 and s.geometry_info() == (np.prod(shape), 0)
+    s.init_random_uniaxial(2)
+    q = s.get_q()
+    p = lqmin.fire_params(**dict(synth.FIRE_DEFAULTS, max_iter=1000, force_tol=1e-9))
+    r = s.step(p, 0)
+    assert r.iterations == 0 and r.fire_status == lqmin.FIRE_RUNNING
+    assert np.array_equal(s.get_q(), q)
+    # every site an object site: converged at once, zero residual
+    e = lqmin.Solver((4, 3, 1), synth.A_5CB, synth.B_5CB, synth.C_5CB, 2.32)
+    e.add_objects([dict(type="wall", axis=2, plane=0, anchor=HOM())])
+    e.init_random_uniaxial(1)
+    st, r = e.minimize(p)
+    assert st == lqmin.LQ_OK and r.fire_status == lqmin.FIRE_CONVERGED
+    assert r.max_force == 0.0 and r.rms_force == 0.0 and np.isfinite(r.energy)
