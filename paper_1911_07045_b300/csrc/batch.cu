@@ -74,6 +74,7 @@ void drop_batch_graph(lq_batch *b) {
 
 // work items and reduction slots for tile 32 x ty and z chunk zc
 lq_status build_items(lq_batch *b, int ty, int zc_all, bool shadow) {
+    const int tx = 32;
     std::vector<WorkItem> items;
     std::vector<long long> base(b->solvers.size());
     std::vector<int> zcs(b->solvers.size());
@@ -82,7 +83,7 @@ lq_status build_items(lq_batch *b, int ty, int zc_all, bool shadow) {
         const LatticeDev &L = b->solvers[l]->L;
         int zc = zc_all > 0 ? zc_all : effective_zchunk(b->solvers[l]);
         zcs[l] = zc;
-        int gx = (L.nx + 31) / 32, gy = (L.ny + ty - 1) / ty, gz = (L.nz + zc - 1) / zc;
+        int gx = (L.nx + tx - 1) / tx, gy = (L.ny + ty - 1) / ty, gz = (L.nz + zc - 1) / zc;
         int nblk = gx * gy * gz;
         base[l] = slots;
         slots += std::max(nblk, 1);
@@ -246,7 +247,7 @@ lq_status batch_new(int device, int fp32, int three, lq_batch **out) {
         return e == cudaErrorMemoryAllocation ? LQ_ENOMEM : LQ_ECUDA;
     }
     int tx, ty;
-    step_tile(fp32, three, &tx, &ty);
+    step_tile(fp32, three, 0, &tx, &ty);   // the narrow tiles of batches
     b->ty = ty;          // default tiling: the solvers' own (z chunk 0 = each lattice's)
     b->zchunk = 0;
     *out = b;

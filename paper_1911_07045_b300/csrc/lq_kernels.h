@@ -21,6 +21,7 @@ struct StepLaunch {
     double *partials;
     int zchunk, force_only, fp32, three;
     int idx64;                // 64-bit element indices even where 32 bits would do
+    int wide;                 // 64-wide tiles (wide_tiles)
 };
 
 // one block's share of a batched step: lattice, tile, z range, and its
@@ -30,7 +31,8 @@ struct WorkItem {
 };
 
 dim3 step_grid(const LatticeDev &L, int zchunk, int tx, int ty);
-void step_tile(int fp32, int three, int *tx, int *ty);
+bool wide_tiles(int fp32, int three, int nx);
+void step_tile(int fp32, int three, int nx, int *tx, int *ty);
 cudaError_t prepare_fire_step(int fp32, int three);
 cudaError_t launch_fire_step(const StepLaunch &sl, cudaStream_t stream);
 

@@ -64,7 +64,7 @@ struct DeviceGuard {
 
 int auto_zchunk(const lq_solver *s) {
     int tx, ty;
-    step_tile(s->fp32, s->three, &tx, &ty);
+    step_tile(s->fp32, s->three, s->L.nx, &tx, &ty);
     long long tiles = (long long)((s->L.nx + tx - 1) / tx) * ((s->L.ny + ty - 1) / ty);
     // enough blocks for several waves on 148 SMs, marches of at most 128
     // planes (measured best at 512^3), at least 8 planes to amortise the halo
@@ -115,6 +115,7 @@ StepLaunch make_launch(lq_solver *s, int force_only) {
     sl.three = s->three;
     sl.ext = s->ext;
     sl.idx64 = s->idx64;
+    sl.wide = wide_tiles(s->fp32, s->three, s->L.nx);
     return sl;
 }
 
@@ -122,7 +123,7 @@ void drop_graph(lq_solver *s);
 
 lq_status ensure_partials(lq_solver *s) {
     int tx, ty;
-    step_tile(s->fp32, s->three, &tx, &ty);
+    step_tile(s->fp32, s->three, s->L.nx, &tx, &ty);
     dim3 g = step_grid(s->L, effective_zchunk(s), tx, ty);
     int need = std::max<int>(g.x * g.y * g.z, 148 * 64);
     if (need > s->partials_cap) {

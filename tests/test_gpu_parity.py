@@ -210,3 +210,24 @@ def test_empty_and_zero_length_inputs():
     st, r = e.minimize(p)
     assert st == lqmin.LQ_OK and r.fire_status == lqmin.FIRE_CONVERGED
     assert r.max_force == 0.0 and r.rms_force == 0.0 and np.isfinite(r.energy)
+
+
+def test_wide_tiles_of_wide_one_constant_fp32_lattices(oracle_mod):
+    """One-constant FP32 lattices at least 256 sites wide run 64-wide tiles
+    (the ragged last tile here holds 4 columns); force and FIRE steps against
+    the oracle."""
+    shape = (260, 12, 10)
+    objs = [dict(type="sphere", c=(130.0, 6.0, 5.0), R=3.5, anchor=HOM()),
+            dict(type="wall", axis=1, plane=0, anchor=PLANAR()),
+            dict(type="sites", xyz=[[0, 5, 5], [63, 5, 5], [64, 5, 5], [259, 7, 3]],
+                 anchor=HOM(2.0))]
+    s, o = make_pair(oracle_mod, shape, (2.32, 0.0, 0.0), objs, precision=1)
+    q = np.round(rand_q(o.N, 41) * 2.0 ** 28) / 2.0 ** 28
+    s.set_q(q)
+    sim = o.simulated()
+    assert force_rel_err(s.force(), o.force(q), sim) < FORCE_TOL_FP32
+    fp = dict(synth.FIRE_DEFAULTS, max_iter=10 ** 6, force_tol=1e-14)
+    r = s.step(lqmin.fire_params(**fp), 40)
+    qo, vo, Fo, st = o.fire(q, fp, 40)
+    assert r.iterations == st["iter"] == 40
+    assert np.abs(s.get_q()[:, sim] - qo[:, sim]).max() < 1e-5
