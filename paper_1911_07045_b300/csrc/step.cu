@@ -141,15 +141,16 @@ struct Site5<double> {
 #pragma unroll
         for (int c = 0; c < 5; ++c) out[c] = Prec<double>::drift(q[c], v[c], f[c], alpha, beta, bad);
     }
-    // v_new = v_mix + dt/2 (F_old + F_new) and the site's P, |F|^2, |v|^2
+    // v_new = v_mix + dt/2 (F_old + F_new) = cv v + (cF + dt/2) F_old + dt/2 F_new
+    // (cFh = cF + dt/2) and the site's P, |F|^2, |v|^2
     __device__ static __forceinline__ void kick(const double *vold, const double *fold, const double *fn,
-                                                double cv, double cF, double hdt, double *vn, double &pv,
+                                                double cv, double cFh, double hdt, double *vn, double &pv,
                                                 double &ff, double &vv) {
         pv = ff = vv = 0.0;
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
-            double vx = fma_rn(cv, vold[c], mul_rn(cF, fold[c]));
-            vn[c] = fma_rn(hdt, add_rn(fold[c], fn[c]), vx);
+            double vx = fma_rn(cFh, fold[c], mul_rn(cv, vold[c]));
+            vn[c] = fma_rn(hdt, fn[c], vx);
             pv = fma_rn(fn[c], vn[c], pv);
             ff = fma_rn(fn[c], fn[c], ff);
             vv = fma_rn(vn[c], vn[c], vv);
@@ -187,23 +188,23 @@ struct Site5<float> {
         }
     }
     __device__ static __forceinline__ void kick(const float *vold, const float *fold, const float *fn,
-                                                float cv, float cF, float hdt, float *vn, float &pv,
+                                                float cv, float cFh, float hdt, float *vn, float &pv,
                                                 float &ff, float &vv) {
-        const float2 CV = make_float2(cv, cv), CF = make_float2(cF, cF), H = make_float2(hdt, hdt);
+        const float2 CV = make_float2(cv, cv), CF = make_float2(cFh, cFh), H = make_float2(hdt, hdt);
         float2 p2 = make_float2(0.f, 0.f), f2 = p2, v2 = p2;
 #pragma unroll
         for (int c = 0; c < 4; c += 2) {
             const float2 vo = make_float2(vold[c], vold[c + 1]), fo = make_float2(fold[c], fold[c + 1]);
             const float2 fnew = make_float2(fn[c], fn[c + 1]);
-            const float2 vx = __ffma2_rn(CV, vo, __fmul2_rn(CF, fo));
-            const float2 w = __ffma2_rn(H, __fadd2_rn(fo, fnew), vx);
+            const float2 vx = __ffma2_rn(CF, fo, __fmul2_rn(CV, vo));
+            const float2 w = __ffma2_rn(H, fnew, vx);
             vn[c] = w.x; vn[c + 1] = w.y;
             p2 = __ffma2_rn(fnew, w, p2);
             f2 = __ffma2_rn(fnew, fnew, f2);
             v2 = __ffma2_rn(w, w, v2);
         }
-        const float vx4 = __fmaf_rn(cv, vold[4], __fmul_rn(cF, fold[4]));
-        vn[4] = __fmaf_rn(hdt, __fadd_rn(fold[4], fn[4]), vx4);
+        const float vx4 = __fmaf_rn(cFh, fold[4], __fmul_rn(cv, vold[4]));
+        vn[4] = __fmaf_rn(hdt, fn[4], vx4);
         pv = __fmaf_rn(fn[4], vn[4], __fadd_rn(p2.x, p2.y));
         ff = __fmaf_rn(fn[4], fn[4], __fadd_rn(f2.x, f2.y));
         vv = __fmaf_rn(vn[4], vn[4], __fadd_rn(v2.x, v2.y));
@@ -548,22 +549,27 @@ __device__ __forceinline__ void link_flux(uint8_t ma, uint8_t mb, const typename
 
 template <typename T>
 __device__ __forceinline__ void bulk_force(const T *q, T A, T B, T C, T *out) {
-    T a = q[0], b = q[1], c = q[2], d = q[3], e = q[4], f = -a - d;
-    T s_xx = a * a + b * b + c * c;
-    T s_yy = b * b + d * d + e * e;
-    T s_zz = c * c + e * e + f * f;
-    T s_xy = a * b + b * d + c * e;
-    T s_xz = a * c + b * e + c * f;
-    T s_yz = b * c + d * e + e * f;
-    T tr2 = s_xx + s_yy + s_zz;
-    T g = A + C * tr2;
-    T jq[5];
-    jt_sym(q, jq);
-    out[0] = -(g * jq[0] + B * (s_xx - s_zz));
-    out[1] = -(g * jq[1] + B * T(2) * s_xy);
-    out[2] = -(g * jq[2] + B * T(2) * s_xz);
-    out[3] = -(g * jq[3] + B * (s_yy - s_zz));
-    out[4] = -(g * jq[4] + B * T(2) * s_yz);
+    // -(A + C tr Q^2) J^T q - B d/dq tr Q^3 / 3 with f = Qzz = -(a + d): J^T q =
+    // (2a + d, 2b, 2c, a + 2d, 2e) = j, tr Q^2 = q . j, and the cubic term
+    // needs (Q^2)_xx - (Q^2)_zz = b^2 - e^2 - d (2a + d), (Q^2)_yy - (Q^2)_zz =
+    // b^2 - c^2 - a (a + 2d), (Q^2)_xy = ce - bf, (Q^2)_xz = be - cd,
+    // (Q^2)_yz = bc - ae (the squares of Qzz folded into j)
+    const T a = q[0], b = q[1], c = q[2], d = q[3], e = q[4];
+    const T j0 = T(2) * a + d, j3 = T(2) * d + a, j1 = T(2) * b, j2 = T(2) * c, j4 = T(2) * e;
+    const T tr2 = a * j0 + b * j1 + c * j2 + d * j3 + e * j4;
+    const T bb = b * b;
+    const T dxz = (bb - e * e) - d * j0;
+    const T dyz = (bb - c * c) - a * j3;
+    const T sxy = c * e + b * (a + d);
+    const T sxz = b * e - c * d;
+    const T syz = b * c - a * e;
+    const T ng = -(A + C * tr2);
+    const T nB = -B, n2B = T(-2) * B;
+    out[0] = ng * j0 + nB * dxz;
+    out[1] = ng * j1 + n2B * sxy;
+    out[2] = ng * j2 + n2B * sxz;
+    out[3] = ng * j3 + nB * dyz;
+    out[4] = ng * j4 + n2B * syz;
 }
 
 // anchoring force of one record (Nobili-Durand or Fournier-Galatola)
@@ -871,6 +877,8 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
         beta = T(args.st->c_beta * P::scale);
         hdt = T(args.st->c_kick);
     }
+    // the old force's weight in the kick, cF + dt/2, rounded once
+    const T cFh = fo_mode ? T(0) : T(args.st->cF + args.st->c_kick);
 
     // ring sites of a staged plane: top row, bottom row, left/right columns
     constexpr int NRING = 2 * SM::SX + 2 * TY;
@@ -1208,7 +1216,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                 for (int c = 0; c < 5; ++c) Fout[c * N + i] = Fn[c];
             } else {
                 T pv, ff, vv, vn[5];
-                Site5<T>::kick(vold, fold, Fn, cv, cF, hdt, vn, pv, ff, vv);
+                Site5<T>::kick(vold, fold, Fn, cv, cFh, hdt, vn, pv, ff, vv);
 #pragma unroll
                 for (int c = 0; c < 5; ++c) {
                     __stcs(qout + c * N + i, q0[c]);
