@@ -94,10 +94,10 @@ struct Prec<double> {
     static constexpr double scale = 1.0;   // storage unit of Q
     __device__ static __forceinline__ double val(double q) { return q; }
     __device__ static __forceinline__ double diff(double a, double b) { return b - a; }
-    // q + alpha v + beta F; never out of range in FP64
+    // q + alpha v + beta F as two fused multiply-adds; never out of range in FP64
     __device__ static __forceinline__ double drift(double q, double v, double f, double alpha,
                                                    double beta, bool &bad) {
-        return __dadd_rn(q, __fma_rn(alpha, v, __dmul_rn(beta, f)));
+        return __fma_rn(alpha, v, __fma_rn(beta, f, q));
     }
 };
 template <>
@@ -413,6 +413,8 @@ struct Smem {
     static constexpr int SLOT_BYTES = 5 * sizeof(QS) * PL;      // multiple of 16
     unsigned char *Q;  // [slots] x SLOT_BYTES
     T *X;              // [2][2][5][PL] cross terms (general path)
+    T *D;              // [2][2][5][PL] FP64 three-constant form: the central
+                       // differences D_y, D_z of a plane (regular path)
     uint8_t *M;        // [slots][PL]
     __device__ __forceinline__ int idx(int lx, int ly) const { return ly * SX + lx; }
     __device__ __forceinline__ QS &q(int slot, int c, int lx, int ly) {
@@ -457,7 +459,19 @@ struct Smem {
     __device__ __forceinline__ T &x(int slot, int ax, int c, int lx, int ly) {
         return X[((slot * 2 + ax) * 5 + c) * PL + idx(lx, ly)];
     }
+    __device__ __forceinline__ T &d(int slot, int ax, int c, int lx, int ly) {
+        return D[((slot * 2 + ax) * 5 + c) * PL + idx(lx, ly)];
+    }
 };
+
+// the FP64 three-constant form shares the central differences of a plane
+// between the mixed differences of neighbouring sites (FP64 operations are
+// that form's limit): D_y(s) = q(s + y) - q(s - y) and D_z(s) = q(s + z) -
+// q(s - z), so that E_xy(j) = D_y(j + x) - D_y(j - x), E_xz(j) = D_z(j + x) -
+// D_z(j - x) and E_yz(j) = D_z(j + y) - D_z(j - y) -- the same operations in
+// the same order as (a - b) - (c - d) on the four diagonal neighbours
+template <typename T, int FORM>
+constexpr bool shared_diffs() { return sizeof(T) == 8 && FORM == 1; }
 
 // mean of the allowed one-sided differences along axis K at (lx, ly) of
 // plane slot sc; splus / sminus are the slots of the planes above / below
@@ -759,7 +773,7 @@ struct Stencil<float> {
 //   F4 = 2 L1 s4 + L23 (y4 + z4) + L23/4 (a2 + b1 - c0)
 template <bool THREE, typename T, int TX, int TY>
 __device__ __forceinline__ void regular_force(Smem<T, TX, TY> &S, int lx, int ly, int sc, int sp,
-                                              int sm, T L1s, T L23s, T L2q, T L3q, T *Fd) {
+                                              int sm, int dslot, T L1s, T L23s, T L2q, T L3q, T *Fd) {
     using ST = Stencil<T>;
     using QS = typename Prec<T>::Q;
     T dx[5], dy[5], dz[5];
@@ -789,7 +803,16 @@ __device__ __forceinline__ void regular_force(Smem<T, TX, TY> &S, int lx, int ly
     Fd[4] = L1s2 * s4;
     if (!THREE) return;
     T a[5], b[5], c[5];   // E_xy, E_xz, E_yz
-    {
+    if constexpr (sizeof(T) == 8) {
+        // from the plane's shared central differences (shared_diffs)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) a[k] = S.d(dslot, 0, k, lx + 1, ly) - S.d(dslot, 0, k, lx - 1, ly);
+#pragma unroll
+        for (int k = 1; k < 5; ++k) b[k] = S.d(dslot, 1, k, lx + 1, ly) - S.d(dslot, 1, k, lx - 1, ly);
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+            if (k != 3) c[k] = S.d(dslot, 1, k, lx, ly + 1) - S.d(dslot, 1, k, lx, ly - 1);
+    } else {
         QS p0[5], p1[5], p2[5], p3[5];
         S.load5(sc, lx + 1, ly + 1, p0);
         S.load5(sc, lx + 1, ly - 1, p1);
@@ -839,7 +862,9 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
     SM S;
     S.Q = smem_raw;
     S.X = reinterpret_cast<T *>(smem_raw + NSLOT * SM::SLOT_BYTES);
-    S.M = reinterpret_cast<uint8_t *>(S.X + (THREE ? 2 * 2 * 5 * SM::PL : 0));
+    S.D = S.X + (THREE ? 2 * 2 * 5 * SM::PL : 0);
+    constexpr bool DIFFS = sizeof(T) == 8 && THREE;
+    S.M = reinterpret_cast<uint8_t *>(S.D + (DIFFS ? 2 * 2 * 5 * SM::PL : 0));
     const LatticeDev L = args.L;
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const int x0 = bx * TX, y0 = by * TY;
@@ -960,6 +985,33 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
     }
     __syncthreads();   // the first regularity check reads neighbours' masks
 
+    // central differences of plane `pz` (slot s_pl, the planes below and
+    // above in s_dn, s_up) into the difference slot pz & 1: D_z at the tile,
+    // the ring columns and rows, D_y at the tile and the ring columns
+    auto plane_diffs = [&](int pz, int s_pl, int s_dn, int s_up) {
+        const int ds = pz & 1;
+        auto one = [&](int sx, int sy, bool with_y) {
+            QS u[5], w[5];
+            S.load5(s_up, sx, sy, u);
+            S.load5(s_dn, sx, sy, w);
+#pragma unroll
+            for (int c = 0; c < 5; ++c) S.d(ds, 1, c, sx, sy) = T(u[c]) - T(w[c]);
+            if (with_y) {
+                S.load5(s_pl, sx, sy + 1, u);
+                S.load5(s_pl, sx, sy - 1, w);
+#pragma unroll
+                for (int c = 0; c < 5; ++c) S.d(ds, 0, c, sx, sy) = T(u[c]) - T(w[c]);
+            }
+        };
+        one(lx, ly, true);
+        if (rx >= 0) {
+            const bool col = (rx == 0 || rx == SM::SX - 1) && ry >= 1 && ry <= TY;
+            const bool row = (ry == 0 || ry == SM::SY - 1) && rx >= 1 && rx <= TX;
+            if (col || row) one(rx, ry, col);
+        }
+    };
+    if constexpr (shared_diffs<T, FORM>()) plane_diffs(z0, slot_of(z0), slot_of(z0 - 1), slot_of(z0 + 1));
+
     const T L1 = args.L1, L23 = args.L2 + args.L3;
     // chiral / cubic terms: taken by the general path on every plane
     constexpr bool ext = FORM == 2;
@@ -1001,10 +1053,15 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
         }
         // the barrier publishes plane z+2 and decides the path of this plane
         const bool all_reg = __syncthreads_and(reg) != 0;
+        // the next plane's central differences: planes z .. z+2 are published,
+        // and the slot (z+1) & 1 was last read by the previous plane's force
+        if constexpr (shared_diffs<T, FORM>()) {
+            if (z + 1 < z1) plane_diffs(z + 1, sp, sc, s2);
+        }
 
         T Fd[5];
         if (all_reg) {
-            if (own) regular_force<THREE>(S, lx, ly, sc, sp, sm, L1s, L23s, L2q, L3q, Fd);
+            if (own) regular_force<THREE>(S, lx, ly, sc, sp, sm, z & 1, L1s, L23s, L2q, L3q, Fd);
         } else {
             // general path (planes touching objects or open edges): the z
             // link below and the in-plane means are rebuilt on every such plane
@@ -1304,7 +1361,9 @@ template <typename T, bool THREE, int TX, int TY>
 static size_t step_smem_bytes() {
     using SM = Smem<T, TX, TY>;
     constexpr int PL = SM::PL;
-    size_t b = 5 * (size_t)SM::SLOT_BYTES + sizeof(T) * (THREE ? 2 * 2 * 5 * PL : 0) + 5 * PL;
+    constexpr bool DIFFS = sizeof(T) == 8 && THREE;   // shared_diffs (form 1; unused by form 2)
+    size_t b = 5 * (size_t)SM::SLOT_BYTES + sizeof(T) * (THREE ? 2 * 2 * 5 * PL : 0) +
+               sizeof(T) * (DIFFS ? 2 * 2 * 5 * PL : 0) + 5 * PL;
     return (b + 15) & ~size_t(15);
 }
 
