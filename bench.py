@@ -45,14 +45,15 @@ DESIGN_BYTES = {"fp32": 6 * 5 * 4 + 1, "fp64": 6 * 5 * 8 + 1}
 DRAM_BYTES_PER_SITE = {"fp32": 2.035445e9 / 256 ** 3, "fp64": 4.203127e9 / 256 ** 3}
 # FP64 form: bound by the FP64 pipe (2 FP64 operations per clock per SM).
 # FP64 arithmetic operations per site-update of the regular three-constant
-# site, counted from the kernel's arithmetic: stencil 104 (second
+# site, counted from the kernel's arithmetic: stencil 94 (second
 # differences 15 x 2, the site's central differences D_y, D_z 10, mixed
-# differences from them 13, sums 10, one- and three-constant combinations
-# 41), bulk force 33, force sum 5, drift 10, mixing and kick 15, reductions
-# 18 (ring sites' drift and central differences are not counted)
-FP64_OPS_PER_SITE = 185
+# differences from them 13, shared partial sums 12, one- and three-constant
+# combinations 29), bulk force 33, force sum 5, drift 10, mixing and kick
+# 15, reductions 18 (ring sites' drift and central differences are not
+# counted)
+FP64_OPS_PER_SITE = 175
 # the same for a one-constant site: the stencil is 15 second differences (add
-# + FMA), 10 adds for the three-axis sums and 8 scalings (48 instead of 104)
+# + FMA), 10 adds for the three-axis sums and 8 scalings (48 instead of 94)
 FP64_OPS_PER_SITE_1C = 129
 FP64_OPS_PER_CLK_SM = 2
 N_SM = 148

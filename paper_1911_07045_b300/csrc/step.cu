@@ -793,15 +793,24 @@ __device__ __forceinline__ void regular_force(Smem<T, TX, TY> &S, int lx, int ly
 #pragma unroll
         for (int c = 0; c < 5; ++c) dz[c] = ST::sec(a[c], b[c], c0[c]);
     }
-    T s0 = dx[0] + dy[0] + dz[0], s1 = dx[1] + dy[1] + dz[1], s2 = dx[2] + dy[2] + dz[2];
-    T s3 = dx[3] + dy[3] + dz[3], s4 = dx[4] + dy[4] + dz[4];
     const T L1s2 = T(2) * L1s;
-    Fd[0] = L1s * (T(2) * s0 + s3);
-    Fd[1] = L1s2 * s1;
-    Fd[2] = L1s2 * s2;
-    Fd[3] = L1s * (s0 + T(2) * s3);
-    Fd[4] = L1s2 * s4;
-    if (!THREE) return;
+    if (!THREE || sizeof(T) == 4) {
+        T s0 = dx[0] + dy[0] + dz[0], s1 = dx[1] + dy[1] + dz[1], s2 = dx[2] + dy[2] + dz[2];
+        T s3 = dx[3] + dy[3] + dz[3], s4 = dx[4] + dy[4] + dz[4];
+        Fd[0] = L1s * (T(2) * s0 + s3);
+        Fd[1] = L1s2 * s1;
+        Fd[2] = L1s2 * s2;
+        Fd[3] = L1s * (s0 + T(2) * s3);
+        Fd[4] = L1s2 * s4;
+        if (!THREE) return;
+    }
+    // FP64: the L1 sums s_c = x_c + y_c + z_c and the L2 + L3 sums (below)
+    // share their partial sums (in the FP32 form this costs a register and
+    // measured 13% slower, so that form keeps separate sums)
+    const T p0 = dx[0] + dz[0], p3 = dy[3] + dz[3];
+    const T t1 = dx[1] + dy[1], t2 = dx[2] + dz[2], t4 = dy[4] + dz[4];
+    const T s0 = p0 + dy[0], s1 = t1 + dz[1], s2 = t2 + dy[2], s3 = p3 + dx[3], s4 = t4 + dx[4];
+    const T t0 = p0 + dz[3], t3 = p3 + dz[0];
     T a[5], b[5], c[5];   // E_xy, E_xz, E_yz
     if constexpr (sizeof(T) == 8) {
         // from the plane's shared central differences (shared_diffs)
@@ -835,11 +844,19 @@ __device__ __forceinline__ void regular_force(Smem<T, TX, TY> &S, int lx, int ly
             if (k != 3) c[k] = ST::mix(p0[k], p1[k], p2[k], p3[k]);
     }
     const T kq = T(0.25) * L23s;
-    Fd[0] += L23s * (dx[0] + dz[0] + dz[3]) + kq * (a[1] - c[4]);
-    Fd[1] += L23s * (dx[1] + dy[1]) + kq * ((a[0] + a[3]) + (b[4] + c[2]));
-    Fd[2] += L23s * (dx[2] + dz[2]) + kq * (a[4] - b[3] + c[1]);
-    Fd[3] += L23s * (dy[3] + dz[0] + dz[3]) + kq * (a[1] - b[2]);
-    Fd[4] += L23s * (dy[4] + dz[4]) + kq * (a[2] + b[1] - c[0]);
+    if constexpr (sizeof(T) == 8) {
+        Fd[0] = L1s * (T(2) * s0 + s3) + (L23s * t0 + kq * (a[1] - c[4]));
+        Fd[1] = L1s2 * s1 + (L23s * t1 + kq * ((a[0] + a[3]) + (b[4] + c[2])));
+        Fd[2] = L1s2 * s2 + (L23s * t2 + kq * (a[4] - b[3] + c[1]));
+        Fd[3] = L1s * (s0 + T(2) * s3) + (L23s * t3 + kq * (a[1] - b[2]));
+        Fd[4] = L1s2 * s4 + (L23s * t4 + kq * (a[2] + b[1] - c[0]));
+    } else {
+        Fd[0] += L23s * (dx[0] + dz[0] + dz[3]) + kq * (a[1] - c[4]);
+        Fd[1] += L23s * (dx[1] + dy[1]) + kq * ((a[0] + a[3]) + (b[4] + c[2]));
+        Fd[2] += L23s * (dx[2] + dz[2]) + kq * (a[4] - b[3] + c[1]);
+        Fd[3] += L23s * (dy[3] + dz[0] + dz[3]) + kq * (a[1] - b[2]);
+        Fd[4] += L23s * (dy[4] + dz[4]) + kq * (a[2] + b[1] - c[0]);
+    }
     (void)L2q; (void)L3q;
 }
 
