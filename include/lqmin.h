@@ -446,6 +446,18 @@ lq_status lq_energy_noalloc(const lq_lattice *lattice, const lq_material *materi
                             const double *q_dev, const uint8_t *mask_dev, double *parts_dev,
                             void *cuda_stream);
 
+/* ---- testing: host-side fault injection ------------------------------------------
+   After lq_inject_fault(kind, after), the (after + 1)-th device allocation
+   (LQ_FAULT_DEVICE_ALLOC) or step-kernel launch (LQ_FAULT_STEP_LAUNCH, one
+   launch of the single-lattice or the batched step kernel, direct or while
+   a CUDA graph is captured) that the library makes fails as if CUDA had
+   returned out-of-memory or a launch failure: nothing is allocated or
+   launched for it, and the calling entry point returns LQ_ENOMEM or
+   LQ_ECUDA.  No device fault is ever made.  One-shot and process-wide;
+   LQ_FAULT_NONE cancels.  LQ_EINVAL for an unknown kind or after < 0. */
+enum { LQ_FAULT_NONE = 0, LQ_FAULT_DEVICE_ALLOC = 1, LQ_FAULT_STEP_LAUNCH = 2 };
+lq_status lq_inject_fault(int kind, int64_t after);
+
 /* ---- tuning ---------------------------------------------------------------------- */
 
 /* Number of z planes one thread block marches through (0 = automatic). */

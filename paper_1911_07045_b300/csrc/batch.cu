@@ -104,13 +104,13 @@ lq_status build_items(lq_batch *b, int ty, int zc_all, bool shadow) {
     if ((int)items.size() > b->items_cap) {
         cudaFree(b->items);
         b->items = nullptr;
-        BK(cudaMalloc(&b->items, items.size() * sizeof(WorkItem)));
+        BK(dev_malloc(&b->items, items.size() * sizeof(WorkItem)));
         b->items_cap = (int)items.size();
     }
     if (slots > b->partials_cap) {
         cudaFree(b->partials);
         b->partials = nullptr;
-        BK(cudaMalloc(&b->partials, slots * 4 * sizeof(double)));
+        BK(dev_malloc(&b->partials, slots * 4 * sizeof(double)));
         b->partials_cap = slots;
     }
     BK(cudaMemcpyAsync(b->items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
@@ -240,7 +240,7 @@ lq_status batch_new(int device, int fp32, int three, lq_batch **out) {
         for (int i32 : {0, 1})
             for (int form : {three ? 1 : 0, three ? 2 : 0})
                 if (e == cudaSuccess) e = prepare_fire_batch(fp32, form, ty, i32);
-    if (e == cudaSuccess) e = cudaMalloc(&b->running, sizeof(unsigned int));
+    if (e == cudaSuccess) e = dev_malloc(&b->running, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMallocHost(&b->running_host, sizeof(unsigned int));
     if (e != cudaSuccess) {
         lq_batch_destroy(b);
@@ -277,10 +277,10 @@ lq_status batch_set_members(lq_batch *b, lq_solver *const *solvers, int n) {
         b->cap = 0;
         size_t ab = step_args_bytes(b->fp32);
         int cap = std::max(n, 8);
-        BK(cudaMalloc(&b->args, ab * cap));
-        BK(cudaMalloc(&b->shadow_args, ab * cap));
-        BK(cudaMalloc(&b->shadow, sizeof(FireDev) * cap));
-        BK(cudaMalloc(&b->states, sizeof(FireDev *) * cap));
+        BK(dev_malloc(&b->args, ab * cap));
+        BK(dev_malloc(&b->shadow_args, ab * cap));
+        BK(dev_malloc(&b->shadow, sizeof(FireDev) * cap));
+        BK(dev_malloc(&b->states, sizeof(FireDev *) * cap));
         b->cap = cap;
     }
     std::vector<FireDev *> st(std::max(n, 1));

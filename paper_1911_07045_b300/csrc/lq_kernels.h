@@ -39,6 +39,20 @@ cudaError_t launch_fire_step(const StepLaunch &sl, cudaStream_t stream);
 // true when the state arrays of a lattice of N sites are indexed in 32 bits
 bool step_index32(long long N);
 
+// host-side fault injection (lq_inject_fault): true once when an injected
+// failure of this kind (1 device allocation, 2 step-kernel launch) is due
+bool fault_due(int kind);
+// cudaMalloc, or cudaErrorMemoryAllocation without allocating when an
+// injected allocation failure is due
+template <typename P>
+inline cudaError_t dev_malloc(P **p, size_t bytes) {
+    if (fault_due(1)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(reinterpret_cast<void **>(p), bytes);
+}
+
 // batched steps (tile 32 x ty, ty in {4, 8}; form 0 one-constant, 1
 // three-constant, 2 with the chiral / cubic terms; idx32: every lattice of
 // the batch indexed in 32 bits)

@@ -5,6 +5,7 @@
 // custom boundary text format (section VI, custom boundary files) and the
 // dipolar initial condition about a colloid (section IV.A).
 #include <algorithm>
+#include <atomic>
 #include <cctype>
 #include <cmath>
 #include <cstdio>
@@ -19,6 +20,29 @@
 
 using namespace lq;
 using namespace lq::detail;
+
+namespace lq {
+
+// injected failures: kind and the number of operations of that kind that
+// still succeed before the one that fails
+static std::atomic<int> g_fault_kind{0};
+static std::atomic<long long> g_fault_after{0};
+
+bool fault_due(int kind) {
+    if (g_fault_kind.load(std::memory_order_acquire) != kind) return false;
+    long long left = g_fault_after.load(std::memory_order_acquire);
+    for (;;) {
+        if (g_fault_kind.load(std::memory_order_acquire) != kind) return false;
+        if (left > 0) {
+            if (g_fault_after.compare_exchange_weak(left, left - 1)) return false;
+            continue;
+        }
+        int k = kind;
+        return g_fault_kind.compare_exchange_strong(k, 0);   // one-shot
+    }
+}
+
+}  // namespace lq
 
 namespace {
 
@@ -156,6 +180,14 @@ bool parse_boundary(const char *text, Parsed *P) {
 }  // namespace
 
 extern "C" {
+
+lq_status lq_inject_fault(int kind, int64_t after) {
+    if (kind < LQ_FAULT_NONE || kind > LQ_FAULT_STEP_LAUNCH || after < 0) return LQ_EINVAL;
+    g_fault_kind.store(LQ_FAULT_NONE, std::memory_order_release);
+    g_fault_after.store(after, std::memory_order_release);
+    g_fault_kind.store(kind, std::memory_order_release);
+    return LQ_OK;
+}
 
 lq_status lq_frank_to_landau(double K1, double K2, double K3, double K24, double q0, double S,
                              double L[5]) {

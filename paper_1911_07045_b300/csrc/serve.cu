@@ -140,21 +140,25 @@ void finish(lq_server *sv, Active &a, lq_status st, bool have_result) {
     sv->cv.notify_all();
 }
 
-void rebuild_batches(lq_server *sv) {
+// false when a batch could not be built (retried on the next round)
+bool rebuild_batches(lq_server *sv) {
     std::vector<lq_solver *> group[2];
     for (Active &a : sv->active) group[a.s->three ? 1 : 0].push_back(a.s);
+    bool ok = true;
     for (int g = 0; g < 2; ++g) {
         if (!sv->batch[g]) {
             if (group[g].empty()) continue;
-            if (batch_new(sv->device, sv->fp32, g, &sv->batch[g]) != LQ_OK) continue;
+            if (batch_new(sv->device, sv->fp32, g, &sv->batch[g]) != LQ_OK) { ok = false; continue; }
         }
-        batch_set_members(sv->batch[g], group[g].data(), (int)group[g].size());
+        if (batch_set_members(sv->batch[g], group[g].data(), (int)group[g].size()) != LQ_OK) ok = false;
     }
+    return ok;
 }
 
 void worker_loop(lq_server *sv) {
     cudaSetDevice(sv->device);
     bool changed = false;
+    int failed_rounds = 0;   // consecutive rounds without a batch or with a failed launch
     for (;;) {
         // admit what the budget and the slot limit allow
         std::vector<Request> admit;
@@ -190,20 +194,42 @@ void worker_loop(lq_server *sv) {
             changed = true;
         }
         if (sv->active.empty()) continue;
+        if (changed) changed = !rebuild_batches(sv);   // a failed build is retried
         if (changed) {
-            rebuild_batches(sv);   // a failed rebuild leaves the batch unlaunchable
-            changed = false;
+            // no batch for this round: fail everything after repeated failures
+            if (++failed_rounds >= 3) {
+                for (Active &a : sv->active) finish(sv, a, LQ_ENOMEM, false);
+                sv->active.clear();
+                failed_rounds = 0;
+                changed = true;    // the batches still name the finished solves
+            }
+            continue;
         }
         // one round of the persistent kernel over every active solve
         long long sites = 0;
         for (Active &a : sv->active) sites += a.s->L.N;
         int k = (int)std::max(1LL, std::min(64LL, (1LL << 27) / std::max(1LL, sites)));
         unsigned int running_total = 0;
+        lq_status round_err = LQ_OK;
         for (int g = 0; g < 2; ++g) {
             if (batch_members(sv->batch[g]) == 0) continue;
             unsigned int running = 0;
-            if (batch_round(sv->batch[g], k, &running) == LQ_OK) running_total += running;
+            lq_status st = batch_round(sv->batch[g], k, &running);
+            if (st == LQ_OK) running_total += running;
+            else round_err = st;
         }
+        if (round_err != LQ_OK) {
+            // a round that failed (its lattices stay resident): rebuild and
+            // retry; after three failures in a row its solves fail with it
+            changed = true;
+            if (++failed_rounds >= 3) {
+                for (Active &a : sv->active) finish(sv, a, round_err, false);
+                sv->active.clear();
+                failed_rounds = 0;
+            }
+            continue;   // changed is set: the next round rebuilds the batches
+        }
+        failed_rounds = 0;
         // retire the finished and the timed-out
         auto now = Clock::now();
         bool any_done = running_total < sv->active.size();

@@ -130,7 +130,7 @@ lq_status ensure_partials(lq_solver *s) {
         drop_graph(s);  // captured launches hold the old pointer
         if (s->partials) cudaFree(s->partials);
         s->partials = nullptr;
-        CK(cudaMalloc(&s->partials, sizeof(double) * 4 * (size_t)need));
+        CK(dev_malloc(&s->partials, sizeof(double) * 4 * (size_t)need));
         s->partials_cap = need;
     }
     return LQ_OK;
@@ -168,7 +168,7 @@ lq_status build_geometry(lq_solver *s) {
         d.n = (long long)h.xyz.size() / 3;
         if (d.n > 0) {
             int32_t *dx = nullptr;
-            cudaError_t e = cudaMalloc(&dx, h.xyz.size() * sizeof(int32_t));
+            cudaError_t e = dev_malloc(&dx, h.xyz.size() * sizeof(int32_t));
             if (e != cudaSuccess) { cleanup(); return fail(s, LQ_ENOMEM, "geometry: %s", cudaGetErrorString(e)); }
             temps.push_back(dx);
             cudaMemcpyAsync(dx, h.xyz.data(), h.xyz.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
@@ -182,7 +182,7 @@ lq_status build_geometry(lq_solver *s) {
                 for (int k = 0; k < 3; ++k) ps[t].dir[k] = h.per_site[t].dir[k];
             }
             AnchorSpecDev *dp = nullptr;
-            cudaError_t e = cudaMalloc(&dp, std::max<size_t>(1, ps.size()) * sizeof(AnchorSpecDev));
+            cudaError_t e = dev_malloc(&dp, std::max<size_t>(1, ps.size()) * sizeof(AnchorSpecDev));
             if (e != cudaSuccess) { cleanup(); return fail(s, LQ_ENOMEM, "geometry: %s", cudaGetErrorString(e)); }
             temps.push_back(dp);
             cudaMemcpyAsync(dp, ps.data(), ps.size() * sizeof(AnchorSpecDev), cudaMemcpyHostToDevice, st);
@@ -205,13 +205,13 @@ lq_status build_geometry(lq_solver *s) {
                         "geometry: %s: %s", #call, cudaGetErrorString(e));                \
         }                                                                                 \
     } while (0)
-    GK(cudaMalloc(&dobj, sizeof(GeoObjDev) * hobj.size()));
+    GK(dev_malloc(&dobj, sizeof(GeoObjDev) * hobj.size()));
     temps.push_back(dobj);
     GK(cudaMemcpyAsync(dobj, hobj.data(), sizeof(GeoObjDev) * hobj.size(), cudaMemcpyHostToDevice, st));
-    GK(cudaMalloc(&owner, sizeof(int) * L.N));
+    GK(dev_malloc(&owner, sizeof(int) * L.N));
     temps.push_back(owner);
     if (any_anch) {
-        GK(cudaMalloc(&xclaim, sizeof(unsigned long long) * L.N));
+        GK(dev_malloc(&xclaim, sizeof(unsigned long long) * L.N));
         temps.push_back(xclaim);
         GK(cudaMemsetAsync(xclaim, 0xff, sizeof(unsigned long long) * L.N, st));
     }
@@ -222,7 +222,7 @@ lq_status build_geometry(lq_solver *s) {
     }
     GK(geo_mask(L, owner, xclaim, s->mask, st));
     long long rows = (long long)L.ny * L.nz;
-    GK(cudaMalloc(&counts, sizeof(int) * rows));
+    GK(dev_malloc(&counts, sizeof(int) * rows));
     temps.push_back(counts);
     GK(geo_row_count(L, s->mask, counts, st));
     std::vector<int> hc(rows), hstart(rows + 1);
@@ -237,9 +237,9 @@ lq_status build_geometry(lq_solver *s) {
     if (s->recs) cudaFree(s->recs);
     s->row_start = nullptr; s->rec_x = nullptr; s->recs = nullptr;
     size_t rsize = s->fp32 ? sizeof(AnchorRec<float>) : sizeof(AnchorRec<double>);
-    GK(cudaMalloc(&s->row_start, sizeof(int) * (rows + 1)));
-    GK(cudaMalloc(&s->rec_x, sizeof(int) * std::max<long long>(1, acc)));
-    GK(cudaMalloc(&s->recs, rsize * std::max<long long>(1, acc)));
+    GK(dev_malloc(&s->row_start, sizeof(int) * (rows + 1)));
+    GK(dev_malloc(&s->rec_x, sizeof(int) * std::max<long long>(1, acc)));
+    GK(dev_malloc(&s->recs, rsize * std::max<long long>(1, acc)));
     GK(cudaMemcpyAsync(s->row_start, hstart.data(), sizeof(int) * (rows + 1), cudaMemcpyHostToDevice, st));
     GK(geo_fill(L, s->mask, owner, xclaim, dobj, s->S0, s->row_start, s->rec_x, s->recs, s->fp32, st));
     s->nrec = acc;
@@ -501,18 +501,18 @@ lq_status lq_create(const lq_lattice *lat, const lq_material *mat, int precision
     size_t sb = 5 * (size_t)N * s->esize;
     cudaError_t e;
     for (int b = 0; b < 2; ++b) {
-        if ((e = cudaMalloc(&s->q[b], sb)) != cudaSuccess) return bad(e);
-        if ((e = cudaMalloc(&s->v[b], sb)) != cudaSuccess) return bad(e);
-        if ((e = cudaMalloc(&s->F[b], sb)) != cudaSuccess) return bad(e);
+        if ((e = dev_malloc(&s->q[b], sb)) != cudaSuccess) return bad(e);
+        if ((e = dev_malloc(&s->v[b], sb)) != cudaSuccess) return bad(e);
+        if ((e = dev_malloc(&s->F[b], sb)) != cudaSuccess) return bad(e);
         if ((e = cudaMemsetAsync(s->q[b], 0, sb, s->stream)) != cudaSuccess) return bad(e);
         if ((e = cudaMemsetAsync(s->v[b], 0, sb, s->stream)) != cudaSuccess) return bad(e);
         if ((e = cudaMemsetAsync(s->F[b], 0, sb, s->stream)) != cudaSuccess) return bad(e);
     }
-    if ((e = cudaMalloc(&s->mask, (size_t)N)) != cudaSuccess) return bad(e);
-    if ((e = cudaMalloc(&s->xfer, 5 * (size_t)N * sizeof(double))) != cudaSuccess) return bad(e);
-    if ((e = cudaMalloc(&s->st, sizeof(FireDev))) != cudaSuccess) return bad(e);
+    if ((e = dev_malloc(&s->mask, (size_t)N)) != cudaSuccess) return bad(e);
+    if ((e = dev_malloc(&s->xfer, 5 * (size_t)N * sizeof(double))) != cudaSuccess) return bad(e);
+    if ((e = dev_malloc(&s->st, sizeof(FireDev))) != cudaSuccess) return bad(e);
     if ((e = cudaMemsetAsync(s->st, 0, sizeof(FireDev), s->stream)) != cudaSuccess) return bad(e);
-    if ((e = cudaMalloc(&s->out3, 4 * sizeof(double))) != cudaSuccess) return bad(e);
+    if ((e = dev_malloc(&s->out3, 4 * sizeof(double))) != cudaSuccess) return bad(e);
     if ((e = cudaMallocHost(&s->st_host, sizeof(FireDev))) != cudaSuccess) return bad(e);
     memset(s->st_host, 0, sizeof(FireDev));
     if ((e = prepare_fire_step(s->fp32, s->three)) != cudaSuccess) return bad(e);

@@ -1500,6 +1500,7 @@ struct LaunchStep {
 };
 
 cudaError_t launch_fire_step(const StepLaunch &sl, cudaStream_t stream) {
+    if (fault_due(2)) return cudaErrorLaunchFailure;   // injected: nothing is launched
     const int form = sl.three ? (sl.ext ? 2 : 1) : 0;
     return dispatch_single(sl.fp32, form, step_index32(sl.L.N) && !sl.idx64, LaunchStep{sl, stream});
 }
@@ -1556,6 +1557,7 @@ int fire_batch_blocks_per_sm(int fp32, int form, int ty, int idx32) {
 
 cudaError_t launch_fire_batch(int fp32, int form, int ty, int idx32, const void *dev_args,
                               const WorkItem *items, int nitems, int grid, cudaStream_t stream) {
+    if (fault_due(2)) return cudaErrorLaunchFailure;   // injected: nothing is launched
     return dispatch(fp32, form, ty, idx32 != 0, LaunchBatch{dev_args, items, nitems, grid, stream});
 }
 

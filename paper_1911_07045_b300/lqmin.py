@@ -41,7 +41,7 @@ EXPORTS = [
     "lq_server_poll", "lq_server_wait", "lq_server_stats_get", "lq_boundary_check",
     "lq_add_boundary_text", "lq_load_boundary_file", "lq_object_count", "lq_move_object",
     "lq_clear_objects", "lq_set_material", "lq_clone", "lq_pmf_sweep", "lq_init_dipolar",
-    "lq_frank_to_landau", "lq_set_index_width",
+    "lq_frank_to_landau", "lq_set_index_width", "lq_inject_fault",
 ]
 
 
@@ -178,6 +178,7 @@ def load(path: str = LIB_PATH):
         "lq_init_dipolar": (C.c_int, [S, C.POINTER(C.c_double), C.POINTER(C.c_double), d, d]),
         "lq_frank_to_landau": (C.c_int, [d, d, d, d, d, d, C.POINTER(C.c_double)]),
         "lq_set_index_width": (C.c_int, [S, C.c_int]),
+        "lq_inject_fault": (C.c_int, [C.c_int, i64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -225,6 +226,16 @@ def frank_to_landau(K1, K2, K3, K24, q0, S):
     if st != LQ_OK:
         raise LqError(st, "lq_frank_to_landau: S must be positive and inputs finite")
     return dict(zip(("L1", "L2", "L3", "L4", "L6"), list(out)))
+
+
+LQ_FAULT_NONE, LQ_FAULT_DEVICE_ALLOC, LQ_FAULT_STEP_LAUNCH = 0, 1, 2
+
+
+def inject_fault(kind, after=0):
+    """Host-side fault injection for tests (see ``lq_inject_fault``)."""
+    st = load().lq_inject_fault(int(kind), int(after))
+    if st != LQ_OK:
+        raise LqError(st, "lq_inject_fault")
 
 
 def boundary_check(text):
