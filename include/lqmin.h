@@ -457,6 +457,13 @@ lq_status lq_energy_noalloc(const lq_lattice *lattice, const lq_material *materi
    LQ_FAULT_NONE cancels.  LQ_EINVAL for an unknown kind or after < 0. */
 enum { LQ_FAULT_NONE = 0, LQ_FAULT_DEVICE_ALLOC = 1, LQ_FAULT_STEP_LAUNCH = 2 };
 lq_status lq_inject_fault(int kind, int64_t after);
+/* The bounds-checked build of the library (compiled with LQ_BOUNDS_CHECK)
+   checks every shared-memory slot, tile and ring index and every global
+   element index of the step kernels; an index out of range is counted and
+   replaced by 0, so nothing is accessed out of range.  *hits: the count
+   since the library was loaded.  The release build has no checks and
+   returns LQ_EINVAL with *hits = 0. */
+lq_status lq_bounds_check_hits(uint32_t *hits);
 
 /* ---- tuning ---------------------------------------------------------------------- */
 

@@ -14,6 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblqmin.so")
+LIB_BOUNDS = os.path.join(HERE, "liblqmin_bounds.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -34,20 +35,27 @@ def needs_build(lib=LIB) -> bool:
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not needs_build():
-        return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
+def build(force: bool = False, verbose: bool = False, bounds_check: bool = False) -> str:
+    """Build ``liblqmin.so``; with ``bounds_check`` the bounds-checked
+    variant ``liblqmin_bounds.so`` (every index of the step kernels checked
+    and counted, see lq_bounds_check_hits) for the tests."""
+    lib = LIB_BOUNDS if bounds_check else LIB
+    if not force and not needs_build(lib):
+        return lib
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
            "-Xcompiler", "-fPIC", "-shared", "-cudart", "shared",
            "-Xlinker", "-rpath,/usr/local/cuda/lib64",
            "-I", os.path.join(ROOT, "include"), "-o", tmp, *sources()]
+    if bounds_check:
+        cmd.insert(1, "-DLQ_BOUNDS_CHECK")
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv,
+                bounds_check="--bounds-check" in sys.argv))

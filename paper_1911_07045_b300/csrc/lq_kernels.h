@@ -42,6 +42,9 @@ bool step_index32(long long N);
 // host-side fault injection (lq_inject_fault): true once when an injected
 // failure of this kind (1 device allocation, 2 step-kernel launch) is due
 bool fault_due(int kind);
+// bounds-checked build: index checks of the step kernels that failed since
+// load (returns 1; 0 and *out = 0 in the release build; -1 on a CUDA error)
+int bounds_hits(unsigned int *out);
 // cudaMalloc, or cudaErrorMemoryAllocation without allocating when an
 // injected allocation failure is due
 template <typename P>

@@ -181,6 +181,14 @@ bool parse_boundary(const char *text, Parsed *P) {
 
 extern "C" {
 
+lq_status lq_bounds_check_hits(uint32_t *hits) {
+    if (!hits) return LQ_EINVAL;
+    unsigned int h = 0;
+    int r = bounds_hits(&h);
+    *hits = h;
+    return r == 1 ? LQ_OK : (r == 0 ? LQ_EINVAL : LQ_ECUDA);
+}
+
 lq_status lq_inject_fault(int kind, int64_t after) {
     if (kind < LQ_FAULT_NONE || kind > LQ_FAULT_STEP_LAUNCH || after < 0) return LQ_EINVAL;
     g_fault_kind.store(LQ_FAULT_NONE, std::memory_order_release);

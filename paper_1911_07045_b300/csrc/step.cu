@@ -46,6 +46,36 @@
 
 namespace lq {
 
+// Index checks of the bounds-checked build (-DLQ_BOUNDS_CHECK): an index
+// outside [0, n) is counted and replaced by 0, so that nothing is ever read
+// or written out of range; the release build compiles them away.
+#ifdef LQ_BOUNDS_CHECK
+__device__ unsigned int bounds_hits_dev;
+__device__ __forceinline__ int bchk(int i, int n) {
+    if (i < 0 || i >= n) { atomicAdd(&bounds_hits_dev, 1u); return 0; }
+    return i;
+}
+template <typename I>
+__device__ __forceinline__ I bchk_idx(I i, I n) {
+    if (i >= n) { atomicAdd(&bounds_hits_dev, 1u); return I(0); }
+    return i;
+}
+#define LQ_CHK(i, n) bchk((i), (n))
+#define LQ_CHK_IDX(i, n) bchk_idx((i), (n))
+#else
+#define LQ_CHK(i, n) (i)
+#define LQ_CHK_IDX(i, n) (i)
+#endif
+
+int bounds_hits(unsigned int *out) {
+#ifdef LQ_BOUNDS_CHECK
+    return cudaMemcpyFromSymbol(out, bounds_hits_dev, sizeof(unsigned int)) == cudaSuccess ? 1 : -1;
+#else
+    *out = 0;
+    return 0;
+#endif
+}
+
 template <typename T>
 struct Prec;
 
@@ -416,9 +446,9 @@ struct Smem {
     T *D;              // [2][2][5][PL] FP64 three-constant form: the central
                        // differences D_y, D_z of a plane (regular path)
     uint8_t *M;        // [slots][PL]
-    __device__ __forceinline__ int idx(int lx, int ly) const { return ly * SX + lx; }
+    __device__ __forceinline__ int idx(int lx, int ly) const { return LQ_CHK(ly, SY) * SX + LQ_CHK(lx, SX); }
     __device__ __forceinline__ QS &q(int slot, int c, int lx, int ly) {
-        unsigned char *b = Q + slot * SLOT_BYTES;
+        unsigned char *b = Q + LQ_CHK(slot, 5) * SLOT_BYTES;
         int i = idx(lx, ly);
         if (sizeof(QS) == 4) {
             if (c < 4) return reinterpret_cast<QS *>(b)[4 * i + c];
@@ -429,7 +459,7 @@ struct Smem {
         return reinterpret_cast<QS *>(b + 32 * PL)[i];
     }
     __device__ __forceinline__ void load5(int slot, int lx, int ly, QS *o) const {
-        const unsigned char *b = Q + slot * SLOT_BYTES;
+        const unsigned char *b = Q + LQ_CHK(slot, 5) * SLOT_BYTES;
         int i = idx(lx, ly);
         if constexpr (sizeof(QS) == 4) {
             int4 a = reinterpret_cast<const int4 *>(b)[i];
@@ -443,7 +473,7 @@ struct Smem {
         }
     }
     __device__ __forceinline__ void store5(int slot, int lx, int ly, const QS *v) {
-        unsigned char *b = Q + slot * SLOT_BYTES;
+        unsigned char *b = Q + LQ_CHK(slot, 5) * SLOT_BYTES;
         int i = idx(lx, ly);
         if constexpr (sizeof(QS) == 4) {
             reinterpret_cast<int4 *>(b)[i] = make_int4(v[0], v[1], v[2], v[3]);
@@ -454,13 +484,15 @@ struct Smem {
             reinterpret_cast<QS *>(b + 32 * PL)[i] = v[4];
         }
     }
-    __device__ __forceinline__ uint8_t &m(int slot, int lx, int ly) { return M[slot * PL + idx(lx, ly)]; }
+    __device__ __forceinline__ uint8_t &m(int slot, int lx, int ly) {
+        return M[LQ_CHK(slot, 5) * PL + idx(lx, ly)];
+    }
 
     __device__ __forceinline__ T &x(int slot, int ax, int c, int lx, int ly) {
-        return X[((slot * 2 + ax) * 5 + c) * PL + idx(lx, ly)];
+        return X[((LQ_CHK(slot, 2) * 2 + LQ_CHK(ax, 2)) * 5 + LQ_CHK(c, 5)) * PL + idx(lx, ly)];
     }
     __device__ __forceinline__ T &d(int slot, int ax, int c, int lx, int ly) {
-        return D[((slot * 2 + ax) * 5 + c) * PL + idx(lx, ly)];
+        return D[((LQ_CHK(slot, 2) * 2 + LQ_CHK(ax, 2)) * 5 + LQ_CHK(c, 5)) * PL + idx(lx, ly)];
     }
 };
 
@@ -955,7 +987,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
         int Z = wrap_coord(z, L.nz, L.pz);
         r.m = 0;
         if (in && Z >= 0) {
-            I i = (I)Z * NXY + xy;
+            I i = LQ_CHK_IDX((I)Z * NXY + xy, N);
             r.m = __ldg(args.g.mask + i);
 #pragma unroll
             for (int c = 0; c < 5; ++c) r.q[c] = __ldg(qin + c * N + i);
@@ -1062,7 +1094,8 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                         S.m(sc, lx, ly + 1) & S.m(sp, lx, ly) & S.m(sm, lx, ly) & m0;
             reg = (m0 & FULL) == FULL && (a & 0xFC) == 0xFC && !ext;
         }
-        const I i = (I)z * NXY + (I)gy * (I)L.nx + (I)gx;
+        const I i = own ? LQ_CHK_IDX((I)z * NXY + (I)gy * (I)L.nx + (I)gx, N)
+                        : (I)z * NXY + (I)gy * (I)L.nx + (I)gx;
         T vold[5], fold[5];
         if (own && !fo_mode) {
 #pragma unroll

@@ -41,7 +41,7 @@ EXPORTS = [
     "lq_server_poll", "lq_server_wait", "lq_server_stats_get", "lq_boundary_check",
     "lq_add_boundary_text", "lq_load_boundary_file", "lq_object_count", "lq_move_object",
     "lq_clear_objects", "lq_set_material", "lq_clone", "lq_pmf_sweep", "lq_init_dipolar",
-    "lq_frank_to_landau", "lq_set_index_width", "lq_inject_fault",
+    "lq_frank_to_landau", "lq_set_index_width", "lq_inject_fault", "lq_bounds_check_hits",
 ]
 
 
@@ -179,6 +179,7 @@ def load(path: str = LIB_PATH):
         "lq_frank_to_landau": (C.c_int, [d, d, d, d, d, d, C.POINTER(C.c_double)]),
         "lq_set_index_width": (C.c_int, [S, C.c_int]),
         "lq_inject_fault": (C.c_int, [C.c_int, i64]),
+        "lq_bounds_check_hits": (C.c_int, [C.POINTER(C.c_uint32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
