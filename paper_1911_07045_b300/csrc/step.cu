@@ -1462,16 +1462,18 @@ dim3 step_grid(const LatticeDev &L, int zchunk, int tx, int ty) {
 }
 
 // tile of one block: the FP32 form runs 32x4 tiles at 4 blocks per SM (128
-// registers per thread), the FP64 form 32x8 tiles at one block per SM.  A
-// one-constant FP32 lattice at least 256 sites wide runs 64x4 tiles at 2
-// blocks per SM instead (half the ring columns per site: 8% faster at 512^3;
-// 6% slower with three constants, and slower on narrow lattices, where a
-// 64-wide tile is partly empty).  Batches always run 32-wide tiles.
+// registers per thread), the FP64 form 32x8 tiles at one block per SM with
+// three constants and 32x4 tiles at 2 blocks per SM with one constant (4%
+// faster there, 6% slower with three constants).  A one-constant FP32
+// lattice at least 256 sites wide runs 64x4 tiles at 2 blocks per SM
+// instead (half the ring columns per site: 8% faster at 512^3; 6% slower
+// with three constants, and slower on narrow lattices, where a 64-wide tile
+// is partly empty).  Batches always run 32-wide tiles.
 bool wide_tiles(int fp32, int three, int nx) { return fp32 && !three && nx >= 256; }
 
 void step_tile(int fp32, int three, int nx, int *tx, int *ty) {
     *tx = wide_tiles(fp32, three, nx) ? 64 : 32;
-    *ty = fp32 ? 4 : 8;
+    *ty = fp32 || !three ? 4 : 8;
 }
 
 // calls F::template run<T, FORM, TY, I>() for the precision, distortion form
@@ -1492,6 +1494,7 @@ static auto dispatch(int fp32, int form, int ty, bool idx32, F &&f) {
 template <typename F>
 static auto dispatch_single(int fp32, int form, bool idx32, F &&f) {
     if (fp32) return dispatch_form<float, 4>(form, idx32, f);
+    if (form == 0) return dispatch_form<double, 4>(form, idx32, f);
     return dispatch_form<double, 8>(form, idx32, f);
 }
 
