@@ -436,7 +436,7 @@ def run_minimizers(L: int, seconds: float):
     return out
 
 
-def cpu_baseline(L_sample=128, steps=6):
+def cpu_baseline(L_sample=128, steps=16):
     """The oracle as it stands, on the host cores: FIRE iterations on a
     L_sample^3 lattice with the same structure (colloids scaled by L/512,
     planar walls, three constants)."""

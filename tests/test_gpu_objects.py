@@ -298,3 +298,43 @@ def test_dipolar_start_matches_the_oracle(oracle_mod, prec):
         s.init_dipolar(c, (0, 0, 0), rd=5.0)
     with pytest.raises(lqmin.LqError):
         s.init_dipolar(c, (0, 0, 1), rd=-1.0)
+
+
+def test_solvers_driven_from_several_threads_match_sequential_runs():
+    """Distinct solvers may be used from different threads: two lattices
+    minimised concurrently (the binding releases the interpreter lock in
+    every call) end where they end when run one after the other."""
+    import threading
+    shapes = [(30, 26, 22), (28, 28, 20)]
+    objs = [[dict(type="sphere", c=(15.0, 13.0, 11.0), R=4.0, anchor=HOM())], []]
+    p = lqmin.fire_params(**dict(FP, max_iter=3000, force_tol=1e-8))
+
+    def make(k):
+        s = lqmin.Solver(shapes[k], A, B, C, 2.32, 0.5, 0.3)
+        s.add_objects(objs[k])
+        s.init_random_uniaxial(50 + k)
+        return s
+
+    seq = []
+    for k in range(2):
+        s = make(k)
+        s.minimize(p)
+        seq.append(s.get_q())
+        s.close()
+    par = [make(0), make(1)]
+    errors = []
+
+    def run(s):
+        try:
+            s.minimize(p)
+        except Exception as e:   # reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=run, args=(s,)) for s in par]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors
+    for s, q in zip(par, seq):
+        assert np.array_equal(s.get_q(), q)
