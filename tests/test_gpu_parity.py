@@ -231,3 +231,32 @@ def test_wide_tiles_of_wide_one_constant_fp32_lattices(oracle_mod):
     qo, vo, Fo, st = o.fire(q, fp, 40)
     assert r.iterations == st["iter"] == 40
     assert np.abs(s.get_q()[:, sim] - qo[:, sim]).max() < 1e-5
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_set_q_from_device_memory(prec, dtype):
+    """lq_set_q_device takes Q from a device array of doubles or floats (a
+    torch tensor here) and equals the same values given through host memory;
+    the FP32 form refuses values outside its fixed-point range."""
+    import torch
+    shape = (20, 18, 16)
+    objs = [dict(type="sphere", c=(10.0, 9.0, 8.0), R=3.5, anchor=HOM())]
+    a = lqmin.Solver(shape, synth.A_5CB, synth.B_5CB, synth.C_5CB, 2.32, 0.5, 0.3, precision=prec)
+    b = lqmin.Solver(shape, synth.A_5CB, synth.B_5CB, synth.C_5CB, 2.32, 0.5, 0.3, precision=prec)
+    for s in (a, b):
+        s.add_objects(objs)
+    q = synth.random_uniaxial_q(shape, 9)
+    t = torch.tensor(q, dtype=torch.float64 if dtype == 0 else torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    a.set_q_device(t.data_ptr(), dtype)
+    b.set_q(t.cpu().double().numpy())
+    assert np.array_equal(a.get_q(), b.get_q())
+    assert np.array_equal(a.force(), b.force())
+    if prec == 1:
+        bad = torch.full_like(t, 3.0)
+        torch.cuda.synchronize()
+        with pytest.raises(lqmin.LqError):
+            a.set_q_device(bad.data_ptr(), dtype)
+    with pytest.raises(lqmin.LqError):
+        a.set_q_device(t.data_ptr(), 2)
