@@ -4,7 +4,7 @@ energy, a FIRE step, the FP32 form, batches and the allocation-free energy."""
 import numpy as np
 import pytest
 
-from _helpers import CASES, HOM, PLANAR, force_rel_err, make_pair, need_gpu
+from _helpers import CASES, force_rel_err, make_pair, need_gpu
 from paper_1911_07045_b300 import lqmin, synth
 
 pytestmark = pytest.mark.gpu

@@ -5,7 +5,7 @@ from device flags, with nothing that faults the GPU."""
 import numpy as np
 import pytest
 
-from _helpers import HOM, PLANAR, make_pair, need_gpu, rand_q
+from _helpers import HOM, PLANAR, make_pair, need_gpu
 from paper_1911_07045_b300 import lqmin, synth
 
 pytestmark = pytest.mark.gpu

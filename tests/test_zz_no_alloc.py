@@ -10,7 +10,6 @@ parts for the same field.  This file is collected last so that a failure
 here leaves every other test already run."""
 import ctypes as C
 
-import numpy as np
 import pytest
 
 from _helpers import HOM, PLANAR, need_gpu, rand_q
