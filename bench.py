@@ -47,13 +47,13 @@ DRAM_BYTES_PER_SITE = {"fp32": 2.035445e9 / 256 ** 3, "fp64": 4.203127e9 / 256 *
 # site, counted from the kernel's arithmetic: stencil 94 (second
 # differences 15 x 2, the site's central differences D_y, D_z 10, mixed
 # differences from them 13, shared partial sums 12, one- and three-constant
-# combinations 29), bulk force 33, force sum 5, drift 10, mixing and kick
-# 15, reductions 18 (ring sites' drift and central differences are not
-# counted)
-FP64_OPS_PER_SITE = 175
+# combinations 29, which start from the bulk force: no separate sum), bulk
+# force 33, drift 10, mixing and kick 15, reductions 18 (ring sites' drift
+# and central differences are not counted)
+FP64_OPS_PER_SITE = 170
 # the same for a one-constant site: the stencil is 15 second differences (add
 # + FMA), 10 adds for the three-axis sums and 8 scalings (48 instead of 94)
-FP64_OPS_PER_SITE_1C = 129
+FP64_OPS_PER_SITE_1C = 124
 FP64_OPS_PER_CLK_SM = 2
 N_SM = 148
 

@@ -803,9 +803,12 @@ struct Stencil<float> {
 //   F2 = 2 L1 s2 + L23 (x2 + z2) + L23/4 (a4 - b3 + c1)
 //   F3 = L1 (s0 + 2 s3) + L23 (y3 + z0 + z3) + L23/4 (a1 - b2)
 //   F4 = 2 L1 s4 + L23 (y4 + z4) + L23/4 (a2 + b1 - c0)
+// FP64: Fb (the site's bulk and field force) starts each component's chain
+// of fused multiply-adds, so the sum costs no separate additions
 template <bool THREE, typename T, int TX, int TY>
 __device__ __forceinline__ void regular_force(Smem<T, TX, TY> &S, int lx, int ly, int sc, int sp,
-                                              int sm, int dslot, T L1s, T L23s, T L2q, T L3q, T *Fd) {
+                                              int sm, int dslot, T L1s, T L23s, T L2q, T L3q,
+                                              const T *Fb, T *Fd) {
     using ST = Stencil<T>;
     using QS = typename Prec<T>::Q;
     T dx[5], dy[5], dz[5];
@@ -826,6 +829,16 @@ __device__ __forceinline__ void regular_force(Smem<T, TX, TY> &S, int lx, int ly
         for (int c = 0; c < 5; ++c) dz[c] = ST::sec(a[c], b[c], c0[c]);
     }
     const T L1s2 = T(2) * L1s;
+    if constexpr (!THREE && sizeof(T) == 8) {
+        T s0 = dx[0] + dy[0] + dz[0], s1 = dx[1] + dy[1] + dz[1], s2 = dx[2] + dy[2] + dz[2];
+        T s3 = dx[3] + dy[3] + dz[3], s4 = dx[4] + dy[4] + dz[4];
+        Fd[0] = L1s * (T(2) * s0 + s3) + Fb[0];
+        Fd[1] = L1s2 * s1 + Fb[1];
+        Fd[2] = L1s2 * s2 + Fb[2];
+        Fd[3] = L1s * (s0 + T(2) * s3) + Fb[3];
+        Fd[4] = L1s2 * s4 + Fb[4];
+        return;
+    }
     if (!THREE || sizeof(T) == 4) {
         T s0 = dx[0] + dy[0] + dz[0], s1 = dx[1] + dy[1] + dz[1], s2 = dx[2] + dy[2] + dz[2];
         T s3 = dx[3] + dy[3] + dz[3], s4 = dx[4] + dy[4] + dz[4];
@@ -877,11 +890,11 @@ __device__ __forceinline__ void regular_force(Smem<T, TX, TY> &S, int lx, int ly
     }
     const T kq = T(0.25) * L23s;
     if constexpr (sizeof(T) == 8) {
-        Fd[0] = L1s * (T(2) * s0 + s3) + (L23s * t0 + kq * (a[1] - c[4]));
-        Fd[1] = L1s2 * s1 + (L23s * t1 + kq * ((a[0] + a[3]) + (b[4] + c[2])));
-        Fd[2] = L1s2 * s2 + (L23s * t2 + kq * (a[4] - b[3] + c[1]));
-        Fd[3] = L1s * (s0 + T(2) * s3) + (L23s * t3 + kq * (a[1] - b[2]));
-        Fd[4] = L1s2 * s4 + (L23s * t4 + kq * (a[2] + b[1] - c[0]));
+        Fd[0] = L1s * (T(2) * s0 + s3) + (L23s * t0 + (kq * (a[1] - c[4]) + Fb[0]));
+        Fd[1] = L1s2 * s1 + (L23s * t1 + (kq * ((a[0] + a[3]) + (b[4] + c[2])) + Fb[1]));
+        Fd[2] = L1s2 * s2 + (L23s * t2 + (kq * (a[4] - b[3] + c[1]) + Fb[2]));
+        Fd[3] = L1s * (s0 + T(2) * s3) + (L23s * t3 + (kq * (a[1] - b[2]) + Fb[3]));
+        Fd[4] = L1s2 * s4 + (L23s * t4 + (kq * (a[2] + b[1] - c[0]) + Fb[4]));
     } else {
         Fd[0] += L23s * (dx[0] + dz[0] + dz[3]) + kq * (a[1] - c[4]);
         Fd[1] += L23s * (dx[1] + dy[1]) + kq * ((a[0] + a[3]) + (b[4] + c[2]));
@@ -1110,8 +1123,24 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
         }
 
         T Fd[5];
+        // FP64 regular planes: Fd already holds the bulk and field force
+        const bool fused_bulk = sizeof(T) == 8 && all_reg;
         if (all_reg) {
-            if (own) regular_force<THREE>(S, lx, ly, sc, sp, sm, z & 1, L1s, L23s, L2q, L3q, Fd);
+            if (own) {
+                T fb0[5];
+                if constexpr (sizeof(T) == 8) {
+                    QS qc[5];
+                    T qcv[5];
+                    S.load5(sc, lx, ly, qc);
+                    q_values(qc, qcv);
+                    bulk_force(qcv, args.A, args.B, args.C, fb0);
+                    if (args.fields) {
+#pragma unroll
+                        for (int c = 0; c < 5; ++c) fb0[c] += args.fext[c];
+                    }
+                }
+                regular_force<THREE>(S, lx, ly, sc, sp, sm, z & 1, L1s, L23s, L2q, L3q, fb0, Fd);
+            }
         } else {
             // general path (planes touching objects or open edges): the z
             // link below and the in-plane means are rebuilt on every such plane
@@ -1303,12 +1332,17 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
             T qv[5], fb[5], Fn[5];
             S.load5(sc, lx, ly, q0);
             q_values(q0, qv);
-            bulk_force(qv, args.A, args.B, args.C, fb);
-            if (args.fields) {
+            if (fused_bulk) {
 #pragma unroll
-                for (int c = 0; c < 5; ++c) fb[c] += args.fext[c];
+                for (int c = 0; c < 5; ++c) Fn[c] = Fd[c];
+            } else {
+                bulk_force(qv, args.A, args.B, args.C, fb);
+                if (args.fields) {
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) fb[c] += args.fext[c];
+                }
+                add5(Fd, fb, Fn);
             }
-            add5(Fd, fb, Fn);
             if (m0 & M_ANCH) {
                 const AnchorRec<T> *r = find_record<T>(args.g, L, gx, gy, z);
                 if (r) {
