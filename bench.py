@@ -41,7 +41,7 @@ DESIGN_BYTES = {"fp32": 6 * 5 * 4 + 1, "fp64": 6 * 5 * 8 + 1}
 # dram__bytes_write.sum from one ncu capture of the same kernel on the 256^3
 # case of this workload, divided by its 16,777,216 sites (the traffic of a
 # launch grows with the sites it updates); the bench scales it to its lattice
-DRAM_BYTES_PER_SITE = {"fp32": 2.035445e9 / 256 ** 3, "fp64": 4.203127e9 / 256 ** 3}
+DRAM_BYTES_PER_SITE = {"fp32": 2.035445e9 / 256 ** 3, "fp64": 4.210749e9 / 256 ** 3}
 # FP64 form: bound by the FP64 pipe (2 FP64 operations per clock per SM).
 # FP64 arithmetic operations per site-update of the regular three-constant
 # site, counted from the kernel's arithmetic: stencil 94 (second
