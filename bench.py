@@ -403,6 +403,42 @@ def run_step_scaling(sizes, tol: float, seeds=(1, 2, 3)):
     return out
 
 
+def run_precision_check(max_iter: int = 400000):
+    """The FP32-bulk / FP64-reduction form against the plain FP64 path on the
+    same GPU, at the accuracy the precision form must keep (final energy
+    within 1e-6 relative, per-site order parameter within 1e-4): the 128^3
+    colloid slab (homeotropic walls, centred colloid R = 20, three
+    constants) from a smooth start -- a uniform director tilted slightly
+    from z, so that both forms settle in the same basin (from a random start
+    they may reach different defect arrangements) -- minimised by FIRE to a
+    largest site force of 1e-7 (FP64) and 1e-6 (FP32 form)."""
+    from paper_1911_07045_b300 import lqmin
+    cfg = synth.config_colloid_slab()
+    n = np.array([0.1, 0.05, 1.0])
+    n /= np.linalg.norm(n)
+    N = int(np.prod(cfg["shape"]))
+    q0 = np.repeat(synth.uniaxial_q(n[:, None], synth.s0_closed_form(synth.A_5CB, synth.B_5CB,
+                                                                      synth.C_5CB)), N, axis=1)
+    out = {"workload": "128^3 slab, homeotropic walls z=0,127 and colloid R=20 (W=5.3), "
+                       "L1/L2/L3=2.32/0.5/0.3, smooth start (director (0.1, 0.05, 1))"}
+    res = {}
+    for form, prec, tol in (("fp64", lqmin.LQ_FP64, 1e-7), ("fp32", lqmin.LQ_FP32_BULK_FP64_RED, 1e-6)):
+        s = lqmin.solver_for(cfg, precision=prec)
+        s.set_q(q0)
+        st, r = s.minimize(lqmin.fire_params(**dict(synth.FIRE_DEFAULTS, max_iter=max_iter,
+                                                    force_tol=tol)))
+        sim = (s.mask() & 1).astype(bool)
+        res[form] = dict(energy=r.energy, S=s.order_field()[sim], iterations=int(r.iterations),
+                         status=int(r.fire_status), seconds=round(r.seconds, 3), tol=tol)
+        s.close()
+    e64, e32 = res["fp64"]["energy"], res["fp32"]["energy"]
+    out.update({f: {k: v for k, v in r.items() if k != "S"} for f, r in res.items()})
+    out["energy_rel_diff"] = abs(e32 - e64) / abs(e64)
+    out["max_S_diff"] = float(np.abs(res["fp32"]["S"] - res["fp64"]["S"]).max())
+    out["within_tolerance"] = bool(out["energy_rel_diff"] <= 1e-6 and out["max_S_diff"] <= 1e-4)
+    return out
+
+
 def run_minimizers(L: int, seconds: float):
     """FIRE against gradient descent and Nesterov's accelerated gradient on a
     periodic one-constant bulk from a random start (the comparison of Fig. 2,
@@ -518,6 +554,8 @@ def main_ours(args, dist: Dist):
         line["batched"] = run_batch(args.batch_steps)
     if dist.world == 1 and args.serving_requests > 0:
         line["served"] = run_serving(args.serving_requests, args.serving_rate)
+    if dist.world == 1 and not args.no_precision_check:
+        line["precision_check"] = run_precision_check()
     if dist.world == 1 and args.minimizers > 0:
         line["minimizers"] = run_minimizers(args.minimizer_size, args.minimizers)
     if dist.world == 1 and args.objects > 0:
@@ -579,6 +617,8 @@ def main(argv=None):
     ap.add_argument("--minimizers", type=float, default=0.0,
                     help="seconds per method of the FIRE / GD / Nesterov comparison (0: skip)")
     ap.add_argument("--minimizer-size", type=int, default=250)
+    ap.add_argument("--no-precision-check", action="store_true",
+                    help="skip the FP32-form-against-FP64 minimisation of the 128^3 slab")
     ap.add_argument("--objects", type=float, default=0.0,
                     help="seconds per method of the Fig. 3 object-geometry comparison (0: skip)")
     ap.add_argument("--step-scaling", default="",

@@ -72,7 +72,10 @@ def uniaxial_q(n: np.ndarray, S) -> np.ndarray:
 
 
 def s0_closed_form(A: float, B: float, C: float) -> float:
-    """S0 of Eq. (S0def): the initial-condition recipe starts at this S."""
+    """The amplitude of the generated start states: the workloads start
+    uniaxial at the closed-form S0 of Eq. (S0def) for their A, B, C.  Only
+    the inputs use it; the CUDA path and the oracle each compute S0 for their
+    own arithmetic (anchoring targets, random starts) independently."""
     return (-B + math.sqrt(B * B - 24.0 * A * C)) / (6.0 * C)
 
 
