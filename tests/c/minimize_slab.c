@@ -47,7 +47,7 @@ int main(void) {
     double smin = 1.0;
     for (size_t i = 0; i < n; ++i)
         if (S[i] > 0.0 && S[i] < smin) smin = S[i];
-    printf("status %d iterations %lld max_force %.3e energy %.10e parts %.6e %.6e %.6e "
+    printf("status %d iterations %lld max_force %.3e energy %.17g parts %.6e %.6e %.6e "
            "simulated %lld anchored %lld minS %.4f\n",
            r.fire_status, (long long)r.iterations, r.max_force, total, parts[0], parts[1],
            parts[2], (long long)nsim, (long long)nrec, smin);
