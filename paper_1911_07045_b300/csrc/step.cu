@@ -503,7 +503,7 @@ struct Smem {
 // D_z(j - x) and E_yz(j) = D_z(j + y) - D_z(j - y) -- the same operations in
 // the same order as (a - b) - (c - d) on the four diagonal neighbours
 template <typename T, int FORM>
-constexpr bool shared_diffs() { return sizeof(T) == 8 && FORM == 1; }
+constexpr bool shared_diffs() { return sizeof(T) == 8 && FORM >= 1; }
 
 // mean of the allowed one-sided differences along axis K at (lx, ly) of
 // plane slot sc; splus / sminus are the slots of the planes above / below
@@ -778,6 +778,7 @@ struct Stencil<double> {
     __device__ static __forceinline__ double mix(double a, double b, double c, double d) {
         return (a - b) - (c - d);
     }
+    __device__ static __forceinline__ double dif(double a, double b) { return a - b; }
 };
 template <>
 struct Stencil<float> {
@@ -786,6 +787,7 @@ struct Stencil<float> {
     __device__ static __forceinline__ float mix(int a, int b, int c, int d) {
         return __int2float_rn((a - b) - (c - d));
     }
+    __device__ static __forceinline__ float dif(int a, int b) { return __int2float_rn(a - b); }
 };
 
 // Distortion force at a regular site: every site within the 19-point
@@ -805,13 +807,22 @@ struct Stencil<float> {
 //   F4 = 2 L1 s4 + L23 (y4 + z4) + L23/4 (a2 + b1 - c0)
 // FP64: Fb (the site's bulk and field force) starts each component's chain
 // of fused multiply-adds, so the sum costs no separate additions
-template <bool THREE, typename T, int TX, int TY>
+//
+// With the chiral term and L6 = 0 (EXT) the averaged one-sided differences
+// of L4/2 eps_lik Q_lj dQ_ij/dx_k at regular sites are the central
+// differences C_k = q(j + e_k) - q(j - e_k), and the gradient of the energy
+// is (L4/2) eps_aik C_k Q_ib; in the five components
+//   F0 = -L4/2 (Cz1 - 2 Cy2 + Cx4)          F1 = -L4/2 (Cz3 - Cy4 + Cx2 - Cz0)
+//   F2 = -L4/2 (Cz4 + 2 Cy0 + Cy3 - Cx1)    F3 = -L4/2 (2 Cx4 - Cz1 - Cy2)
+//   F4 = -L4/2 (Cy1 - Cx0 - 2 Cx3 - Cz2)    (k4 = -L4/2 in storage units)
+template <bool THREE, bool EXT = false, typename T, int TX, int TY>
 __device__ __forceinline__ void regular_force(Smem<T, TX, TY> &S, int lx, int ly, int sc, int sp,
                                               int sm, int dslot, T L1s, T L23s, T L2q, T L3q,
-                                              const T *Fb, T *Fd) {
+                                              const T *Fb, T *Fd, T k4 = T(0)) {
     using ST = Stencil<T>;
     using QS = typename Prec<T>::Q;
     T dx[5], dy[5], dz[5];
+    T cx[5], cy[5], cz[5];
     {
         QS c0[5], a[5], b[5];
         S.load5(sc, lx, ly, c0);
@@ -819,14 +830,26 @@ __device__ __forceinline__ void regular_force(Smem<T, TX, TY> &S, int lx, int ly
         S.load5(sc, lx - 1, ly, b);
 #pragma unroll
         for (int c = 0; c < 5; ++c) dx[c] = ST::sec(a[c], b[c], c0[c]);
+        if (EXT) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) cx[c] = ST::dif(a[c], b[c]);
+        }
         S.load5(sc, lx, ly + 1, a);
         S.load5(sc, lx, ly - 1, b);
 #pragma unroll
         for (int c = 0; c < 5; ++c) dy[c] = ST::sec(a[c], b[c], c0[c]);
+        if (EXT) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) cy[c] = ST::dif(a[c], b[c]);
+        }
         S.load5(sp, lx, ly, a);
         S.load5(sm, lx, ly, b);
 #pragma unroll
         for (int c = 0; c < 5; ++c) dz[c] = ST::sec(a[c], b[c], c0[c]);
+        if (EXT) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) cz[c] = ST::dif(a[c], b[c]);
+        }
     }
     const T L1s2 = T(2) * L1s;
     if constexpr (!THREE && sizeof(T) == 8) {
@@ -901,6 +924,13 @@ __device__ __forceinline__ void regular_force(Smem<T, TX, TY> &S, int lx, int ly
         Fd[2] += L23s * (dx[2] + dz[2]) + kq * (a[4] - b[3] + c[1]);
         Fd[3] += L23s * (dy[3] + dz[0] + dz[3]) + kq * (a[1] - b[2]);
         Fd[4] += L23s * (dy[4] + dz[4]) + kq * (a[2] + b[1] - c[0]);
+    }
+    if (EXT) {
+        Fd[0] += k4 * (cz[1] - T(2) * cy[2] + cx[4]);
+        Fd[1] += k4 * ((cz[3] - cz[0]) + (cx[2] - cy[4]));
+        Fd[2] += k4 * (cz[4] + T(2) * cy[0] + cy[3] - cx[1]);
+        Fd[3] += k4 * (T(2) * cx[4] - cz[1] - cy[2]);
+        Fd[4] += k4 * (cy[1] - cx[0] - T(2) * cx[3] - cz[2]);
     }
     (void)L2q; (void)L3q;
 }
@@ -1075,8 +1105,10 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
     if constexpr (shared_diffs<T, FORM>()) plane_diffs(z0, slot_of(z0), slot_of(z0 - 1), slot_of(z0 + 1));
 
     const T L1 = args.L1, L23 = args.L2 + args.L3;
-    // chiral / cubic terms: taken by the general path on every plane
+    // chiral / cubic terms: the cubic term takes the general path on every
+    // plane; the chiral term alone (L6 = 0) has a regular-site path
     constexpr bool ext = FORM == 2;
+    const bool chiral_only = ext && args.L6 == T(0);
     const T L4 = args.L4, L6 = ext ? args.L6 : T(0);
     const T sc_ = T(Stencil<T>::scale);
     const T L1s = L1 * sc_, L23s = L23 * sc_;
@@ -1105,7 +1137,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
         if (own) {
             uint8_t a = S.m(sc, lx - 1, ly) & S.m(sc, lx + 1, ly) & S.m(sc, lx, ly - 1) &
                         S.m(sc, lx, ly + 1) & S.m(sp, lx, ly) & S.m(sm, lx, ly) & m0;
-            reg = (m0 & FULL) == FULL && (a & 0xFC) == 0xFC && !ext;
+            reg = (m0 & FULL) == FULL && (a & 0xFC) == 0xFC && (!ext || chiral_only);
         }
         const I i = own ? LQ_CHK_IDX((I)z * NXY + (I)gy * (I)L.nx + (I)gx, N)
                         : (I)z * NXY + (I)gy * (I)L.nx + (I)gx;
@@ -1139,7 +1171,8 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                         for (int c = 0; c < 5; ++c) fb0[c] += args.fext[c];
                     }
                 }
-                regular_force<THREE>(S, lx, ly, sc, sp, sm, z & 1, L1s, L23s, L2q, L3q, fb0, Fd);
+                regular_force<THREE, ext>(S, lx, ly, sc, sp, sm, z & 1, L1s, L23s, L2q, L3q, fb0, Fd,
+                                          T(-0.5) * args.L4 * sc_);
             }
         } else {
             // general path (planes touching objects or open edges): the z
