@@ -1102,7 +1102,10 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
             if (col || row) one(rx, ry, col);
         }
     };
-    if constexpr (shared_diffs<T, FORM>()) plane_diffs(z0, slot_of(z0), slot_of(z0 - 1), slot_of(z0 + 1));
+    // (the cubic term takes the general path everywhere: no differences to share)
+    if constexpr (shared_diffs<T, FORM>()) {
+        if (FORM == 1 || args.L6 == T(0)) plane_diffs(z0, slot_of(z0), slot_of(z0 - 1), slot_of(z0 + 1));
+    }
 
     const T L1 = args.L1, L23 = args.L2 + args.L3;
     // chiral / cubic terms: the cubic term takes the general path on every
@@ -1151,7 +1154,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
         // the next plane's central differences: planes z .. z+2 are published,
         // and the slot (z+1) & 1 was last read by the previous plane's force
         if constexpr (shared_diffs<T, FORM>()) {
-            if (z + 1 < z1) plane_diffs(z + 1, sp, sc, s2);
+            if (z + 1 < z1 && (FORM == 1 || chiral_only)) plane_diffs(z + 1, sp, sc, s2);
         }
 
         T Fd[5];
