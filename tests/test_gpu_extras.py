@@ -136,3 +136,44 @@ def test_noalloc_energy_with_chiral_cubic_fields(oracle_mod):
     _, po = o.energy(q)
     # bulk (with fields) and distortion (with L4, L6); anchoring is not part of it
     assert np.allclose(out.cpu().numpy()[:2], po[:2], rtol=1e-12, atol=1e-10)
+
+
+CHIRAL = dict(L4=0.7, H=(0.3, -0.2, 0.5), mu0_dchi=1.3)
+
+
+@pytest.mark.parametrize("name", THREE_CASES)
+@pytest.mark.parametrize("zchunk", [0, 3])
+def test_chiral_alone_regular_path_fp64(oracle_mod, name, zchunk):
+    """The chiral term without the cubic one (L6 = 0) runs the regular-site
+    path on regular planes (central differences) and the general path
+    elsewhere: force and energy against the oracle on every three-constant
+    geometry."""
+    c = CASES[name]
+    per = c.get("periodic", (1, 1, 1))
+    s, o = make_pair(oracle_mod, c["shape"], c["L"], c["objects"], per, zchunk=zchunk, **CHIRAL)
+    q = synth.random_uniaxial_q(c["shape"], 34)
+    s.set_q(q)
+    sim = o.simulated()
+    assert force_rel_err(s.force(), o.force(q), sim) < 1e-10
+    Eg, pg = s.energy()
+    Eo, po = o.energy(q)
+    assert abs(Eg - Eo) <= 1e-12 * abs(Eo)
+
+
+@pytest.mark.parametrize("name", ["bulk3c_ragged", "sphere_walls_fg_3c"])
+def test_chiral_alone_fp32_form_and_steps(oracle_mod, name):
+    c = CASES[name]
+    per = c.get("periodic", (1, 1, 1))
+    s, o = make_pair(oracle_mod, c["shape"], c["L"], c["objects"], per,
+                     precision=lqmin.LQ_FP32_BULK_FP64_RED, **CHIRAL)
+    q = np.round(synth.random_uniaxial_q(c["shape"], 35) * 2.0 ** 28) / 2.0 ** 28
+    s.set_q(q)
+    assert force_rel_err(s.force(), o.force(q), o.simulated()) < 5e-5
+    f64, _ = make_pair(oracle_mod, c["shape"], c["L"], c["objects"], per, **CHIRAL)
+    fp = dict(synth.FIRE_DEFAULTS, max_iter=10 ** 6, force_tol=1e-14)
+    f64.set_q(q)
+    r = f64.step(lqmin.fire_params(**fp), 60)
+    qo, vo, Fo, st = o.fire(q, fp, 60)
+    assert r.iterations == st["iter"] == 60
+    sim = o.simulated()
+    assert np.abs(f64.get_q()[:, sim] - qo[:, sim]).max() < 1e-9
