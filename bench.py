@@ -184,8 +184,8 @@ class ClockSampler:
 def run_form(precision: str, L: int, steps: int, warmup: int, dist: Dist, sampler_gpu: int):
     """One precision form on the L^3 workload; a "_1c" suffix runs the same
     geometry with one-constant elasticity (L2 = L3 = 0), a "_chiral" suffix
-    adds the chiral term L4 = 0.05 (the kernel form with the chiral and
-    cubic terms)."""
+    adds the chiral term L4 = 0.05 and "_cubic" also the cubic term L6 = 0.3
+    (the kernel form with the chiral and cubic terms)."""
     import torch
     from paper_1911_07045_b300 import lqmin
     cfg = synth.config_large(L)
@@ -193,9 +193,10 @@ def run_form(precision: str, L: int, steps: int, warmup: int, dist: Dist, sample
         cfg = dict(cfg, L2=0.0, L3=0.0)
     stream = torch.cuda.Stream()
     prec = lqmin.LQ_FP32_BULK_FP64_RED if precision.startswith("fp32") else lqmin.LQ_FP64
-    if precision.endswith("_chiral"):
+    if precision.endswith("_chiral") or precision.endswith("_cubic"):
         s = lqmin.Solver(cfg["shape"], synth.A_5CB, synth.B_5CB, synth.C_5CB, cfg["L1"], cfg["L2"],
-                         cfg["L3"], precision=prec, stream=stream.cuda_stream, L4=0.05)
+                         cfg["L3"], precision=prec, stream=stream.cuda_stream, L4=0.05,
+                         L6=0.3 if precision.endswith("_cubic") else 0.0)
         s.add_objects(cfg["objects"])
     else:
         s = lqmin.solver_for(cfg, precision=prec, stream=stream.cuda_stream)

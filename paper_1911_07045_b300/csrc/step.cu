@@ -790,6 +790,108 @@ struct Stencil<float> {
     __device__ static __forceinline__ float dif(int a, int b) { return __int2float_rn(a - b); }
 };
 
+// The cubic term L6/2 Q_lk dQ_ij/dx_l dQ_ij/dx_k at a regular site.  Averaged
+// over the allowed differences, a site's density is L6/2 [sum_k Q_kk
+// (|f_k|^2 + |b_k|^2)/2 + sum_{l != k} Q_lk C_l . C_k / 4] with f_k, b_k the
+// forward and backward differences and C_k = f_k + b_k (dots over the nine
+// entries).  Differentiating the sum over the site and its six neighbours
+// with respect to Q(j) gives L6/2 (G_A + G_B), with G_A the density's own
+// Q factor -- (|f_k|^2 + |b_k|^2)/2 at (k,k), C_l . C_k / 4 at (l,k) -- and
+// G_B = sum_k [-Q_kk(j) D2_k + Q_kk(j - e_k) b_k - Q_kk(j + e_k) f_k]
+//     + 1/2 sum_k sum_{l != k} [Q_lk(j - e_k) C_l(j - e_k) - Q_lk(j + e_k) C_l(j + e_k)]
+// (D2_k = f_k - b_k); the force is -J^T (L6/2)(G_A + G_B).  Differences are
+// in storage units, s is the value of one unit.
+template <typename T, int TX, int TY>
+__device__ __noinline__ void l6_regular(Smem<T, TX, TY> &S, int lx, int ly, int sc, int sp, int sm,
+                                        T L6h, T s, T *F) {
+    using ST = Stencil<T>;
+    using QS = typename Prec<T>::Q;
+    QS c0[5], a[5], b[5];
+    S.load5(sc, lx, ly, c0);
+    T qv[5];
+    q_values(c0, qv);
+    T GB[5] = {T(0), T(0), T(0), T(0), T(0)};
+    T nrm[3], C[3][5];
+    T qo[3][2][2];   // neighbours' off-diagonal components (see the pairs below)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (k == 0) { S.load5(sc, lx + 1, ly, a); S.load5(sc, lx - 1, ly, b); }
+        if (k == 1) { S.load5(sc, lx, ly + 1, a); S.load5(sc, lx, ly - 1, b); }
+        if (k == 2) { S.load5(sp, lx, ly, a); S.load5(sm, lx, ly, b); }
+        T f[5], bk[5], av[5], bv[5];
+        q_values(a, av);
+        q_values(b, bv);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            f[c] = ST::dif(a[c], c0[c]);
+            bk[c] = ST::dif(c0[c], b[c]);
+            C[k][c] = ST::dif(a[c], b[c]);
+        }
+        nrm[k] = dot5(f, f) + dot5(bk, bk);
+        const T qkk_c = k == 0 ? qv[0] : (k == 1 ? qv[3] : -qv[0] - qv[3]);
+        const T qkk_p = k == 0 ? av[0] : (k == 1 ? av[3] : -av[0] - av[3]);
+        const T qkk_m = k == 0 ? bv[0] : (k == 1 ? bv[3] : -bv[0] - bv[3]);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) GB[c] += qkk_m * bk[c] - qkk_p * f[c] - qkk_c * (f[c] - bk[c]);
+        // Q_lk of the neighbours along k for the two l != k:
+        // k = x: (Q_xy, Q_xz); k = y: (Q_xy, Q_yz); k = z: (Q_xz, Q_yz)
+        const int c1 = k == 2 ? 2 : 1, c2 = k == 0 ? 2 : 4;
+        qo[k][0][0] = av[c1]; qo[k][0][1] = av[c2];
+        qo[k][1][0] = bv[c1]; qo[k][1][1] = bv[c2];
+    }
+    // G_B's cross part from the central differences of the twelve edge
+    // neighbours, grouped by the plane they lie in
+    auto cross = [&](T qm, const T *cm, T qp, const T *cp) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) GB[c] += T(0.5) * (qm * cm[c] - qp * cp[c]);
+    };
+    {   // xy corners: C_y(j +- x) for (k = x, l = y), C_x(j +- y) for (k = y, l = x)
+        QS pp[5], pm[5], mp[5], mm[5];
+        S.load5(sc, lx + 1, ly + 1, pp); S.load5(sc, lx + 1, ly - 1, pm);
+        S.load5(sc, lx - 1, ly + 1, mp); S.load5(sc, lx - 1, ly - 1, mm);
+        T u[5], w[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) { u[c] = ST::dif(mp[c], mm[c]); w[c] = ST::dif(pp[c], pm[c]); }
+        cross(qo[0][1][0], u, qo[0][0][0], w);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) { u[c] = ST::dif(pm[c], mm[c]); w[c] = ST::dif(pp[c], mp[c]); }
+        cross(qo[1][1][0], u, qo[1][0][0], w);
+    }
+    {   // xz edges: C_z(j +- x) for (k = x, l = z), C_x(j +- z) for (k = z, l = x)
+        QS pp[5], pm[5], mp[5], mm[5];   // (x+, z+), (x+, z-), (x-, z+), (x-, z-)
+        S.load5(sp, lx + 1, ly, pp); S.load5(sm, lx + 1, ly, pm);
+        S.load5(sp, lx - 1, ly, mp); S.load5(sm, lx - 1, ly, mm);
+        T u[5], w[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) { u[c] = ST::dif(mp[c], mm[c]); w[c] = ST::dif(pp[c], pm[c]); }
+        cross(qo[0][1][1], u, qo[0][0][1], w);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) { u[c] = ST::dif(pm[c], mm[c]); w[c] = ST::dif(pp[c], mp[c]); }
+        cross(qo[2][1][0], u, qo[2][0][0], w);
+    }
+    {   // yz edges: C_z(j +- y) for (k = y, l = z), C_y(j +- z) for (k = z, l = y)
+        QS pp[5], pm[5], mp[5], mm[5];   // (y+, z+), (y+, z-), (y-, z+), (y-, z-)
+        S.load5(sp, lx, ly + 1, pp); S.load5(sm, lx, ly + 1, pm);
+        S.load5(sp, lx, ly - 1, mp); S.load5(sm, lx, ly - 1, mm);
+        T u[5], w[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) { u[c] = ST::dif(mp[c], mm[c]); w[c] = ST::dif(pp[c], pm[c]); }
+        cross(qo[1][1][1], u, qo[1][0][1], w);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) { u[c] = ST::dif(pm[c], mm[c]); w[c] = ST::dif(pp[c], mp[c]); }
+        cross(qo[2][1][1], u, qo[2][0][1], w);
+    }
+    T jb[5];
+    jt_sym(GB, jb);
+    const T s2 = s * s;
+    const T h = T(0.5) * s2;
+    F[0] = -L6h * (h * (nrm[0] - nrm[2]) + s * jb[0]);
+    F[1] = -L6h * (h * dot5(C[0], C[1]) + s * jb[1]);
+    F[2] = -L6h * (h * dot5(C[0], C[2]) + s * jb[2]);
+    F[3] = -L6h * (h * (nrm[1] - nrm[2]) + s * jb[3]);
+    F[4] = -L6h * (h * dot5(C[1], C[2]) + s * jb[4]);
+}
+
 // Distortion force at a regular site: every site within the 19-point
 // stencil and at distance 2 along the axes is simulated, so every allowed
 // difference count is 2 and every weight 1/2.  Then the per-site cross terms
@@ -818,7 +920,7 @@ struct Stencil<float> {
 template <bool THREE, bool EXT = false, typename T, int TX, int TY>
 __device__ __forceinline__ void regular_force(Smem<T, TX, TY> &S, int lx, int ly, int sc, int sp,
                                               int sm, int dslot, T L1s, T L23s, T L2q, T L3q,
-                                              const T *Fb, T *Fd, T k4 = T(0)) {
+                                              const T *Fb, T *Fd, T k4 = T(0), T L6h = T(0)) {
     using ST = Stencil<T>;
     using QS = typename Prec<T>::Q;
     T dx[5], dy[5], dz[5];
@@ -931,6 +1033,12 @@ __device__ __forceinline__ void regular_force(Smem<T, TX, TY> &S, int lx, int ly
         Fd[2] += k4 * (cz[4] + T(2) * cy[0] + cy[3] - cx[1]);
         Fd[3] += k4 * (T(2) * cx[4] - cz[1] - cy[2]);
         Fd[4] += k4 * (cy[1] - cx[0] - T(2) * cx[3] - cz[2]);
+        if (L6h != T(0)) {
+            T F6[5];
+            l6_regular(S, lx, ly, sc, sp, sm, L6h, T(Stencil<T>::scale), F6);
+#pragma unroll
+            for (int c = 0; c < 5; ++c) Fd[c] += F6[c];
+        }
     }
     (void)L2q; (void)L3q;
 }
@@ -1102,16 +1210,12 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
             if (col || row) one(rx, ry, col);
         }
     };
-    // (the cubic term takes the general path everywhere: no differences to share)
-    if constexpr (shared_diffs<T, FORM>()) {
-        if (FORM == 1 || args.L6 == T(0)) plane_diffs(z0, slot_of(z0), slot_of(z0 - 1), slot_of(z0 + 1));
-    }
+    if constexpr (shared_diffs<T, FORM>()) plane_diffs(z0, slot_of(z0), slot_of(z0 - 1), slot_of(z0 + 1));
 
     const T L1 = args.L1, L23 = args.L2 + args.L3;
-    // chiral / cubic terms: the cubic term takes the general path on every
-    // plane; the chiral term alone (L6 = 0) has a regular-site path
+    // chiral / cubic terms: both have a regular-site path (central
+    // differences; l6_regular) besides the general link-flux path
     constexpr bool ext = FORM == 2;
-    const bool chiral_only = ext && args.L6 == T(0);
     const T L4 = args.L4, L6 = ext ? args.L6 : T(0);
     const T sc_ = T(Stencil<T>::scale);
     const T L1s = L1 * sc_, L23s = L23 * sc_;
@@ -1140,7 +1244,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
         if (own) {
             uint8_t a = S.m(sc, lx - 1, ly) & S.m(sc, lx + 1, ly) & S.m(sc, lx, ly - 1) &
                         S.m(sc, lx, ly + 1) & S.m(sp, lx, ly) & S.m(sm, lx, ly) & m0;
-            reg = (m0 & FULL) == FULL && (a & 0xFC) == 0xFC && (!ext || chiral_only);
+            reg = (m0 & FULL) == FULL && (a & 0xFC) == 0xFC;
         }
         const I i = own ? LQ_CHK_IDX((I)z * NXY + (I)gy * (I)L.nx + (I)gx, N)
                         : (I)z * NXY + (I)gy * (I)L.nx + (I)gx;
@@ -1154,7 +1258,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
         // the next plane's central differences: planes z .. z+2 are published,
         // and the slot (z+1) & 1 was last read by the previous plane's force
         if constexpr (shared_diffs<T, FORM>()) {
-            if (z + 1 < z1 && (FORM == 1 || chiral_only)) plane_diffs(z + 1, sp, sc, s2);
+            if (z + 1 < z1) plane_diffs(z + 1, sp, sc, s2);
         }
 
         T Fd[5];
@@ -1175,7 +1279,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                     }
                 }
                 regular_force<THREE, ext>(S, lx, ly, sc, sp, sm, z & 1, L1s, L23s, L2q, L3q, fb0, Fd,
-                                          T(-0.5) * args.L4 * sc_);
+                                          T(-0.5) * args.L4 * sc_, T(0.5) * L6);
             }
         } else {
             // general path (planes touching objects or open edges): the z
