@@ -800,10 +800,11 @@ struct Stencil<float> {
 // G_B = sum_k [-Q_kk(j) D2_k + Q_kk(j - e_k) b_k - Q_kk(j + e_k) f_k]
 //     + 1/2 sum_k sum_{l != k} [Q_lk(j - e_k) C_l(j - e_k) - Q_lk(j + e_k) C_l(j + e_k)]
 // (D2_k = f_k - b_k); the force is -J^T (L6/2)(G_A + G_B).  Differences are
-// in storage units, s is the value of one unit.
+// in storage units, s is the value of one unit.  Inlined in the FP64 form;
+// a call in the FP32 form, whose 128 registers would spill (l6_regular_call).
 template <typename T, int TX, int TY>
-__device__ __noinline__ void l6_regular(Smem<T, TX, TY> &S, int lx, int ly, int sc, int sp, int sm,
-                                        T L6h, T s, T *F) {
+__device__ __forceinline__ void l6_regular(Smem<T, TX, TY> &S, int lx, int ly, int sc, int sp, int sm,
+                                           T L6h, T s, T *F) {
     using ST = Stencil<T>;
     using QS = typename Prec<T>::Q;
     QS c0[5], a[5], b[5];
@@ -890,6 +891,12 @@ __device__ __noinline__ void l6_regular(Smem<T, TX, TY> &S, int lx, int ly, int 
     F[2] = -L6h * (h * dot5(C[0], C[2]) + s * jb[2]);
     F[3] = -L6h * (h * (nrm[1] - nrm[2]) + s * jb[3]);
     F[4] = -L6h * (h * dot5(C[1], C[2]) + s * jb[4]);
+}
+
+template <typename T, int TX, int TY>
+__device__ __noinline__ void l6_regular_call(Smem<T, TX, TY> &S, int lx, int ly, int sc, int sp, int sm,
+                                             T L6h, T s, T *F) {
+    l6_regular(S, lx, ly, sc, sp, sm, L6h, s, F);
 }
 
 // Distortion force at a regular site: every site within the 19-point
@@ -1035,7 +1042,10 @@ __device__ __forceinline__ void regular_force(Smem<T, TX, TY> &S, int lx, int ly
         Fd[4] += k4 * (cy[1] - cx[0] - T(2) * cx[3] - cz[2]);
         if (L6h != T(0)) {
             T F6[5];
-            l6_regular(S, lx, ly, sc, sp, sm, L6h, T(Stencil<T>::scale), F6);
+            if constexpr (sizeof(T) == 8)
+                l6_regular(S, lx, ly, sc, sp, sm, L6h, T(Stencil<T>::scale), F6);
+            else
+                l6_regular_call(S, lx, ly, sc, sp, sm, L6h, T(Stencil<T>::scale), F6);
 #pragma unroll
             for (int c = 0; c < 5; ++c) Fd[c] += F6[c];
         }
