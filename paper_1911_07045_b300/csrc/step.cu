@@ -1557,7 +1557,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
 
 // one FIRE iteration of one lattice: one block per tile and z chunk
 template <typename T, int FORM, int TX, int TY, typename I>
-__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 512 / (TX * TY) : 1)
+__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? (FORM == 2 ? 384 : 512) / (TX * TY) : 1)
 fire_step_kernel(StepArgs<T> args) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[4 * (TX * TY / 32)];
@@ -1575,7 +1575,7 @@ fire_step_kernel(StepArgs<T> args) {
 // partial sums, last-block ticket and FIRE state, so a lattice advances
 // exactly as it would alone with the same tile and z chunk
 template <typename T, int FORM, int TX, int TY, typename I>
-__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 512 / (TX * TY) : 1)
+__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? (FORM == 2 ? 384 : 512) / (TX * TY) : 1)
 fire_batch_kernel(const StepArgs<T> *__restrict__ args, const WorkItem *__restrict__ items,
                   int nitems) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
