@@ -217,6 +217,38 @@ struct Site5<float> {
             }
         }
     }
+    // the old-state part of the kick, cv v + cFh F (the same operations as
+    // in kick)
+    __device__ static __forceinline__ void mix_old(const float *vold, const float *fold, float cv,
+                                                   float cFh, float *w) {
+        const float2 CV = make_float2(cv, cv), CF = make_float2(cFh, cFh);
+#pragma unroll
+        for (int c = 0; c < 4; c += 2) {
+            const float2 vo = make_float2(vold[c], vold[c + 1]), fo = make_float2(fold[c], fold[c + 1]);
+            const float2 vx = __ffma2_rn(CF, fo, __fmul2_rn(CV, vo));
+            w[c] = vx.x; w[c + 1] = vx.y;
+        }
+        w[4] = __fmaf_rn(cFh, fold[4], __fmul_rn(cv, vold[4]));
+    }
+    // kick from the kept old-state part: v_new = w + dt/2 F_new
+    __device__ static __forceinline__ void kick_w(const float *w, const float *fn, float hdt, float *vn,
+                                                  float &pv, float &ff, float &vv) {
+        const float2 H = make_float2(hdt, hdt);
+        float2 p2 = make_float2(0.f, 0.f), f2 = p2, v2 = p2;
+#pragma unroll
+        for (int c = 0; c < 4; c += 2) {
+            const float2 fnew = make_float2(fn[c], fn[c + 1]);
+            const float2 wv = __ffma2_rn(H, fnew, make_float2(w[c], w[c + 1]));
+            vn[c] = wv.x; vn[c + 1] = wv.y;
+            p2 = __ffma2_rn(fnew, wv, p2);
+            f2 = __ffma2_rn(fnew, fnew, f2);
+            v2 = __ffma2_rn(wv, wv, v2);
+        }
+        vn[4] = __fmaf_rn(hdt, fn[4], w[4]);
+        pv = __fmaf_rn(fn[4], vn[4], __fadd_rn(p2.x, p2.y));
+        ff = __fmaf_rn(fn[4], fn[4], __fadd_rn(f2.x, f2.y));
+        vv = __fmaf_rn(vn[4], vn[4], __fadd_rn(v2.x, v2.y));
+    }
     __device__ static __forceinline__ void kick(const float *vold, const float *fold, const float *fn,
                                                 float cv, float cFh, float hdt, float *vn, float &pv,
                                                 float &ff, float &vv) {
@@ -435,6 +467,12 @@ __device__ __forceinline__ void jt_extra_local(const T *mx, const T *my, const T
 // the tile and its ring with the five components of a site packed so that a
 // site loads in 2 (fixed point: int4 + int) or 3 (FP64: 2 double2 + double)
 // conflict-free instructions: [c0..c3 | c4] or [c0 c1 | c2 c3 | c4] arrays.
+// FP32 form: each own site's old-state part of the kick, cv v + cFh F, is
+// kept in shared memory from its drift to its kick (three planes), instead
+// of re-reading v, F; not in the L1/L2/L3 form, whose L1 it would shrink
+template <typename T, int FORM>
+__host__ __device__ constexpr bool keeps_w() { return sizeof(T) == 4 && FORM != 1; }
+
 template <typename T, int TX, int TY>
 struct Smem {
     using QS = typename Prec<T>::Q;
@@ -445,7 +483,12 @@ struct Smem {
     T *X;              // [2][2][5][PL] cross terms (general path)
     T *D;              // [2][2][5][PL] FP64 three-constant form: the central
                        // differences D_y, D_z of a plane (regular path)
+    T *W;              // [3][5][TX*TY] FP32 form: each own site's mixed old
+                       // velocity cv v + (cF + dt/2) F, kept from its drift
     uint8_t *M;        // [slots][PL]
+    __device__ __forceinline__ T &w(int slot, int c) {
+        return W[(LQ_CHK(slot, 3) * 5 + LQ_CHK(c, 5)) * (TX * TY) + threadIdx.x];
+    }
     __device__ __forceinline__ int idx(int lx, int ly) const { return LQ_CHK(ly, SY) * SX + LQ_CHK(lx, SX); }
     __device__ __forceinline__ QS &q(int slot, int c, int lx, int ly) {
         unsigned char *b = Q + LQ_CHK(slot, 5) * SLOT_BYTES;
@@ -1074,7 +1117,9 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
     S.X = reinterpret_cast<T *>(smem_raw + NSLOT * SM::SLOT_BYTES);
     S.D = S.X + (THREE ? 2 * 2 * 5 * SM::PL : 0);
     constexpr bool DIFFS = sizeof(T) == 8 && THREE;
-    S.M = reinterpret_cast<uint8_t *>(S.D + (DIFFS ? 2 * 2 * 5 * SM::PL : 0));
+    constexpr bool WCACHE = keeps_w<T, FORM>();
+    S.W = S.D + (DIFFS ? 2 * 2 * 5 * SM::PL : 0);
+    S.M = reinterpret_cast<uint8_t *>(S.W + (WCACHE ? 3 * 5 * NT : 0));
     const LatticeDev L = args.L;
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const int x0 = bx * TX, y0 = by * TY;
@@ -1174,6 +1219,20 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
         S.store5(slot, sx, sy, qh);
     };
 
+    // FP32 form: the own site's part of the kick that needs only the old
+    // state, cv v + cFh F, computed while v, F are in registers
+    auto keep_w = [&](int z, const Raw &r) {
+        if constexpr (WCACHE) {
+            if (!fo_mode && (r.m & M_SIM)) {
+                T w[5];
+                Site5<T>::mix_old(r.v, r.f, cv, cFh, w);
+                const int ws = ((z % 3) + 3) % 3;
+#pragma unroll
+                for (int c = 0; c < 5; ++c) S.w(ws, c) = w[c];
+            }
+        }
+    };
+
     // plane z lives in slot z mod 5: at step z the slots of z-1, z, z+1 are
     // read, z+2 is written before the barrier; slot z+3 = z-2 is the one the
     // next step writes, which no thread of this step reads
@@ -1185,6 +1244,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
         for (int p = -1; p <= 1; ++p) {
             fetch(in_own, xy_own, z0 + p, r);
             commit(slot_of(z0 + p), lx, ly, r, true);
+            if (p >= 0) keep_w(z0 + p, r);
             if (rx >= 0) {
                 fetch(in_ring, xy_ring, z0 + p, r);
                 commit(slot_of(z0 + p), rx, ry, r, false);
@@ -1241,6 +1301,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
         // pipeline: plane z+2 into its slot, plane z+3 in flight
         if (z + 2 <= z1) {
             commit(s2, lx, ly, pf_own, true);
+            if (z + 2 < z1) keep_w(z + 2, pf_own);
             if (rx >= 0) commit(s2, rx, ry, pf_ring, false);
         }
         if (z + 3 <= z1) {
@@ -1259,9 +1320,11 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
         const I i = own ? LQ_CHK_IDX((I)z * NXY + (I)gy * (I)L.nx + (I)gx, N)
                         : (I)z * NXY + (I)gy * (I)L.nx + (I)gx;
         T vold[5], fold[5];
-        if (own && !fo_mode) {
+        if constexpr (!WCACHE) {
+            if (own && !fo_mode) {
 #pragma unroll
-            for (int c = 0; c < 5; ++c) { vold[c] = __ldg(vin + c * N + i); fold[c] = __ldg(Fin + c * N + i); }
+                for (int c = 0; c < 5; ++c) { vold[c] = __ldg(vin + c * N + i); fold[c] = __ldg(Fin + c * N + i); }
+            }
         }
         // the barrier publishes plane z+2 and decides the path of this plane
         const bool all_reg = __syncthreads_and(reg) != 0;
@@ -1507,7 +1570,14 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                 for (int c = 0; c < 5; ++c) Fout[c * N + i] = Fn[c];
             } else {
                 T pv, ff, vv, vn[5];
-                Site5<T>::kick(vold, fold, Fn, cv, cFh, hdt, vn, pv, ff, vv);
+                if constexpr (WCACHE) {
+                    T w[5];
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) w[c] = S.w(z % 3, c);
+                    Site5<T>::kick_w(w, Fn, hdt, vn, pv, ff, vv);
+                } else {
+                    Site5<T>::kick(vold, fold, Fn, cv, cFh, hdt, vn, pv, ff, vv);
+                }
 #pragma unroll
                 for (int c = 0; c < 5; ++c) {
                     __stcs(qout + c * N + i, q0[c]);
@@ -1591,13 +1661,15 @@ fire_batch_kernel(const StepArgs<T> *__restrict__ args, const WorkItem *__restri
 
 // ---- host launchers ---------------------------------------------------------
 
-template <typename T, bool THREE, int TX, int TY>
+template <typename T, int FORM, int TX, int TY>
 static size_t step_smem_bytes() {
+    constexpr bool THREE = FORM >= 1;
     using SM = Smem<T, TX, TY>;
     constexpr int PL = SM::PL;
     constexpr bool DIFFS = sizeof(T) == 8 && THREE;   // shared_diffs (form 1; unused by form 2)
     size_t b = 5 * (size_t)SM::SLOT_BYTES + sizeof(T) * (THREE ? 2 * 2 * 5 * PL : 0) +
-               sizeof(T) * (DIFFS ? 2 * 2 * 5 * PL : 0) + 5 * PL;
+               sizeof(T) * (DIFFS ? 2 * 2 * 5 * PL : 0) + 5 * PL +
+               (keeps_w<T, FORM>() ? sizeof(T) * 3 * 5 * TX * TY : 0);
     return (b + 15) & ~size_t(15);
 }
 
@@ -1634,7 +1706,7 @@ template <typename T, int FORM, int TX, int TY, typename I>
 static cudaError_t launch_impl(const StepLaunch &sl, cudaStream_t stream) {
     StepArgs<T> a;
     pack_args<T>(sl, a);
-    size_t smem = step_smem_bytes<T, (FORM >= 1), TX, TY>();
+    size_t smem = step_smem_bytes<T, FORM, TX, TY>();
     auto kern = fire_step_kernel<T, FORM, TX, TY, I>;
     dim3 grid = step_grid(sl.L, sl.zchunk, TX, TY);
     kern<<<grid, TX * TY, smem, stream>>>(a);
@@ -1687,12 +1759,12 @@ struct PrepareStep {
     cudaError_t run() {
         cudaError_t e = cudaFuncSetAttribute(fire_step_kernel<T, FORM, 32, TY, I>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)step_smem_bytes<T, (FORM >= 1), 32, TY>());
+                                             (int)step_smem_bytes<T, FORM, 32, TY>());
         if constexpr (sizeof(T) == 4 && FORM == 0) {
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(fire_step_kernel<T, FORM, 64, TY, I>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)step_smem_bytes<T, false, 64, TY>());
+                                         (int)step_smem_bytes<T, 0, 64, TY>());
         }
         return e;
     }
@@ -1739,7 +1811,7 @@ struct PrepareBatch {
     cudaError_t run() {
         return cudaFuncSetAttribute(fire_batch_kernel<T, FORM, 32, TY, I>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)step_smem_bytes<T, (FORM >= 1), 32, TY>());
+                                    (int)step_smem_bytes<T, FORM, 32, TY>());
     }
 };
 
@@ -1748,7 +1820,7 @@ struct BlocksBatch {
     int run() {
         int nb = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fire_batch_kernel<T, FORM, 32, TY, I>,
-                                                      32 * TY, step_smem_bytes<T, (FORM >= 1), 32, TY>());
+                                                      32 * TY, step_smem_bytes<T, FORM, 32, TY>());
         return nb;
     }
 };
@@ -1760,7 +1832,7 @@ struct LaunchBatch {
     cudaStream_t stream;
     template <typename T, int FORM, int TY, typename I>
     cudaError_t run() {
-        fire_batch_kernel<T, FORM, 32, TY, I><<<grid, 32 * TY, step_smem_bytes<T, (FORM >= 1), 32, TY>(),
+        fire_batch_kernel<T, FORM, 32, TY, I><<<grid, 32 * TY, step_smem_bytes<T, FORM, 32, TY>(),
                                                 stream>>>(static_cast<const StepArgs<T> *>(args), items,
                                                           nitems);
         return cudaGetLastError();
