@@ -43,7 +43,8 @@ DESIGN_BYTES = {"fp32": 6 * 5 * 4 + 1, "fp64": 6 * 5 * 8 + 1}
 # launch grows with the sites it updates); the bench scales it to its lattice.
 # The FP64 one-constant form moves the same state bytes as the three-constant
 # one and takes its figure.
-DRAM_BYTES_PER_SITE = {"fp32": 2.035445e9 / 256 ** 3, "fp64": 4.210749e9 / 256 ** 3,
+DRAM_BYTES_PER_SITE = {"fp32": (1.075125e9 + 0.961110e9) / 256 ** 3,
+                       "fp64": (2.252918e9 + 1.955041e9) / 256 ** 3,
                        "fp32_1c": (1.060582e9 + 0.956583e9) / 256 ** 3}
 # FP64 form: bound by the FP64 pipe (2 FP64 operations per clock per SM).
 # FP64 arithmetic operations per site-update of the regular three-constant
@@ -238,15 +239,22 @@ def run_form(precision: str, L: int, steps: int, warmup: int, dist: Dist, sample
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     s.set_q(q_host)
-    for _ in range(k_e2e):
+    for j in range(k_e2e):
         r = s.step(p, 1)        # returns the residual (max |F|) to the host
+        if j == 0:
+            ta = time.perf_counter()
+    tb = time.perf_counter()
     s._ck(s.lib.lq_get_q(s.h, lqmin._ptr(q_host)))
     t1 = time.perf_counter()
     dist.barrier()
     e2e_val, _ = aggregate(dist, N * k_e2e, t1 - t0)
     out["e2e"] = dict(value=e2e_val, unit=UNIT, steps=k_e2e,
                       h2d_bytes_per_step=int(5 * N * 8 / k_e2e),
-                      d2h_bytes_per_step=int((5 * N * 8) / k_e2e + 160))
+                      d2h_bytes_per_step=int((5 * N * 8) / k_e2e + 160),
+                      # where the time goes: the upload with the first step,
+                      # the other steps (each with its residual read), the download
+                      upload_and_first_step_s=round(ta - t0, 4), steps_s=round(tb - ta, 4),
+                      download_s=round(t1 - tb, 4))
     s.close()
     return out
 

@@ -480,7 +480,9 @@ struct Smem {
     static constexpr int PL = ((SX * SY + 3) / 4) * 4;          // sites per plane slot
     static constexpr int SLOT_BYTES = 5 * sizeof(QS) * PL;      // multiple of 16
     unsigned char *Q;  // [slots] x SLOT_BYTES
-    T *X;              // [2][2][5][PL] cross terms (general path)
+    T *X;              // [2][5][PL] cross terms of one plane (general path):
+                       // the plane barrier orders the last reads of a plane
+                       // before the first writes of the next
     T *D;              // [2][2][5][PL] FP64 three-constant form: the central
                        // differences D_y, D_z of a plane (regular path)
     T *W;              // [3][5][TX*TY] FP32 form: each own site's mixed old
@@ -531,8 +533,8 @@ struct Smem {
         return M[LQ_CHK(slot, 5) * PL + idx(lx, ly)];
     }
 
-    __device__ __forceinline__ T &x(int slot, int ax, int c, int lx, int ly) {
-        return X[((LQ_CHK(slot, 2) * 2 + LQ_CHK(ax, 2)) * 5 + LQ_CHK(c, 5)) * PL + idx(lx, ly)];
+    __device__ __forceinline__ T &x(int ax, int c, int lx, int ly) {
+        return X[(LQ_CHK(ax, 2) * 5 + LQ_CHK(c, 5)) * PL + idx(lx, ly)];
     }
     __device__ __forceinline__ T &d(int slot, int ax, int c, int lx, int ly) {
         return D[((LQ_CHK(slot, 2) * 2 + LQ_CHK(ax, 2)) * 5 + LQ_CHK(c, 5)) * PL + idx(lx, ly)];
@@ -1115,7 +1117,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
     SM S;
     S.Q = smem_raw;
     S.X = reinterpret_cast<T *>(smem_raw + NSLOT * SM::SLOT_BYTES);
-    S.D = S.X + (THREE ? 2 * 2 * 5 * SM::PL : 0);
+    S.D = S.X + (THREE ? 2 * 5 * SM::PL : 0);
     constexpr bool DIFFS = sizeof(T) == 8 && THREE;
     constexpr bool WCACHE = keeps_w<T, FORM>();
     S.W = S.D + (DIFFS ? 2 * 2 * 5 * SM::PL : 0);
@@ -1390,7 +1392,6 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                 link_flux<2, THREE, ext>(S.m(sm, lx, ly), m0, qa, qb, xz_m, xz_cur, L1, L23, phi_zm, L6);
             }
             T xz_nxt[5], mx_nxt[5], my_nxt[5];
-            const int xs = z & 1;
             if (THREE) {
                 // cross terms of the tile at plane z
                 if (m0 & M_SIM) {
@@ -1404,7 +1405,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                         for (int c = 0; c < 5; ++c) o[c] += e[c];
                     }
 #pragma unroll
-                    for (int c = 0; c < 5; ++c) S.x(xs, 0, c, lx, ly) = o[c];
+                    for (int c = 0; c < 5; ++c) S.x(0, c, lx, ly) = o[c];
                     jt_cross<1>(mx_cur, mz_cur, args.L2, args.L3, o);
                     if (ext) {
                         jt_extra_x<1>(qv, mx_cur, mz_cur, L4, L6, e);
@@ -1412,7 +1413,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                         for (int c = 0; c < 5; ++c) o[c] += e[c];
                     }
 #pragma unroll
-                    for (int c = 0; c < 5; ++c) S.x(xs, 1, c, lx, ly) = o[c];
+                    for (int c = 0; c < 5; ++c) S.x(1, c, lx, ly) = o[c];
                 }
                 // ring: X_x on the left/right columns, X_y on the top/bottom rows
                 if ((int)threadIdx.x < 2 * TY) {
@@ -1430,7 +1431,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                             for (int c = 0; c < 5; ++c) o[c] += e[c];
                         }
 #pragma unroll
-                        for (int c = 0; c < 5; ++c) S.x(xs, 0, c, sx, sy) = o[c];
+                        for (int c = 0; c < 5; ++c) S.x(0, c, sx, sy) = o[c];
                     }
                 } else if ((int)threadIdx.x < 2 * TY + 2 * TX) {
                     int r = threadIdx.x - 2 * TY;
@@ -1448,7 +1449,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                             for (int c = 0; c < 5; ++c) o[c] += e[c];
                         }
 #pragma unroll
-                        for (int c = 0; c < 5; ++c) S.x(xs, 1, c, sx, sy) = o[c];
+                        for (int c = 0; c < 5; ++c) S.x(1, c, sx, sy) = o[c];
                     }
                 }
                 // in-plane means and z cross term of the own column at plane z + 1
@@ -1486,7 +1487,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
 #pragma unroll
                 for (int c = 0; c < 5; ++c) {
                     qn[c] = S.q(sc, c, lx - 1, ly);
-                    if (THREE) { xa[c] = S.x(xs, 0, c, lx - 1, ly); xb[c] = S.x(xs, 0, c, lx, ly); }
+                    if (THREE) { xa[c] = S.x(0, c, lx - 1, ly); xb[c] = S.x(0, c, lx, ly); }
                 }
                 link_flux<0, THREE, ext>(S.m(sc, lx - 1, ly), m0, qn, q0, xa, xb, L1, L23, phi, L6);
 #pragma unroll
@@ -1495,7 +1496,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
 #pragma unroll
                 for (int c = 0; c < 5; ++c) {
                     qn[c] = S.q(sc, c, lx + 1, ly);
-                    if (THREE) { xa[c] = xb[c]; xb[c] = S.x(xs, 0, c, lx + 1, ly); }
+                    if (THREE) { xa[c] = xb[c]; xb[c] = S.x(0, c, lx + 1, ly); }
                 }
                 link_flux<0, THREE, ext>(m0, S.m(sc, lx + 1, ly), q0, qn, xa, xb, L1, L23, phi, L6);
 #pragma unroll
@@ -1504,7 +1505,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
 #pragma unroll
                 for (int c = 0; c < 5; ++c) {
                     qn[c] = S.q(sc, c, lx, ly - 1);
-                    if (THREE) { xa[c] = S.x(xs, 1, c, lx, ly - 1); xb[c] = S.x(xs, 1, c, lx, ly); }
+                    if (THREE) { xa[c] = S.x(1, c, lx, ly - 1); xb[c] = S.x(1, c, lx, ly); }
                 }
                 link_flux<1, THREE, ext>(S.m(sc, lx, ly - 1), m0, qn, q0, xa, xb, L1, L23, phi, L6);
 #pragma unroll
@@ -1513,7 +1514,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
 #pragma unroll
                 for (int c = 0; c < 5; ++c) {
                     qn[c] = S.q(sc, c, lx, ly + 1);
-                    if (THREE) { xa[c] = xb[c]; xb[c] = S.x(xs, 1, c, lx, ly + 1); }
+                    if (THREE) { xa[c] = xb[c]; xb[c] = S.x(1, c, lx, ly + 1); }
                 }
                 link_flux<1, THREE, ext>(m0, S.m(sc, lx, ly + 1), q0, qn, xa, xb, L1, L23, phi, L6);
 #pragma unroll
@@ -1667,7 +1668,7 @@ static size_t step_smem_bytes() {
     using SM = Smem<T, TX, TY>;
     constexpr int PL = SM::PL;
     constexpr bool DIFFS = sizeof(T) == 8 && THREE;   // shared_diffs (form 1; unused by form 2)
-    size_t b = 5 * (size_t)SM::SLOT_BYTES + sizeof(T) * (THREE ? 2 * 2 * 5 * PL : 0) +
+    size_t b = 5 * (size_t)SM::SLOT_BYTES + sizeof(T) * (THREE ? 2 * 5 * PL : 0) +
                sizeof(T) * (DIFFS ? 2 * 2 * 5 * PL : 0) + 5 * PL +
                (keeps_w<T, FORM>() ? sizeof(T) * 3 * 5 * TX * TY : 0);
     return (b + 15) & ~size_t(15);
