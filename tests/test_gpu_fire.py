@@ -172,3 +172,44 @@ def test_fp32_form_reaches_fp64_minimum(oracle_mod):
     assert abs(r.energy - Eo) <= 1e-6 * abs(Eo)
     sim = o.simulated()
     assert np.abs(s.order_field()[sim] - o.order_field(qo)[sim]).max() < 1e-4
+
+
+FP32_KERNELS = {
+    # one constant on a lattice narrower than 256 sites: 32-wide tiles
+    "one_constant_32wide": dict(shape=(40, 20, 18), L=(2.32, 0.0, 0.0), extra={},
+                                objects=[dict(type="sphere", c=(20.0, 10.0, 9.0), R=4.5,
+                                              anchor=HOM())]),
+    # one constant, 256 sites wide: 64-wide tiles
+    "one_constant_64wide": dict(shape=(256, 10, 12), L=(2.32, 0.0, 0.0), extra={},
+                                objects=[dict(type="wall", axis=2, plane=0, anchor=HOM()),
+                                         dict(type="wall", axis=2, plane=11, anchor=PLANAR()),
+                                         dict(type="sphere", c=(128.0, 5.0, 6.0), R=3.0,
+                                              anchor=HOM())]),
+    # three constants: the kernel that reads the own site's v, F again at the kick
+    "three_constants": dict(GEOMS["colloid_walls_3c"], extra={}),
+    # the chiral term and a field: the third kernel form
+    "chiral_field": dict(GEOMS["colloid_walls_3c"],
+                         extra=dict(L4=0.7, H=(0.3, -0.2, 0.5), mu0_dchi=1.3)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(FP32_KERNELS))
+def test_fp32_form_steps_in_every_kernel_form(oracle_mod, name):
+    """Five FIRE steps of the FP32 form against the FP64 oracle in each of
+    its kernel forms.  The one-constant and chiral kernels keep each own
+    site's cv v + (cF + dt/2) F in shared memory from its drift to its kick;
+    a wrong or stale coefficient there shows as an O(1e-2) error in v."""
+    c = FP32_KERNELS[name]
+    s, o = make_pair(oracle_mod, c["shape"], c["L"], c["objects"], precision=1, **c["extra"])
+    q0 = np.round(synth.random_uniaxial_q(c["shape"], 12) * 2.0 ** 28) / 2.0 ** 28
+    s.set_q(q0)
+    params = dict(FP, max_iter=10 ** 6, force_tol=1e-12)
+    r = s.step(lqmin.fire_params(**params), 5)
+    qo, vo, Fo, st = o.fire(q0, params, 5)
+    sim = o.simulated()
+    assert r.iterations == st["iter"] == 5
+    assert abs(r.dt - st["dt"]) <= 1e-12 * st["dt"]
+    # measured: q 1.7e-8, F 1.2e-7 to 1.4e-7, v 1.4e-7 to 1.7e-7 (float rounding)
+    assert rel(s.get_q()[:, sim], qo[:, sim]) < 2e-7
+    assert rel(s.get_force()[:, sim], Fo[:, sim]) < 2e-6
+    assert rel(s.get_velocity()[:, sim], vo[:, sim]) < 2e-6
