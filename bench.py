@@ -556,10 +556,7 @@ def main_ours(args, dist: Dist):
         "steps": h["launches"], "warmup": args.warmup, "ms_per_step": h["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if head == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": f"{args.size}^3 lattice, 4 homeotropic colloids (W=5.3), planar "
-                               f"walls z=0,{args.size - 1} (W=1), L1/L2/L3=2.32/0.5/0.3, random "
-                               f"uniaxial start (seed 3)",
-                   "form": head, "sites_per_gpu": h["N"], "simulated_sites": h["nsim"],
+        "config": {"workload": workload_name(args.size), "form": head, "sites_per_gpu": h["N"], "simulated_sites": h["nsim"],
                    "anchored_sites": h["nanchored"],
                    "parallelism": f"replicas x{dist.world}" if dist.world > 1 else "1 GPU",
                    "l2": "inputs larger than L2 (state > 126 MB)"},
@@ -591,6 +588,11 @@ def main_ours(args, dist: Dist):
     return line
 
 
+def workload_name(size: int) -> str:
+    return (f"{size}^3 lattice, 4 homeotropic colloids (W=5.3), planar walls z=0,{size - 1} (W=1), "
+            f"L1/L2/L3=2.32/0.5/0.3, random uniaxial start (seed 3)")
+
+
 def main_reference(args, dist: Dist):
     """CPU oracle as the reference arm: each step is one FIRE iteration of
     the oracle on a bounded 96^3 sample of the workload."""
@@ -616,8 +618,9 @@ def main_reference(args, dist: Dist):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"{args.size}^3 lattice workload, sampled at {Ls}^3",
-                       "form": "fp64 oracle"},
+            "config": {"workload": workload_name(args.size), "form": "fp64 oracle",
+                       "sample": f"{Ls}^3 lattice with the same structure",
+                       "parallelism": f"1 process, {oracle.num_threads()} host threads"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
