@@ -45,7 +45,7 @@ def requests():
 
 
 def params():
-    # the benchmark spec tolerance: two runs that differ by rounding then agree in S
+    # convergence to max|F| < 1e-6: two runs that differ by rounding then agree in S
     # to ~|F| / (slowest stiffness ~0.03) = 3e-5
     return lqmin.fire_params(**dict(synth.FIRE_DEFAULTS, max_iter=200000, force_tol=1e-6))
 
