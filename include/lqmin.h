@@ -345,7 +345,9 @@ typedef struct lq_batch lq_batch;
 lq_status lq_batch_create(lq_solver *const *solvers, int n, lq_batch **out);
 void lq_batch_destroy(lq_batch *b);
 const char *lq_batch_last_error(const lq_batch *b);
-/* Tiling of the persistent kernel: tile 32 x tile_y (4 or 8), z chunk > 0. */
+/* Tiling of the persistent kernel: tile 32 x tile_y (4 or 8) and z chunk
+   (0 = each lattice's own z chunk, as lq_set_zchunk left it); LQ_EINVAL for
+   other tile heights or a negative z chunk, the tiling unchanged. */
 lq_status lq_batch_set_tiling(lq_batch *b, int tile_y, int zchunk);
 lq_status lq_batch_get_tiling(const lq_batch *b, int *tile_y, int *zchunk);
 /* Autotuner: times every tile_y in {4, 8} and z chunk in {8, ..., 128} over

@@ -352,7 +352,9 @@ void lq_batch_destroy(lq_batch *b) {
 const char *lq_batch_last_error(const lq_batch *b) { return b ? b->err.c_str() : "null batch"; }
 
 lq_status lq_batch_set_tiling(lq_batch *b, int tile_y, int zchunk) {
-    if (!b || (tile_y != 4 && tile_y != 8) || zchunk < 0) return LQ_EINVAL;
+    if (!b) return LQ_EINVAL;
+    if ((tile_y != 4 && tile_y != 8) || zchunk < 0)
+        return bfail(b, LQ_EINVAL, "tile height must be 4 or 8 and the z chunk >= 0");
     cudaSetDevice(b->device);
     return set_tiling(b, tile_y, zchunk);
 }

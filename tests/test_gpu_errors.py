@@ -101,3 +101,37 @@ def test_bad_calls_change_nothing(precision):
     assert np.array_equal(a.mask(), b.mask())
     a.close()
     b.close()
+
+
+def test_batch_rejects_mixed_members_and_bad_tiling():
+    """A batch needs one precision and one distortion form; tile heights are
+    4 or 8 and z chunks >= 0.  Failed calls leave no batch, or the batch as
+    it was."""
+    def solver(precision=lqmin.LQ_FP64, L=(2.32, 0.5, 0.3)):
+        s = lqmin.Solver((20, 16, 12), synth.A_5CB, synth.B_5CB, synth.C_5CB, *L,
+                         precision=precision)
+        s.set_q(synth.random_uniaxial_q((20, 16, 12), 5))
+        return s
+    a, b = solver(), solver()
+    f32 = solver(precision=lqmin.LQ_FP32_BULK_FP64_RED)
+    one = solver(L=(2.32, 0.0, 0.0))
+    lib = a.lib
+    out = C.c_void_p(99)
+    for members in ([a, f32], [a, one]):
+        arr = (C.c_void_p * len(members))(*[m.h.value for m in members])
+        assert lib.lq_batch_create(arr, len(members), C.byref(out)) == lqmin.LQ_EINVAL
+        assert out.value is None
+    arr = (C.c_void_p * 2)(a.h.value, b.h.value)
+    assert lib.lq_batch_create(arr, 0, C.byref(out)) == lqmin.LQ_EINVAL
+    assert lib.lq_batch_create(None, 2, C.byref(out)) == lqmin.LQ_EINVAL
+    batch = lqmin.Batch([a, b])
+    before = batch.tiling()
+    for ty, zc in ((5, 16), (4, -1), (8, -3)):
+        assert lib.lq_batch_set_tiling(batch.h, ty, zc) == lqmin.LQ_EINVAL
+        assert lib.lq_batch_last_error(batch.h).decode()
+    assert batch.tiling() == before
+    res = batch.step(lqmin.fire_params(**FP), 3)
+    assert [r.iterations for r in res] == [3, 3]
+    batch.close()
+    for s in (a, b, f32, one):
+        s.close()
