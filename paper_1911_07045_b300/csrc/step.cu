@@ -469,7 +469,8 @@ __device__ __forceinline__ void jt_extra_local(const T *mx, const T *my, const T
 // conflict-free instructions: [c0..c3 | c4] or [c0 c1 | c2 c3 | c4] arrays.
 // FP32 form: each own site's old-state part of the kick, cv v + cFh F, is
 // kept in shared memory from its drift to its kick (three planes), instead
-// of re-reading v, F; not in the L1/L2/L3 form, whose L1 it would shrink
+// of re-reading v, F; not in the L1/L2/L3 form, where at 128 registers it
+// causes spills and runs slower
 template <typename T, int FORM>
 __host__ __device__ constexpr bool keeps_w() { return sizeof(T) == 4 && FORM != 1; }
 
