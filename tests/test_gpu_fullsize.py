@@ -1,8 +1,10 @@
 """The benchmark workload at full size (512^3, four colloids, planar walls,
-three constants), in the launch configuration the benchmark times: one FIRE
-step of each precision form from a seeded random start, compared with the
-oracle at sampled sites -- tile and chunk seams, the walls, the colloid
-surfaces and random interior sites -- plus properties that hold at any size.
+three constants, and the same geometry with one constant), in the launch
+configurations the benchmark times (the one-constant FP32 form on 64-wide
+tiles): one FIRE step of each precision form from a seeded random start,
+compared with the oracle at sampled sites -- tile and chunk seams, the
+walls, the colloid surfaces and random interior sites -- plus properties
+that hold at any size.
 
 Expected values at the samples come from the oracle alone: the force at q0
 (Eq. 10 with the averaged differences of Eqs. 7-9), the velocity-Verlet drift
@@ -38,8 +40,8 @@ def samples(cfg, seed=0):
     nx, ny, nz = cfg["shape"]
     r = np.random.default_rng(seed)
     pts = [r.integers(0, nx * ny * nz, 1500)]
-    # tile seams (32 x 4 and 32 x 8 tiles) and chunk seams along z
-    xs = np.array([0, 1, 31, 32, 33, 63, 64, 255, 256, 510, 511])
+    # tile seams (32 x 4, 32 x 8 and 64 x 4 tiles) and chunk seams along z
+    xs = np.array([0, 1, 31, 32, 33, 63, 64, 65, 127, 128, 255, 256, 510, 511])
     ys = np.array([0, 3, 4, 7, 8, 11, 12, 255, 256, 511])
     zs = np.array([0, 1, 2, 3, 7, 8, 15, 16, 31, 32, 63, 64, 127, 128, 129, 255, 256,
                    383, 384, 508, 509, 510, 511])
@@ -59,10 +61,12 @@ def samples(cfg, seed=0):
     return np.unique(np.concatenate(pts))
 
 
-@pytest.fixture(scope="module")
-def workload(oracle_mod):
+@pytest.fixture(scope="module", params=["three_constants", "one_constant"])
+def workload(request, oracle_mod):
     need_gpu()
     cfg = synth.config_large(L)
+    if request.param == "one_constant":
+        cfg = dict(cfg, L2=0.0, L3=0.0)
     q0 = synth.random_uniaxial_q(cfg["shape"], cfg["seed"])
     o = oracle_mod.Oracle(cfg["shape"], synth.A_5CB, synth.B_5CB, synth.C_5CB, cfg["L1"],
                           cfg["L2"], cfg["L3"], objects=cfg["objects"])
