@@ -177,3 +177,43 @@ def test_chiral_alone_fp32_form_and_steps(oracle_mod, name):
     assert r.iterations == st["iter"] == 60
     sim = o.simulated()
     assert np.abs(f64.get_q()[:, sim] - qo[:, sim]).max() < 1e-9
+
+
+@pytest.mark.parametrize("precision", [lqmin.LQ_FP64, lqmin.LQ_FP32_BULK_FP64_RED])
+@pytest.mark.parametrize("L6", [0.0, 0.9])
+def test_helix_energy_on_the_gpu_is_the_closed_form(precision, L6):
+    """A twist helix n = (cos kz, sin kz, 0) on a periodic lattice: every
+    site sees the same averaged differences, so the distortion energy per
+    site is (9 S^2/8) L1 (1 - cos 2k) + (9 S^2/16) L4 sin 2k
+    - (9 L6 S^3/16)(1 - cos 2k), with no L2, L3 part (Q_iz = 0 for i != z).
+    The GPU's energy equals N times that, and the lowest-energy helix among
+    the lattice's wave numbers is the one nearest tan 2k = -L4 / (2 L1)
+    (with L6 = 0); no bulk terms (A = B = C = 0, S0 given)."""
+    shape = (4, 4, 120)
+    S, L1 = 0.5, 2.32
+    z = np.repeat(np.arange(shape[2]), shape[0] * shape[1]).astype(float)
+    N = shape[0] * shape[1] * shape[2]
+    for L4 in (-0.5, 0.5):
+        s = lqmin.Solver(shape, 0.0, 0.0, 0.0, L1, 0.5, 0.3, precision=precision, L4=L4, L6=L6,
+                         n_constants=3, S0=S)
+        ks = 2 * np.pi * np.arange(-6, 7) / shape[2]
+        E = []
+        for k in ks:
+            n = np.stack([np.cos(k * z), np.sin(k * z), np.zeros_like(z)])
+            q = synth.uniaxial_q(n, S)
+            if precision == lqmin.LQ_FP32_BULK_FP64_RED:
+                q = np.round(q * 2.0 ** 28) / 2.0 ** 28
+            s.set_q(q)
+            _, parts = s.energy()
+            per = (9 * S ** 2 / 8 * L1 * (1 - np.cos(2 * k)) + 9 * S ** 2 / 16 * L4 * np.sin(2 * k)
+                   - 9 * L6 * S ** 3 / 16 * (1 - np.cos(2 * k)))
+            # FP32 form: the energy of the fixed-point-rounded state
+            tol = 1e-12 if precision == lqmin.LQ_FP64 else 2e-6
+            assert abs(parts[1] - N * per) <= tol * N * max(abs(per), 1e-3)
+            E.append(parts[1])
+        if L6 == 0.0:
+            kbest = ks[int(np.argmin(E))]
+            kstar = -0.5 * np.arctan(L4 / (2 * L1))
+            assert np.sign(kbest) == np.sign(kstar)
+            assert abs(kbest - kstar) <= np.pi / shape[2]
+        s.close()
