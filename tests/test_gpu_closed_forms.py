@@ -84,3 +84,41 @@ def test_plane_wave_is_an_eigenvector_of_the_one_constant_force(precision, nx, e
         assert np.abs(F[[2, 4]]).max() <= (1e-30 if precision == lqmin.LQ_FP64 else 1e-12)
         assert np.abs(F[[0, 3]]).max() <= 2 * abs(B) * eps ** 2
     s.close()
+
+
+@pytest.mark.parametrize("precision", [lqmin.LQ_FP64, lqmin.LQ_FP32_BULK_FP64_RED])
+@pytest.mark.parametrize("kind", [lqmin.ND_HOMEOTROPIC, lqmin.FG_PLANAR])
+def test_wall_anchoring_energy_of_a_uniform_director(precision, kind):
+    """A wall at z = 0 (normal nu = e_z) and a uniform uniaxial state at S0
+    with director n, c = n . nu.  Per boundary site (area weight 1):
+    Nobili-Durand homeotropic W |Q - Q0|^2 = W (9 S0^2 / 2)(1 - c^2);
+    Fournier-Galatola planar W |Qt - P Qt P|^2 = W (9 S0^2 / 4)(2 c^2 - c^4)
+    (Qt = Q + S0/2 I = 3 S0/2 nn, P = I - nu nu).  The aligned state (c = 1
+    homeotropic, c = 0 planar) feels no force anywhere."""
+    shape = (8, 6, 10)
+    W = 1.7
+    s = lqmin.Solver(shape, A, B, C, 2.32, 0.5, 0.3, precision=precision)
+    s.add_wall(2, 0, kind, W)
+    S0 = synth.s0_closed_form(A, B, C)
+    N = shape[0] * shape[1] * shape[2]
+    _, nanch = s.geometry_info()
+    assert nanch == 2 * shape[0] * shape[1]      # planes z = 1 and z = 9 (periodic)
+    tol = 1e-12 if precision == lqmin.LQ_FP64 else 1e-6
+    for c in (1.0, 0.6, 0.0):
+        n = np.array([[math.sqrt(1 - c * c)], [0.0], [c]])
+        q = np.repeat(synth.uniaxial_q(n, S0), N, axis=1)
+        if precision == lqmin.LQ_FP32_BULK_FP64_RED:
+            q = np.round(q * 2.0 ** 28) / 2.0 ** 28
+        s.set_q(q)
+        _, parts = s.energy()
+        if kind == lqmin.ND_HOMEOTROPIC:
+            per = W * 4.5 * S0 ** 2 * (1 - c * c)
+        else:
+            per = W * 2.25 * S0 ** 2 * (2 * c * c - c ** 4)
+        assert abs(parts[2] - nanch * per) <= tol * max(nanch * per, 1.0)
+        assert abs(parts[1]) <= tol        # uniform: no distortion energy
+        aligned = (c == 1.0) if kind == lqmin.ND_HOMEOTROPIC else (c == 0.0)
+        if aligned:
+            sim = s.mask() & 1
+            assert np.abs(s.force()[:, sim.astype(bool)]).max() < (1e-12 if tol == 1e-12 else 1e-6)
+    s.close()
