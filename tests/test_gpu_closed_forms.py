@@ -122,3 +122,34 @@ def test_wall_anchoring_energy_of_a_uniform_director(precision, kind):
             sim = s.mask() & 1
             assert np.abs(s.force()[:, sim.astype(bool)]).max() < (1e-12 if tol == 1e-12 else 1e-6)
     s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(lqmin.LQ_FP64, 1e-12),
+                                           (lqmin.LQ_FP32_BULK_FP64_RED, 2e-6)])
+def test_fire_from_rest_on_a_harmonic_bulk_is_velocity_verlet(precision, tol):
+    """With B = C = 0 the bulk density A/2 tr Q^2 is harmonic in q:
+    -dF/dq_xx = -A (2 q_xx + q_yy), -dF/dq_xz = -2A q_xz, so q_xx = q_yy is a
+    mode with w^2 = 3A and q_xz one with w^2 = 2A.  FIRE with alpha0 = 0 and
+    f_inc = 1 is plain velocity Verlet while P > 0, and velocity Verlet from
+    rest follows q_n = q_0 cos(n theta), cos theta = 1 - w^2 dt^2 / 2
+    (the Stormer recurrence), for every mode and every site."""
+    shape = (6, 4, 4)
+    N = shape[0] * shape[1] * shape[2]
+    Ah, dt = 1.0, 0.05
+    s = lqmin.Solver(shape, Ah, 0.0, 0.0, 2.32, 0.5, 0.3, precision=precision, S0=0.5)
+    q0 = np.zeros((5, N))
+    q0[0] = q0[3] = 0.125
+    q0[2] = 0.25
+    s.set_q(q0)
+    p = lqmin.fire_params(dt0=dt, dt_max=dt, alpha0=0.0, f_alpha=0.99, f_inc=1.0, f_dec=0.5,
+                          n_min=5, max_iter=10 ** 6, force_tol=1e-14)
+    n = 10
+    r = s.step(p, n)
+    assert r.iterations == n and r.dt == dt and r.npos == n
+    q = s.get_q()
+    for c, w2 in ((0, 3 * Ah), (3, 3 * Ah), (2, 2 * Ah)):
+        theta = math.acos(1 - w2 * dt * dt / 2)
+        want = q0[c] * math.cos(n * theta)
+        assert np.abs(q[c] - want).max() <= tol * abs(want[0])
+    assert np.abs(q[[1, 4]]).max() == 0.0
+    s.close()
