@@ -153,3 +153,34 @@ def test_fire_from_rest_on_a_harmonic_bulk_is_velocity_verlet(precision, tol):
         assert np.abs(q[c] - want).max() <= tol * abs(want[0])
     assert np.abs(q[[1, 4]]).max() == 0.0
     s.close()
+
+
+@pytest.mark.parametrize("method", [lqmin.LQ_MIN_GD, lqmin.LQ_MIN_NESTEROV])
+def test_descent_on_a_harmonic_bulk_follows_its_recurrence(method):
+    """The same harmonic bulk, modes w^2 = 3A (q_xx = q_yy) and 2A (q_xz):
+    gradient descent with step eta gives a_n = (1 - eta w^2)^n a_0; Nesterov
+    with momentum mu gives a_{k+1} = (1 - eta w^2) b_k, b_k = a_k + mu (a_k -
+    a_{k-1}), a_{-1} = a_0, and the state it holds is the evaluation point
+    b_n."""
+    shape = (6, 4, 4)
+    N = shape[0] * shape[1] * shape[2]
+    Ah, eta, mu, n = 1.0, 0.05, 0.7, 25
+    s = lqmin.Solver(shape, Ah, 0.0, 0.0, 2.32, 0.5, 0.3, S0=0.5)
+    q0 = np.zeros((5, N))
+    q0[0] = q0[3] = 0.125
+    q0[2] = 0.25
+    s.set_q(q0)
+    m = mu if method == lqmin.LQ_MIN_NESTEROV else 0.0
+    r = s.step(lqmin.descent_params(method, eta, momentum=m, max_iter=10 ** 6, force_tol=1e-14), n)
+    assert r.iterations == n
+    q = s.get_q()
+    for c, w2 in ((0, 3 * Ah), (3, 3 * Ah), (2, 2 * Ah)):
+        a_prev = a = 1.0
+        for _ in range(n):
+            b = a + m * (a - a_prev)
+            a_prev, a = a, (1 - eta * w2) * b
+        held = a + m * (a - a_prev)
+        want = q0[c] * held
+        assert np.abs(q[c] - want).max() <= 1e-12 * abs(q0[c, 0])
+    assert np.abs(q[[1, 4]]).max() == 0.0
+    s.close()
