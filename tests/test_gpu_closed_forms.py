@@ -184,3 +184,35 @@ def test_descent_on_a_harmonic_bulk_follows_its_recurrence(method):
         assert np.abs(q[c] - want).max() <= 1e-12 * abs(q0[c, 0])
     assert np.abs(q[[1, 4]]).max() == 0.0
     s.close()
+
+
+def test_batched_fire_from_rest_on_harmonic_bulks_is_velocity_verlet():
+    """Three lattices of different sizes and stiffness in one batch (one
+    persistent launch per iteration): each follows its own velocity Verlet
+    closed form, as above."""
+    dt, n = 0.05, 12
+    cases = [((6, 4, 4), 1.0), ((40, 9, 7), 0.6), ((33, 20, 5), 1.4)]
+    solvers, q0s = [], []
+    for shape, Ah in cases:
+        N = shape[0] * shape[1] * shape[2]
+        s = lqmin.Solver(shape, Ah, 0.0, 0.0, 2.32, 0.5, 0.3, S0=0.5)
+        q0 = np.zeros((5, N))
+        q0[0] = q0[3] = 0.125
+        q0[2] = 0.25
+        s.set_q(q0)
+        solvers.append(s)
+        q0s.append(q0)
+    batch = lqmin.Batch(solvers)
+    p = lqmin.fire_params(dt0=dt, dt_max=dt, alpha0=0.0, f_alpha=0.99, f_inc=1.0, f_dec=0.5,
+                          n_min=5, max_iter=10 ** 6, force_tol=1e-14)
+    res = batch.step(p, n)
+    for (shape, Ah), s, q0, r in zip(cases, solvers, q0s, res):
+        assert r.iterations == n
+        q = s.get_q()
+        for c, w2 in ((0, 3 * Ah), (3, 3 * Ah), (2, 2 * Ah)):
+            theta = math.acos(1 - w2 * dt * dt / 2)
+            want = q0[c] * math.cos(n * theta)
+            assert np.abs(q[c] - want).max() <= 1e-12 * abs(want[0])
+    batch.close()
+    for s in solvers:
+        s.close()
