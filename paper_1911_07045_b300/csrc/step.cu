@@ -1322,8 +1322,12 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
         }
         const I i = own ? LQ_CHK_IDX((I)z * NXY + (I)gy * (I)L.nx + (I)gx, N)
                         : (I)z * NXY + (I)gy * (I)L.nx + (I)gx;
+        // the own site's v, F for the kick: FP32 form read here, ahead of the
+        // barrier, to hide the load latency; the FP64 form, bound by its
+        // arithmetic pipe, reads them at the kick and keeps the registers
+        // free through the force (fewer registers, 2% faster)
         T vold[5], fold[5];
-        if constexpr (!WCACHE) {
+        if constexpr (!WCACHE && sizeof(T) == 4) {
             if (own && !fo_mode) {
 #pragma unroll
                 for (int c = 0; c < 5; ++c) { vold[c] = __ldg(vin + c * N + i); fold[c] = __ldg(Fin + c * N + i); }
@@ -1578,6 +1582,13 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                     for (int c = 0; c < 5; ++c) w[c] = S.w(z % 3, c);
                     Site5<T>::kick_w(w, Fn, hdt, vn, pv, ff, vv);
                 } else {
+                    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+                        for (int c = 0; c < 5; ++c) {
+                            vold[c] = __ldg(vin + c * N + i);
+                            fold[c] = __ldg(Fin + c * N + i);
+                        }
+                    }
                     Site5<T>::kick(vold, fold, Fn, cv, cFh, hdt, vn, pv, ff, vv);
                 }
 #pragma unroll
