@@ -416,7 +416,8 @@ lq_status lq_server_submit(lq_server *sv, const lq_request *rq, uint64_t *ticket
    converged, LQ_ENOTCONVERGED, LQ_EDIVERGED, LQ_ETIMEOUT, or the error that
    stopped its set-up), *out with out->seconds = time from submission to
    completion and the final energy, S_out (N doubles, may be NULL) the order
-   field if requested.  A finished ticket can be read once. */
+   field if requested.  A finished ticket can be read once: LQ_EINVAL for a
+   ticket the server never issued or has already handed back. */
 lq_status lq_server_poll(lq_server *sv, uint64_t ticket, lq_result *out, double *S_out);
 /* As lq_server_poll, waiting up to timeout_s (<= 0: no limit). */
 lq_status lq_server_wait(lq_server *sv, uint64_t ticket, double timeout_s, lq_result *out,

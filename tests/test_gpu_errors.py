@@ -135,3 +135,20 @@ def test_batch_rejects_mixed_members_and_bad_tiling():
     batch.close()
     for s in (a, b, f32, one):
         s.close()
+
+
+def test_server_tickets_are_read_once_and_unknown_ones_refused():
+    sv = lqmin.Server(1 << 30, max_active=4)
+    cfg = dict(shape=(16, 16, 12), L1=2.32, objects=[])
+    p = lqmin.fire_params(**dict(synth.FIRE_DEFAULTS, max_iter=200000, force_tol=1e-5))
+    t = sv.submit(cfg, p, seed=3)
+    r = lqmin.Result()
+    lib = sv.lib
+    assert lib.lq_server_wait(sv.h, C.c_uint64(t), 300.0, C.byref(r), None) == lqmin.LQ_OK
+    assert r.fire_status == lqmin.FIRE_CONVERGED
+    # handed back once: a second read, and a ticket never issued, are refused
+    assert lib.lq_server_poll(sv.h, C.c_uint64(t), C.byref(r), None) == lqmin.LQ_EINVAL
+    assert lib.lq_server_wait(sv.h, C.c_uint64(t), 1.0, C.byref(r), None) == lqmin.LQ_EINVAL
+    assert lib.lq_server_poll(sv.h, C.c_uint64(t + 1000), C.byref(r), None) == lqmin.LQ_EINVAL
+    assert lib.lq_server_poll(None, C.c_uint64(t), C.byref(r), None) == lqmin.LQ_EINVAL
+    sv.close()
