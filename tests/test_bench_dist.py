@@ -57,3 +57,22 @@ def test_single_rank_is_identity():
     assert d.world == int(os.environ.get("WORLD_SIZE", "1"))
     if d.world == 1:
         assert bench.aggregate(d, 10.0, 2.0) == (5.0, 2.0)
+
+
+def test_reference_arm_line_keeps_the_contract():
+    """The reference arm (the CPU oracle) on rank 0: one JSON-ready line with
+    the GPU arm's metric, unit and workload name, its cpu_baseline and a
+    zero-copy e2e, from a short run."""
+    import argparse
+    import bench
+    d = bench.Dist(backend=None)
+    args = argparse.Namespace(steps=1, warmup=1, size=512)
+    line = bench.main_reference(args, d)
+    assert line["impl"] == "reference"
+    assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["higher_is_better"] is True and line["value"] > 0
+    assert line["config"]["workload"] == bench.workload_name(512)
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT,
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
