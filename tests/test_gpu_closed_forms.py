@@ -216,3 +216,49 @@ def test_batched_fire_from_rest_on_harmonic_bulks_is_velocity_verlet():
     batch.close()
     for s in solvers:
         s.close()
+
+
+def test_l2_and_l3_agree_on_a_periodic_lattice_without_objects():
+    """On a fully periodic lattice without objects the averaged L2 and L3
+    terms are equal for every Q (centred differences commute and sum by
+    parts), so the GPU's energies and forces with (L2, L3) = (1, 0) and
+    (0, 1) agree, at a size the oracle is never run on."""
+    shape = (96, 80, 64)
+    q = synth.random_uniaxial_q(shape, 17)
+    out = []
+    for L2, L3 in ((1.0, 0.0), (0.0, 1.0)):
+        s = lqmin.Solver(shape, A, B, C, 0.0, L2, L3, n_constants=3)
+        s.set_q(q)
+        out.append((s.energy()[1][1], s.force()))
+        s.close()
+    (e2, F2), (e3, F3) = out
+    assert abs(e2 - e3) <= 1e-11 * abs(e2)
+    assert np.abs(F2 - F3).max() <= 1e-10 * np.abs(F2).max()
+
+
+def test_swapping_x_and_y_maps_energy_and_force():
+    """The mirror x <-> y of lattice, objects and Q (Q'_xx = Q_yy, Q'_xy =
+    Q_xy, Q'_xz = Q_yz, ...) leaves the bulk, L1, L2, L3 and anchoring
+    energy unchanged and maps the force the same way."""
+    n = 40
+    shape = (n, n, 24)
+    c = (17.0, 17.0, 12.0)     # on the diagonal: the sphere is its own mirror image
+    objs = [dict(type="wall", axis=2, plane=0, anchor=(lqmin.FG_PLANAR, 1.0, (0, 0, 1))),
+            dict(type="sphere", c=c, R=6.0, anchor=(lqmin.ND_HOMEOTROPIC, 5.3, (0, 0, 1)))]
+    q = synth.random_uniaxial_q(shape, 18)
+    qs = q.reshape(5, shape[2], n, n)            # [c][z][y][x]
+    perm = [3, 1, 4, 0, 2]                       # (xx, xy, xz, yy, yz) <- (yy, xy, yz, xx, xz)
+    qm = qs[perm].transpose(0, 1, 3, 2).reshape(5, -1)
+    res = []
+    for state in (q, qm):
+        s = lqmin.Solver(shape, A, B, C, 2.32, 0.5, 0.3)
+        s.add_objects(objs)
+        s.set_q(state)
+        res.append((s.energy(), s.force()))
+        s.close()
+    (E, parts), F = res[0]
+    (Em, partsm), Fm = res[1]
+    assert abs(E - Em) <= 1e-12 * abs(E)
+    assert np.allclose(parts, partsm, rtol=1e-12, atol=1e-12 * abs(E))
+    Fmap = F.reshape(5, shape[2], n, n)[perm].transpose(0, 1, 3, 2).reshape(5, -1)
+    assert np.abs(Fm - Fmap).max() <= 1e-10 * np.abs(F).max()
