@@ -262,3 +262,30 @@ def test_swapping_x_and_y_maps_energy_and_force():
     assert np.allclose(parts, partsm, rtol=1e-12, atol=1e-12 * abs(E))
     Fmap = F.reshape(5, shape[2], n, n)[perm].transpose(0, 1, 3, 2).reshape(5, -1)
     assert np.abs(Fm - Fmap).max() <= 1e-10 * np.abs(F).max()
+
+
+@pytest.mark.parametrize("precision,tol", [(lqmin.LQ_FP64, 1e-10),
+                                           (lqmin.LQ_FP32_BULK_FP64_RED, 1e-5)])
+def test_chiral_term_is_odd_under_the_mirror(precision, tol):
+    """The chiral density eps_lik Q_lj dQ_ij/dx_k changes sign under a
+    reflection: with only L4 (no bulk, no other elastic term) the mirror
+    x <-> y of Q negates the energy and the mapped force."""
+    n = 32
+    shape = (n, n, 20)
+    q = synth.random_uniaxial_q(shape, 19)
+    if precision == lqmin.LQ_FP32_BULK_FP64_RED:
+        q = np.round(q * 2.0 ** 28) / 2.0 ** 28
+    perm = [3, 1, 4, 0, 2]
+    qm = q.reshape(5, shape[2], n, n)[perm].transpose(0, 1, 3, 2).reshape(5, -1)
+    res = []
+    for state in (q, qm):
+        s = lqmin.Solver(shape, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, precision=precision, L4=0.7,
+                         n_constants=3, S0=0.5)
+        s.set_q(state)
+        res.append((s.energy()[1][1], s.force()))
+        s.close()
+    (e, F), (em, Fm) = res
+    assert abs(e) > 1.0
+    assert abs(e + em) <= tol * abs(e)
+    Fmap = F.reshape(5, shape[2], n, n)[perm].transpose(0, 1, 3, 2).reshape(5, -1)
+    assert np.abs(Fm + Fmap).max() <= tol * np.abs(F).max()
