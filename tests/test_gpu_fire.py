@@ -213,3 +213,23 @@ def test_fp32_form_steps_in_every_kernel_form(oracle_mod, name):
     assert rel(s.get_q()[:, sim], qo[:, sim]) < 2e-7
     assert rel(s.get_force()[:, sim], Fo[:, sim]) < 2e-6
     assert rel(s.get_velocity()[:, sim], vo[:, sim]) < 2e-6
+
+
+@pytest.mark.parametrize("zchunk", [1, 2, 3, 5])
+@pytest.mark.parametrize("name", ["one_constant_32wide", "one_constant_64wide", "chiral_field"])
+def test_fp32_kept_kick_part_with_short_z_chunks(oracle_mod, name, zchunk):
+    """Chunks of one to five planes exercise the first and last planes of
+    the three-plane store of the kick's old-state part; five FIRE steps
+    still match the oracle to float accuracy."""
+    c = FP32_KERNELS[name]
+    s, o = make_pair(oracle_mod, c["shape"], c["L"], c["objects"], precision=1, zchunk=zchunk,
+                     **c["extra"])
+    q0 = np.round(synth.random_uniaxial_q(c["shape"], 13) * 2.0 ** 28) / 2.0 ** 28
+    s.set_q(q0)
+    params = dict(FP, max_iter=10 ** 6, force_tol=1e-12)
+    r = s.step(lqmin.fire_params(**params), 5)
+    qo, vo, Fo, st = o.fire(q0, params, 5)
+    sim = o.simulated()
+    assert r.iterations == st["iter"] == 5
+    assert rel(s.get_q()[:, sim], qo[:, sim]) < 2e-7
+    assert rel(s.get_velocity()[:, sim], vo[:, sim]) < 2e-6
