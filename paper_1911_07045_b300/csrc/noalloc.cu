@@ -18,6 +18,7 @@
 
 #include "lqmin.h"
 #include "lq_common.cuh"
+#include "solver_internal.h"
 
 namespace lq {
 namespace {
@@ -78,14 +79,19 @@ k_plane_energy(int nx, int ny, int nz, int px, int py, int pz, double A, double 
         eb -= (K.v[0] * a + K.v[3] * d + K.v[5] * f + 2.0 * (K.v[1] * b + K.v[2] * c3 + K.v[4] * e)) / 3.0;
         double mk[3][5], sqF[3], squ[3];
         for (int k = 0; k < 3; ++k) {
-            int fo = (m & m_fwd(k)) ? 1 : 0, bo = (m & m_bwd(k)) ? 1 : 0;
+            // a mask bit that names a neighbour outside a non-periodic edge
+            // (a mask built for other periodic flags) counts as absent, so
+            // that no site outside the lattice is ever read
+            const long long jn[2] = {step_site(nx, ny, nz, per, x, y, z, k, 1),
+                                     step_site(nx, ny, nz, per, x, y, z, k, -1)};
+            int fo = ((m & m_fwd(k)) && jn[0] >= 0) ? 1 : 0, bo = ((m & m_bwd(k)) && jn[1] >= 0) ? 1 : 0;
             for (int c = 0; c < 5; ++c) mk[k][c] = 0.0;
             sqF[k] = squ[k] = 0.0;
             if (fo + bo == 0) continue;
             double w = 1.0 / (fo + bo);
             for (int s = 0; s < 2; ++s) {
                 if ((s == 0 && !fo) || (s == 1 && !bo)) continue;
-                long long j = step_site(nx, ny, nz, per, x, y, z, k, s == 0 ? 1 : -1);
+                const long long j = jn[s];
                 double dd[5];
                 for (int c = 0; c < 5; ++c) dd[c] = s == 0 ? q[c * N + j] - q0[c] : q0[c] - q[c * N + j];
                 for (int c = 0; c < 5; ++c) mk[k][c] += w * dd[c];
@@ -210,6 +216,10 @@ extern "C" lq_status lq_energy_noalloc(const lq_lattice *lat, const lq_material 
     if (!lat || !mat || !q_dev || !mask_dev || !parts_dev) return LQ_EINVAL;
     if (lat->nx <= 0 || lat->ny <= 0 || lat->nz <= 0) return LQ_EINVAL;
     if (lat->nz > NOALLOC_MAX_NZ) return LQ_EINVAL;
+    // the same lattice and material checks as lq_create (host arithmetic only)
+    if (lat->spacing != 1.0) return LQ_EINVAL;
+    double S0 = 0.0;
+    if (detail::validate_material(mat, &S0)) return LQ_EINVAL;
     lq_status st;
     double *scratch = scratch_for_current_device(&st);
     if (!scratch) return st;

@@ -52,4 +52,47 @@ def test_energy_noalloc_matches_lq_energy():
     st = lib.lq_energy_noalloc(C.byref(big), C.byref(mat), C.c_void_p(qd.data_ptr()),
                                C.c_void_p(mask.data_ptr()), C.c_void_p(out.data_ptr()), None)
     assert st == lqmin.LQ_EINVAL
+    # lattice and material are checked as lq_create checks them
+    bad_spacing = lqmin.Lattice(*shape, 0.5, (C.c_int * 3)(*per))
+    one_c_with_l2 = lqmin.Material(synth.A_5CB, synth.B_5CB, synth.C_5CB, L1, L2, 0.0, 0.0, 0.0, 1, 0.0)
+    two_consts = lqmin.Material(synth.A_5CB, synth.B_5CB, synth.C_5CB, L1, L2, L3, 0.0, 0.0, 2, 0.0)
+    for la, ma in ((bad_spacing, mat), (lat, one_c_with_l2), (lat, two_consts)):
+        st = lib.lq_energy_noalloc(C.byref(la), C.byref(ma), C.c_void_p(qd.data_ptr()),
+                                   C.c_void_p(mask.data_ptr()), C.c_void_p(out.data_ptr()), None)
+        assert st == lqmin.LQ_EINVAL
     s.close()
+
+
+def test_energy_noalloc_mask_for_other_periodic_flags():
+    """A mask built on a fully periodic lattice, passed with a lattice that
+    is open on every axis: its bits that name neighbours across the open
+    edges count as absent neighbours, so the result is finite and equals
+    lq_energy's bulk and distortion parts of the open lattice itself."""
+    need_gpu()
+    import torch
+    shape = (24, 17, 13)
+    objs = [dict(type="sphere", c=(12.0, 8.0, 6.0), R=3.5, anchor=HOM())]
+    L1, L2, L3 = 2.32, 0.5, 0.3
+    lib = lqmin.load()
+    periodic = lqmin.Solver(shape, synth.A_5CB, synth.B_5CB, synth.C_5CB, L1, L2, L3, periodic=(1, 1, 1))
+    periodic.add_objects(objs)
+    open_ = lqmin.Solver(shape, synth.A_5CB, synth.B_5CB, synth.C_5CB, L1, L2, L3, periodic=(0, 0, 0))
+    open_.add_objects(objs)
+    q = rand_q(open_.N, 11)
+    open_.set_q(q)
+    _, want = open_.energy()
+    lat = lqmin.Lattice(*shape, 1.0, (C.c_int * 3)(0, 0, 0))
+    mat = lqmin.Material(synth.A_5CB, synth.B_5CB, synth.C_5CB, L1, L2, L3, 0.0, 0.0, 3, 0.0)
+    mask = torch.from_numpy(periodic.mask()).cuda()
+    qd = torch.from_numpy(q).cuda()
+    out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    st = lib.lq_energy_noalloc(C.byref(lat), C.byref(mat), C.c_void_p(qd.data_ptr()),
+                               C.c_void_p(mask.data_ptr()), C.c_void_p(out.data_ptr()), None)
+    assert st == lqmin.LQ_OK
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert abs(got[0] - want[0]) <= 1e-12 * abs(want[0])
+    assert abs(got[1] - want[1]) <= 1e-12 * abs(want[1])
+    periodic.close()
+    open_.close()
