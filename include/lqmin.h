@@ -347,13 +347,27 @@ void lq_batch_destroy(lq_batch *b);
 const char *lq_batch_last_error(const lq_batch *b);
 /* Tiling of the persistent kernel: tile 32 x tile_y (4 or 8) and z chunk
    (0 = each lattice's own z chunk, as lq_set_zchunk left it); LQ_EINVAL for
-   other tile heights or a negative z chunk, the tiling unchanged. */
+   other tile heights or a negative z chunk, the tiling unchanged.
+   lq_batch_get_tiling reports the height and z chunk of the current tiling,
+   whatever its width. */
 lq_status lq_batch_set_tiling(lq_batch *b, int tile_y, int zchunk);
 lq_status lq_batch_get_tiling(const lq_batch *b, int *tile_y, int *zchunk);
-/* Autotuner: times every tile_y in {4, 8} and z chunk in {8, ..., 128} over
-   `launches` launches on shadow copies of the FIRE states (the lattices'
-   states do not advance) and keeps the fastest; *best_ms may be NULL.
-   Starts FIRE on lattices that have not started. */
+/* The same with the tile width: tile_x 32, or 64 when every lattice is a
+   one-constant FP32-form lattice (the wide tiles of the single-lattice
+   kernel: half the ring columns per site); LQ_EINVAL otherwise, the tiling
+   unchanged.  A lattice advances bit-for-bit as it does alone when its own
+   step runs the same tile (alone, 64-wide tiles serve one-constant FP32-form
+   lattices at least 256 sites wide) and z chunk.  Any pointer of the getter
+   may be NULL.  A change of members that brings a three-constant lattice
+   into a batch with 64-wide tiles turns them back to 32. */
+lq_status lq_batch_set_tile(lq_batch *b, int tile_x, int tile_y, int zchunk);
+lq_status lq_batch_get_tile(const lq_batch *b, int *tile_x, int *tile_y, int *zchunk);
+/* Autotuner: times every tile width the lattices allow (32, and 64 for
+   one-constant FP32-form batches), tile_y in {4, 8} and z chunk in
+   {8, ..., 128}, each over `launches` launches (CUDA events) on shadow copies
+   of the FIRE states (the lattices' states do not advance), and keeps the
+   fastest; *best_ms may be NULL.  Starts FIRE on lattices that have not
+   started. */
 lq_status lq_batch_autotune(lq_batch *b, const lq_fire_params *p, int launches, double *best_ms);
 /* n more FIRE iterations of every lattice (converged ones stay put); out
    holds one lq_result per solver, or NULL. */
@@ -397,6 +411,9 @@ typedef struct {
     int64_t queued, active, completed;
     size_t bytes_in_use, budget;    /* estimated device bytes of the active solves */
     double site_updates;            /* sum over finished solves of N x iterations */
+    double site_updates_issued;     /* N x k over every active solve of every round of
+                                       k launches so far (a solve that converges inside a
+                                       round is counted to the round's end) */
 } lq_server_stats;
 
 /* A server on the current device: a worker thread admits queued requests
@@ -431,12 +448,19 @@ lq_status lq_server_stats_get(lq_server *sv, lq_server_stats *out);
    up front by its own allocator or budget, or a latency-bound loop that
    cannot take the device-wide synchronisation of cudaMalloc/cudaFree.  It
    allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
-   Computes the bulk (Eq. fphase) and averaged-difference distortion
-   (Eq. fdistortionFull) energy of a caller-owned device Q field, summed in
-   FP64: lattice and material as for lq_create; q_dev = 5*N doubles (layout
-   above), mask_dev = N mask bytes in the lq_get_mask layout, both on the
-   device; parts_dev = 3 device doubles receiving (bulk, distortion, 0) --
-   anchoring is not included.  Work runs on cuda_stream (NULL = legacy
+   Computes two parts of the energy of a caller-owned device Q field, summed
+   in FP64: the Landau bulk part (with the external-field term) and the
+   elastic part from the averaged one-sided differences between
+   neighbouring sites (with the chiral and cubic terms when L4, L6 are set);
+   the surface anchoring part is not included.  Lattice and material are
+   checked as lq_create checks them (spacing 1, n_constants 1 or 3, a
+   one-constant material with L2 = L3 = L4 = L6 = 0, a nematic minimum):
+   LQ_EINVAL otherwise.  q_dev = 5*N doubles (layout above), mask_dev = N
+   mask bytes in the lq_get_mask layout, both on the device; a mask bit that
+   names a neighbour beyond a non-periodic edge of this lattice (a mask
+   built for other periodic flags) is treated as an absent neighbour, so
+   nothing outside the arrays is read.  parts_dev = 3 device doubles
+   receiving (bulk, elastic, 0).  Work runs on cuda_stream (NULL = legacy
    default stream) and is not synchronised.  Scratch is a static device
    array of 3 doubles per z plane, for at most 4096 planes (96 KB held on
    every GPU that loads the library until exit): nz > 4096 returns
@@ -480,6 +504,20 @@ lq_status lq_set_zchunk(lq_solver *s, int zchunk);
 lq_status lq_set_index_width(lq_solver *s, int bits);
 /* Bytes of device memory held by the solver. */
 size_t lq_device_bytes(const lq_solver *s);
+
+/* ---- measurement ------------------------------------------------------------------ */
+
+/* Measured FP64 fused multiply-add rate of the current device, the ceiling
+   of the FP64 form of the step (section III.B's force and Algorithm 1's
+   update in double precision), which is bound by the FP64 pipe here rather
+   than by memory.  Every resident thread runs 8 independent chains of iters
+   dependent fused multiply-adds; one untimed launch first, then one launch
+   timed with CUDA events on a stream of its own.  *fma_per_s receives the
+   thread-level fused multiply-adds per second (each is one FP64 operation
+   in the FP64 form's operation count; twice as many flops).  The call
+   allocates and frees a small output buffer.  LQ_EINVAL for iters <= 0 or a
+   null pointer, LQ_ENOMEM / LQ_ECUDA on a CUDA failure. */
+lq_status lq_fp64_fma_rate(int64_t iters, double *fma_per_s);
 
 #ifdef __cplusplus
 }

@@ -26,7 +26,7 @@ struct lq_batch {
     std::vector<lq_solver *> solvers;
     int device = 0, fp32 = 0, three = 0, nsm = 148;
     cudaStream_t stream = nullptr;
-    int ty = 0, zchunk = 0;           // tiling; zchunk 0 = each lattice's own
+    int tx = 32, ty = 0, zchunk = 0;  // tiling; zchunk 0 = each lattice's own
     int idx32 = 1;                    // every lattice indexed in 32 bits
     int form = 0;                     // kernel form: 0 one-, 1 three-constant, 2 with L4 / L6
     bool tables_ok = false;
@@ -72,9 +72,8 @@ void drop_batch_graph(lq_batch *b) {
     b->graph_k = 0;
 }
 
-// work items and reduction slots for tile 32 x ty and z chunk zc
-lq_status build_items(lq_batch *b, int ty, int zc_all, bool shadow) {
-    const int tx = 32;
+// work items and reduction slots for tile tx x ty and z chunk zc
+lq_status build_items(lq_batch *b, int tx, int ty, int zc_all, bool shadow) {
     std::vector<WorkItem> items;
     std::vector<long long> base(b->solvers.size());
     std::vector<int> zcs(b->solvers.size());
@@ -137,21 +136,22 @@ lq_status build_items(lq_batch *b, int ty, int zc_all, bool shadow) {
     return LQ_OK;
 }
 
-int persistent_grid(lq_batch *b, int ty) {
-    int per = fire_batch_blocks_per_sm(b->fp32, b->form, ty, b->idx32);
+int persistent_grid(lq_batch *b, int tx, int ty) {
+    int per = fire_batch_blocks_per_sm(b->fp32, b->form, tx, ty, b->idx32);
     return std::max(1, per) * b->nsm;
 }
 
-lq_status set_tiling(lq_batch *b, int ty, int zc) {
-    if (b->tables_ok && b->ty == ty && b->zchunk == zc) return LQ_OK;
+lq_status set_tiling(lq_batch *b, int tx, int ty, int zc) {
+    if (b->tables_ok && b->tx == tx && b->ty == ty && b->zchunk == zc) return LQ_OK;
     drop_batch_graph(b);
     b->tables_ok = false;
     if (!b->solvers.empty()) {
-        lq_status r = build_items(b, ty, zc, false);
+        lq_status r = build_items(b, tx, ty, zc, false);
         if (r != LQ_OK) return r;
     } else {
         b->nitems = 0;
     }
+    b->tx = tx;
     b->ty = ty;
     b->zchunk = zc;
     b->tables_ok = true;
@@ -163,12 +163,13 @@ lq_status ensure_graph(lq_batch *b) {
     int kk = (int)std::max(1LL, std::min(64LL, k));
     if (b->gexec && b->graph_k == kk) return LQ_OK;
     drop_batch_graph(b);
-    int grid = persistent_grid(b, b->ty);
+    int grid = persistent_grid(b, b->tx, b->ty);
     cudaGraph_t g = nullptr;
     BK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int t = 0; t < kk && e == cudaSuccess; ++t)
-        e = launch_fire_batch(b->fp32, b->form, b->ty, b->idx32, b->args, b->items, b->nitems, grid, b->stream);
+        e = launch_fire_batch(b->fp32, b->form, b->tx, b->ty, b->idx32, b->args, b->items, b->nitems, grid,
+                              b->stream);
     if (e == cudaSuccess) e = batch_running(b->states, (int)b->solvers.size(), b->running, b->stream);
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -236,10 +237,12 @@ lq_status batch_new(int device, int fp32, int three, lq_batch **out) {
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) b->nsm = prop.multiProcessorCount;
     cudaError_t e = cudaSuccess;
-    for (int ty : {4, 8})
-        for (int i32 : {0, 1})
-            for (int form : {three ? 1 : 0, three ? 2 : 0})
-                if (e == cudaSuccess) e = prepare_fire_batch(fp32, form, ty, i32);
+    for (int tx : {32, 64})
+        for (int ty : {4, 8})
+            for (int i32 : {0, 1})
+                for (int form : {three ? 1 : 0, three ? 2 : 0})
+                    if (e == cudaSuccess && batch_tile_ok(fp32, form, tx))
+                        e = prepare_fire_batch(fp32, form, tx, ty, i32);
     if (e == cudaSuccess) e = dev_malloc(&b->running, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMallocHost(&b->running_host, sizeof(unsigned int));
     if (e != cudaSuccess) {
@@ -248,7 +251,8 @@ lq_status batch_new(int device, int fp32, int three, lq_batch **out) {
     }
     int tx, ty;
     step_tile(fp32, three, 0, &tx, &ty);   // the narrow tiles of batches
-    b->ty = ty;          // default tiling: the solvers' own (z chunk 0 = each lattice's)
+    b->tx = 32;          // default tiling: 32-wide tiles of the solvers' height,
+    b->ty = ty;          // z chunk 0 = each lattice's own
     b->zchunk = 0;
     *out = b;
     return LQ_OK;
@@ -291,9 +295,11 @@ lq_status batch_set_members(lq_batch *b, lq_solver *const *solvers, int n) {
         b->sites += b->solvers[l]->L.N;
     }
     if (n > 0) BK(cudaMemcpyAsync(b->states, st.data(), sizeof(FireDev *) * n, cudaMemcpyHostToDevice, b->stream));
-    int ty = b->ty, zc = b->zchunk;
+    // 64-wide tiles only where the form has them (a three-constant member
+    // turns them back to 32)
+    int tx = batch_tile_ok(b->fp32, b->form, b->tx) ? b->tx : 32, ty = b->ty, zc = b->zchunk;
     b->ty = 0;
-    return set_tiling(b, ty, zc);
+    return set_tiling(b, tx, ty, zc);
 }
 
 int batch_members(const lq_batch *b) { return b ? (int)b->solvers.size() : 0; }
@@ -305,9 +311,10 @@ lq_status batch_round(lq_batch *b, int k, unsigned int *running) {
     if (b->solvers.empty()) { *running = 0; return LQ_OK; }
     // stale tables could name lattices that are gone: never launch on them
     if (!b->tables_ok) return bfail(b, LQ_EINVAL, "batch tables are not built");
-    int grid = persistent_grid(b, b->ty);
+    int grid = persistent_grid(b, b->tx, b->ty);
     for (int t = 0; t < k; ++t)
-        BK(launch_fire_batch(b->fp32, b->form, b->ty, b->idx32, b->args, b->items, b->nitems, grid, b->stream));
+        BK(launch_fire_batch(b->fp32, b->form, b->tx, b->ty, b->idx32, b->args, b->items, b->nitems, grid,
+                             b->stream));
     BK(batch_running(b->states, (int)b->solvers.size(), b->running, b->stream));
     BK(cudaMemcpyAsync(b->running_host, b->running, sizeof(unsigned int), cudaMemcpyDeviceToHost, b->stream));
     BK(cudaStreamSynchronize(b->stream));
@@ -352,15 +359,26 @@ void lq_batch_destroy(lq_batch *b) {
 const char *lq_batch_last_error(const lq_batch *b) { return b ? b->err.c_str() : "null batch"; }
 
 lq_status lq_batch_set_tiling(lq_batch *b, int tile_y, int zchunk) {
-    if (!b) return LQ_EINVAL;
-    if ((tile_y != 4 && tile_y != 8) || zchunk < 0)
-        return bfail(b, LQ_EINVAL, "tile height must be 4 or 8 and the z chunk >= 0");
-    cudaSetDevice(b->device);
-    return set_tiling(b, tile_y, zchunk);
+    return lq_batch_set_tile(b, 32, tile_y, zchunk);
 }
 
 lq_status lq_batch_get_tiling(const lq_batch *b, int *tile_y, int *zchunk) {
+    return lq_batch_get_tile(b, nullptr, tile_y, zchunk);
+}
+
+lq_status lq_batch_set_tile(lq_batch *b, int tile_x, int tile_y, int zchunk) {
     if (!b) return LQ_EINVAL;
+    if ((tile_y != 4 && tile_y != 8) || zchunk < 0)
+        return bfail(b, LQ_EINVAL, "tile height must be 4 or 8 and the z chunk >= 0");
+    if (!batch_tile_ok(b->fp32, b->form, tile_x))
+        return bfail(b, LQ_EINVAL, "tile width must be 32, or 64 for one-constant FP32-form lattices");
+    cudaSetDevice(b->device);
+    return set_tiling(b, tile_x, tile_y, zchunk);
+}
+
+lq_status lq_batch_get_tile(const lq_batch *b, int *tile_x, int *tile_y, int *zchunk) {
+    if (!b) return LQ_EINVAL;
+    if (tile_x) *tile_x = b->tx;
     if (tile_y) *tile_y = b->ty;
     if (zchunk) *zchunk = b->zchunk;
     return LQ_OK;
@@ -379,35 +397,39 @@ lq_status lq_batch_autotune(lq_batch *b, const lq_fire_params *p, int launches, 
     cudaEventCreate(&e1);
     int n = (int)b->solvers.size();
     double best = 1e300;
-    int bty = b->ty, bzc = b->zchunk;
+    int btx = b->tx, bty = b->ty, bzc = b->zchunk;
     if (b->solvers.empty()) return LQ_OK;
-    for (int ty : {4, 8}) {
-        for (int zc : {8, 16, 32, 64, 128}) {
-            if (zc > nz_max && zc != 8) continue;
-            r = build_items(b, ty, zc, true);
-            if (r != LQ_OK) break;
-            int grid = persistent_grid(b, ty);
-            // shadow FIRE states: the timed launches leave the real ones alone
-            for (int l = 0; l < n; ++l)
-                cudaMemcpyAsync(b->shadow + l, b->solvers[l]->st, sizeof(FireDev), cudaMemcpyDeviceToDevice,
-                                b->stream);
-            cudaError_t e = launch_fire_batch(b->fp32, b->form, ty, b->idx32, b->shadow_args, b->items, b->nitems,
-                                              grid, b->stream);
-            cudaEventRecord(e0, b->stream);
-            for (int t = 0; t < launches && e == cudaSuccess; ++t) {
-                for (int l = 0; l < n; ++l)   // every timed launch starts from the same state
-                    cudaMemcpyAsync(b->shadow + l, b->solvers[l]->st, sizeof(FireDev),
-                                    cudaMemcpyDeviceToDevice, b->stream);
-                e = launch_fire_batch(b->fp32, b->form, ty, b->idx32, b->shadow_args, b->items, b->nitems, grid,
-                                      b->stream);
+    for (int tx : {32, 64}) {
+        if (!batch_tile_ok(b->fp32, b->form, tx)) continue;
+        for (int ty : {4, 8}) {
+            for (int zc : {8, 16, 32, 64, 128}) {
+                if (zc > nz_max && zc != 8) continue;
+                r = build_items(b, tx, ty, zc, true);
+                if (r != LQ_OK) break;
+                int grid = persistent_grid(b, tx, ty);
+                // shadow FIRE states: the timed launches leave the real ones alone
+                for (int l = 0; l < n; ++l)
+                    cudaMemcpyAsync(b->shadow + l, b->solvers[l]->st, sizeof(FireDev), cudaMemcpyDeviceToDevice,
+                                    b->stream);
+                cudaError_t e = launch_fire_batch(b->fp32, b->form, tx, ty, b->idx32, b->shadow_args, b->items,
+                                                  b->nitems, grid, b->stream);
+                cudaEventRecord(e0, b->stream);
+                for (int t = 0; t < launches && e == cudaSuccess; ++t) {
+                    for (int l = 0; l < n; ++l)   // every timed launch starts from the same state
+                        cudaMemcpyAsync(b->shadow + l, b->solvers[l]->st, sizeof(FireDev),
+                                        cudaMemcpyDeviceToDevice, b->stream);
+                    e = launch_fire_batch(b->fp32, b->form, tx, ty, b->idx32, b->shadow_args, b->items,
+                                          b->nitems, grid, b->stream);
+                }
+                cudaEventRecord(e1, b->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) { r = bfail(b, LQ_ECUDA, "autotune launch", e); break; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                double per = ms / launches;
+                if (per < best) { best = per; btx = tx; bty = ty; bzc = zc; }
             }
-            cudaEventRecord(e1, b->stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            if (e != cudaSuccess) { r = bfail(b, LQ_ECUDA, "autotune launch", e); break; }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            double per = ms / launches;
-            if (per < best) { best = per; bty = ty; bzc = zc; }
+            if (r != LQ_OK) break;
         }
         if (r != LQ_OK) break;
     }
@@ -415,7 +437,7 @@ lq_status lq_batch_autotune(lq_batch *b, const lq_fire_params *p, int launches, 
     cudaEventDestroy(e1);
     b->tables_ok = false;   // force the rebuild of the real tables
     drop_batch_graph(b);
-    lq_status r2 = set_tiling(b, bty, bzc);
+    lq_status r2 = set_tiling(b, btx, bty, bzc);
     if (r != LQ_OK) return r;
     if (best_ms) *best_ms = best;
     return r2;
@@ -431,10 +453,11 @@ lq_status lq_batch_step(lq_batch *b, const lq_fire_params *p, int64_t n, lq_resu
     r = ensure_graph(b);
     if (r != LQ_OK) return r;
     int64_t full = n / b->graph_k, rest = n % b->graph_k;
-    int grid = persistent_grid(b, b->ty);
+    int grid = persistent_grid(b, b->tx, b->ty);
     for (int64_t t = 0; t < full; ++t) BK(cudaGraphLaunch(b->gexec, b->stream));
     for (int64_t t = 0; t < rest; ++t)
-        BK(launch_fire_batch(b->fp32, b->form, b->ty, b->idx32, b->args, b->items, b->nitems, grid, b->stream));
+        BK(launch_fire_batch(b->fp32, b->form, b->tx, b->ty, b->idx32, b->args, b->items, b->nitems, grid,
+                             b->stream));
     BK(cudaStreamSynchronize(b->stream));
     return collect(b, out, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
 }

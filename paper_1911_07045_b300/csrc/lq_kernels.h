@@ -61,9 +61,11 @@ inline cudaError_t dev_malloc(P **p, size_t bytes) {
 // the batch indexed in 32 bits)
 size_t step_args_bytes(int fp32);
 void step_args_pack(const StepLaunch &sl, void *out);   // host memory, step_args_bytes()
-cudaError_t prepare_fire_batch(int fp32, int form, int ty, int idx32);
-int fire_batch_blocks_per_sm(int fp32, int form, int ty, int idx32);
-cudaError_t launch_fire_batch(int fp32, int form, int ty, int idx32, const void *dev_args,
+// batch tiles tx x ty: tx 32 in every form, 64 for one-constant FP32 lattices
+bool batch_tile_ok(int fp32, int form, int tx);
+cudaError_t prepare_fire_batch(int fp32, int form, int tx, int ty, int idx32);
+int fire_batch_blocks_per_sm(int fp32, int form, int tx, int ty, int idx32);
+cudaError_t launch_fire_batch(int fp32, int form, int tx, int ty, int idx32, const void *dev_args,
                               const WorkItem *items, int nitems, int grid, cudaStream_t stream);
 // running[0] = number of lattices whose FIRE status is still running
 cudaError_t batch_running(FireDev *const *states, int n, unsigned int *running, cudaStream_t s);

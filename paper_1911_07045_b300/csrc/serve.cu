@@ -84,6 +84,7 @@ struct lq_server {
     uint64_t next_ticket = 1;
     int64_t n_active = 0, completed = 0;
     double site_updates = 0.0;
+    double site_updates_issued = 0.0;
     bool stop = false;
     std::thread worker;
     std::vector<Active> active;      // worker thread only
@@ -230,6 +231,10 @@ void worker_loop(lq_server *sv) {
             continue;   // changed is set: the next round rebuilds the batches
         }
         failed_rounds = 0;
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            sv->site_updates_issued += (double)sites * k;
+        }
         // retire the finished and the timed-out
         auto now = Clock::now();
         bool any_done = running_total < sv->active.size();
@@ -371,6 +376,7 @@ lq_status lq_server_stats_get(lq_server *sv, lq_server_stats *out) {
     out->bytes_in_use = sv->used;
     out->budget = sv->budget;
     out->site_updates = sv->site_updates;
+    out->site_updates_issued = sv->site_updates_issued;
     return LQ_OK;
 }
 

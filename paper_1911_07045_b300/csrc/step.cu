@@ -172,18 +172,13 @@ struct Site5<double> {
         for (int c = 0; c < 5; ++c) out[c] = Prec<double>::drift(q[c], v[c], f[c], alpha, beta, bad);
     }
     // v_new = v_mix + dt/2 (F_old + F_new) = cv v + (cF + dt/2) F_old + dt/2 F_new
-    // (cFh = cF + dt/2) and the site's P, |F|^2, |v|^2
+    // (cFh = cF + dt/2)
     __device__ static __forceinline__ void kick(const double *vold, const double *fold, const double *fn,
-                                                double cv, double cFh, double hdt, double *vn, double &pv,
-                                                double &ff, double &vv) {
-        pv = ff = vv = 0.0;
+                                                double cv, double cFh, double hdt, double *vn) {
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
             double vx = fma_rn(cFh, fold[c], mul_rn(cv, vold[c]));
             vn[c] = fma_rn(hdt, fn[c], vx);
-            pv = fma_rn(fn[c], vn[c], pv);
-            ff = fma_rn(fn[c], fn[c], ff);
-            vv = fma_rn(vn[c], vn[c], vv);
         }
     }
 };
@@ -231,45 +226,27 @@ struct Site5<float> {
         w[4] = __fmaf_rn(cFh, fold[4], __fmul_rn(cv, vold[4]));
     }
     // kick from the kept old-state part: v_new = w + dt/2 F_new
-    __device__ static __forceinline__ void kick_w(const float *w, const float *fn, float hdt, float *vn,
-                                                  float &pv, float &ff, float &vv) {
+    __device__ static __forceinline__ void kick_w(const float *w, const float *fn, float hdt, float *vn) {
         const float2 H = make_float2(hdt, hdt);
-        float2 p2 = make_float2(0.f, 0.f), f2 = p2, v2 = p2;
 #pragma unroll
         for (int c = 0; c < 4; c += 2) {
-            const float2 fnew = make_float2(fn[c], fn[c + 1]);
-            const float2 wv = __ffma2_rn(H, fnew, make_float2(w[c], w[c + 1]));
+            const float2 wv = __ffma2_rn(H, make_float2(fn[c], fn[c + 1]), make_float2(w[c], w[c + 1]));
             vn[c] = wv.x; vn[c + 1] = wv.y;
-            p2 = __ffma2_rn(fnew, wv, p2);
-            f2 = __ffma2_rn(fnew, fnew, f2);
-            v2 = __ffma2_rn(wv, wv, v2);
         }
         vn[4] = __fmaf_rn(hdt, fn[4], w[4]);
-        pv = __fmaf_rn(fn[4], vn[4], __fadd_rn(p2.x, p2.y));
-        ff = __fmaf_rn(fn[4], fn[4], __fadd_rn(f2.x, f2.y));
-        vv = __fmaf_rn(vn[4], vn[4], __fadd_rn(v2.x, v2.y));
     }
     __device__ static __forceinline__ void kick(const float *vold, const float *fold, const float *fn,
-                                                float cv, float cFh, float hdt, float *vn, float &pv,
-                                                float &ff, float &vv) {
+                                                float cv, float cFh, float hdt, float *vn) {
         const float2 CV = make_float2(cv, cv), CF = make_float2(cFh, cFh), H = make_float2(hdt, hdt);
-        float2 p2 = make_float2(0.f, 0.f), f2 = p2, v2 = p2;
 #pragma unroll
         for (int c = 0; c < 4; c += 2) {
             const float2 vo = make_float2(vold[c], vold[c + 1]), fo = make_float2(fold[c], fold[c + 1]);
-            const float2 fnew = make_float2(fn[c], fn[c + 1]);
             const float2 vx = __ffma2_rn(CF, fo, __fmul2_rn(CV, vo));
-            const float2 w = __ffma2_rn(H, fnew, vx);
+            const float2 w = __ffma2_rn(H, make_float2(fn[c], fn[c + 1]), vx);
             vn[c] = w.x; vn[c + 1] = w.y;
-            p2 = __ffma2_rn(fnew, w, p2);
-            f2 = __ffma2_rn(fnew, fnew, f2);
-            v2 = __ffma2_rn(w, w, v2);
         }
         const float vx4 = __fmaf_rn(cFh, fold[4], __fmul_rn(cv, vold[4]));
         vn[4] = __fmaf_rn(hdt, fn[4], vx4);
-        pv = __fmaf_rn(fn[4], vn[4], __fadd_rn(p2.x, p2.y));
-        ff = __fmaf_rn(fn[4], fn[4], __fadd_rn(f2.x, f2.y));
-        vv = __fmaf_rn(vn[4], vn[4], __fadd_rn(v2.x, v2.y));
     }
 };
 
@@ -301,52 +278,93 @@ __device__ __forceinline__ void q_values(const int *q, float *o) {
     o[4] = __fmul_rn(__int2float_rn(q[4]), float(QFIX_INV));
 }
 
-// per-thread accumulation of the FIRE sums: plain FP64 for the FP64 form;
-// compensated float-float (Knuth's two-sum) for the FP32 form, so that the
-// sums keep ~48 bits without FP64 work per site, and are FP64 from then on
+// Per-thread FIRE contributions of the sites a thread owns: P = sum F.v,
+// |F|^2, |v|^2 and the largest site |F|^2 (Algorithm 1's power, norms and the
+// convergence residual).  FP64 form: FP64 products and sums.  FP32 form: the
+// same quantities without FP64 work per site, to FP64 accuracy.  Every
+// product of two floats is split without error into p = fl(a b) and
+// e = fma(a, b, -p) (the error-free product of Ogita, Rump and Oishi,
+// "Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005); the p are
+// summed with Knuth's two-sum, which returns the rounding error of each
+// addition exactly, and the small parts (the e and the two-sum errors) are
+// added in plain float, where their own rounding is of order 2^-48 of the
+// result.  A site's P and |F|^2 are formed this way as float-float pairs,
+// the largest |F|^2 is kept as a normalised pair, and each site's pair is
+// added into the thread's float-float sums; from there on the sums are FP64.
 template <typename T>
-struct Acc;
+struct FireSums;
 template <>
-struct Acc<double> {
-    double s = 0.0;
-    __device__ __forceinline__ void add(double x) { s += x; }
-    __device__ __forceinline__ double get() const { return s; }
-};
-template <>
-struct Acc<float> {
-    float hi = 0.0f, lo = 0.0f;
-    __device__ __forceinline__ void add(float x) {
-        float t = __fadd_rn(hi, x);
-        float bp = __fsub_rn(t, hi);
-        float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(x, bp));
-        hi = t;
-        lo = __fadd_rn(lo, e);
+struct FireSums<double> {
+    double p = 0.0, f = 0.0, v = 0.0, r = 0.0;
+    __device__ __forceinline__ void site(const double *fn, const double *vn) {
+        double pv = 0.0, ff = 0.0, vv = 0.0;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            pv = fma_rn(fn[c], vn[c], pv);
+            ff = fma_rn(fn[c], fn[c], ff);
+            vv = fma_rn(vn[c], vn[c], vv);
+        }
+        p += pv; f += ff; v += vv;
+        r = fmax(r, ff);
     }
-    __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
-};
-// two sums side by side: the same two-sum per lane, as FADD2 pairs
-template <typename T>
-struct Acc2 {
-    Acc<T> a, b;
-    __device__ __forceinline__ void add(T x, T y) { a.add(x); b.add(y); }
-    __device__ __forceinline__ double get0() const { return a.get(); }
-    __device__ __forceinline__ double get1() const { return b.get(); }
-};
-template <>
-struct Acc2<float> {
-    float2 hi = make_float2(0.f, 0.f), lo = make_float2(0.f, 0.f);
-    // a - b as fma(-1, b, a): exact product, one rounding, as the subtraction
-    __device__ __forceinline__ void add(float x, float y) {
-        const float2 M1 = make_float2(-1.f, -1.f);
-        const float2 X = make_float2(x, y);
-        const float2 t = __fadd2_rn(hi, X);
-        const float2 bp = __ffma2_rn(M1, hi, t);
-        const float2 e = __fadd2_rn(__ffma2_rn(M1, __ffma2_rn(M1, bp, t), hi), __ffma2_rn(M1, bp, X));
-        hi = t;
-        lo = __fadd2_rn(lo, e);
+    __device__ __forceinline__ void get(double &P, double &F2, double &V2, double &R2) const {
+        P = p; F2 = f; V2 = v; R2 = r;
     }
-    __device__ __forceinline__ double get0() const { return (double)hi.x + (double)lo.x; }
-    __device__ __forceinline__ double get1() const { return (double)hi.y + (double)lo.y; }
+};
+// two-sum on two lanes: s + e = a + b exactly, s = fl(a + b) (a - b is
+// written fma(-1, b, a): an exact product and one rounding, as the subtraction)
+__device__ __forceinline__ float2 two_sum2(float2 a, float2 b, float2 &e) {
+    const float2 M1 = make_float2(-1.f, -1.f);
+    const float2 s = __fadd2_rn(a, b);
+    const float2 bp = __ffma2_rn(M1, a, s);
+    e = __fadd2_rn(__ffma2_rn(M1, __ffma2_rn(M1, bp, s), a), __ffma2_rn(M1, bp, b));
+    return s;
+}
+// error-free product on two lanes: p + e = a b exactly
+__device__ __forceinline__ float2 two_prod2(float2 a, float2 b, float2 &e) {
+    const float2 p = __fmul2_rn(a, b);
+    e = __ffma2_rn(a, b, make_float2(-p.x, -p.y));
+    return p;
+}
+template <>
+struct FireSums<float> {
+    float2 pf_hi = make_float2(0.f, 0.f), pf_lo = pf_hi;   // lanes (P, |F|^2)
+    float2 vv_hi = make_float2(0.f, 0.f), vv_lo = vv_hi;   // |v|^2 in two lanes
+    float r_hi = 0.f, r_lo = 0.f;                           // largest site |F|^2
+    __device__ __forceinline__ void site(const float *fn, const float *vn) {
+        // the site's (F.v, |F|^2) as float-float pairs (s, lo)
+        float2 lo, e, t;
+        float2 s = two_prod2(make_float2(fn[0], fn[0]), make_float2(vn[0], fn[0]), lo);
+#pragma unroll
+        for (int c = 1; c < 5; ++c) {
+            const float2 pc = two_prod2(make_float2(fn[c], fn[c]), make_float2(vn[c], fn[c]), e);
+            s = two_sum2(s, pc, t);
+            lo = __fadd2_rn(lo, __fadd2_rn(t, e));
+        }
+        // largest site |F|^2: normalise the pair (fast two-sum, |s| >= |lo|),
+        // compare high parts first
+        {
+            const float h = __fadd_rn(s.y, lo.y);
+            const float l = __fsub_rn(lo.y, __fsub_rn(h, s.y));
+            if (h > r_hi || (h == r_hi && l > r_lo)) { r_hi = h; r_lo = l; }
+        }
+        pf_hi = two_sum2(pf_hi, s, t);
+        pf_lo = __fadd2_rn(pf_lo, __fadd2_rn(t, lo));
+        // |v|^2 product by product: components (0, 1), (2, 3), (4, -)
+#pragma unroll
+        for (int c = 0; c < 5; c += 2) {
+            const float2 vc = make_float2(vn[c], c + 1 < 5 ? vn[c + 1] : 0.f);
+            const float2 pc = two_prod2(vc, vc, e);
+            vv_hi = two_sum2(vv_hi, pc, t);
+            vv_lo = __fadd2_rn(vv_lo, __fadd2_rn(t, e));
+        }
+    }
+    __device__ __forceinline__ void get(double &P, double &F2, double &V2, double &R2) const {
+        P = (double)pf_hi.x + (double)pf_lo.x;
+        F2 = (double)pf_hi.y + (double)pf_lo.y;
+        V2 = ((double)vv_hi.x + (double)vv_lo.x) + ((double)vv_hi.y + (double)vv_lo.y);
+        R2 = (double)r_hi + (double)r_lo;
+    }
 };
 
 template <typename T>
@@ -1294,9 +1312,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
     const T L1s = L1 * sc_, L23s = L23 * sc_;
     const T L2q = T(0.25) * args.L2 * sc_, L3q = T(0.25) * args.L3 * sc_;
 
-    Acc2<T> accPF;
-    Acc<T> accV;
-    T accR = T(0);
+    FireSums<T> sums;
     const uint8_t FULL = M_SIM | 0xFC;
 
     int sm = slot_of(z0 - 1), sc = slot_of(z0), sp = slot_of(z0 + 1), s2 = slot_of(z0 + 2);
@@ -1575,12 +1591,12 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
 #pragma unroll
                 for (int c = 0; c < 5; ++c) Fout[c * N + i] = Fn[c];
             } else {
-                T pv, ff, vv, vn[5];
+                T vn[5];
                 if constexpr (WCACHE) {
                     T w[5];
 #pragma unroll
                     for (int c = 0; c < 5; ++c) w[c] = S.w(z % 3, c);
-                    Site5<T>::kick_w(w, Fn, hdt, vn, pv, ff, vv);
+                    Site5<T>::kick_w(w, Fn, hdt, vn);
                 } else {
                     if constexpr (sizeof(T) == 8) {
 #pragma unroll
@@ -1589,7 +1605,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                             fold[c] = __ldg(Fin + c * N + i);
                         }
                     }
-                    Site5<T>::kick(vold, fold, Fn, cv, cFh, hdt, vn, pv, ff, vv);
+                    Site5<T>::kick(vold, fold, Fn, cv, cFh, hdt, vn);
                 }
 #pragma unroll
                 for (int c = 0; c < 5; ++c) {
@@ -1597,9 +1613,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                     __stcs(vout + c * N + i, vn[c]);
                     __stcs(Fout + c * N + i, Fn[c]);
                 }
-                accPF.add(pv, ff);
-                accV.add(vv);
-                accR = fmax(accR, ff);
+                sums.site(Fn, vn);
             }
         }
         // rotate the plane slots
@@ -1611,8 +1625,9 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
 
     // block reduction, then the last block reduces the partials in order; a
     // fixed-point range violation poisons the max with +inf (-> diverged)
-    double sP = accPF.get0(), sF = accPF.get1(), sV = accV.get();
-    double sR = bad ? (double)INFINITY : (double)accR;
+    double sP, sF, sV, sR;
+    sums.get(sP, sF, sV, sR);
+    if (bad) sR = (double)INFINITY;
     block_reduce4<NT>(sP, sF, sV, sR, red);
     const int nblocks = nblk;
     if (threadIdx.x == 0) {
@@ -1819,9 +1834,21 @@ void step_args_pack(const StepLaunch &sl, void *out) {
     else pack_args<double>(sl, *static_cast<StepArgs<double> *>(out));
 }
 
+// batch tiles: 32 x TY in every form; 64 x TY also for one-constant FP32
+// lattices (the wide tiles of the single-lattice kernel)
+bool batch_tile_ok(int fp32, int form, int tx) { return tx == 32 || (tx == 64 && fp32 && form == 0); }
+
 struct PrepareBatch {
+    int tx;
     template <typename T, int FORM, int TY, typename I>
     cudaError_t run() {
+        if constexpr (sizeof(T) == 4 && FORM == 0) {
+            if (tx == 64)
+                return cudaFuncSetAttribute(fire_batch_kernel<T, FORM, 64, TY, I>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)step_smem_bytes<T, FORM, 64, TY>());
+        }
+        if (tx != 32) return cudaErrorInvalidValue;
         return cudaFuncSetAttribute(fire_batch_kernel<T, FORM, 32, TY, I>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)step_smem_bytes<T, FORM, 32, TY>());
@@ -1829,9 +1856,17 @@ struct PrepareBatch {
 };
 
 struct BlocksBatch {
+    int tx;
     template <typename T, int FORM, int TY, typename I>
     int run() {
         int nb = 0;
+        if constexpr (sizeof(T) == 4 && FORM == 0) {
+            if (tx == 64) {
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fire_batch_kernel<T, FORM, 64, TY, I>,
+                                                              64 * TY, step_smem_bytes<T, FORM, 64, TY>());
+                return nb;
+            }
+        }
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fire_batch_kernel<T, FORM, 32, TY, I>,
                                                       32 * TY, step_smem_bytes<T, FORM, 32, TY>());
         return nb;
@@ -1841,10 +1876,19 @@ struct BlocksBatch {
 struct LaunchBatch {
     const void *args;
     const WorkItem *items;
-    int nitems, grid;
+    int nitems, grid, tx;
     cudaStream_t stream;
     template <typename T, int FORM, int TY, typename I>
     cudaError_t run() {
+        if constexpr (sizeof(T) == 4 && FORM == 0) {
+            if (tx == 64) {
+                fire_batch_kernel<T, FORM, 64, TY, I><<<grid, 64 * TY, step_smem_bytes<T, FORM, 64, TY>(),
+                                                        stream>>>(static_cast<const StepArgs<T> *>(args),
+                                                                  items, nitems);
+                return cudaGetLastError();
+            }
+        }
+        if (tx != 32) return cudaErrorInvalidValue;
         fire_batch_kernel<T, FORM, 32, TY, I><<<grid, 32 * TY, step_smem_bytes<T, FORM, 32, TY>(),
                                                 stream>>>(static_cast<const StepArgs<T> *>(args), items,
                                                           nitems);
@@ -1852,18 +1896,21 @@ struct LaunchBatch {
     }
 };
 
-cudaError_t prepare_fire_batch(int fp32, int form, int ty, int idx32) {
-    return dispatch(fp32, form, ty, idx32 != 0, PrepareBatch{});
+cudaError_t prepare_fire_batch(int fp32, int form, int tx, int ty, int idx32) {
+    if (!batch_tile_ok(fp32, form, tx)) return cudaErrorInvalidValue;
+    return dispatch(fp32, form, ty, idx32 != 0, PrepareBatch{tx});
 }
 
-int fire_batch_blocks_per_sm(int fp32, int form, int ty, int idx32) {
-    return dispatch(fp32, form, ty, idx32 != 0, BlocksBatch{});
+int fire_batch_blocks_per_sm(int fp32, int form, int tx, int ty, int idx32) {
+    if (!batch_tile_ok(fp32, form, tx)) return 0;
+    return dispatch(fp32, form, ty, idx32 != 0, BlocksBatch{tx});
 }
 
-cudaError_t launch_fire_batch(int fp32, int form, int ty, int idx32, const void *dev_args,
+cudaError_t launch_fire_batch(int fp32, int form, int tx, int ty, int idx32, const void *dev_args,
                               const WorkItem *items, int nitems, int grid, cudaStream_t stream) {
     if (fault_due(2)) return cudaErrorLaunchFailure;   // injected: nothing is launched
-    return dispatch(fp32, form, ty, idx32 != 0, LaunchBatch{dev_args, items, nitems, grid, stream});
+    if (!batch_tile_ok(fp32, form, tx)) return cudaErrorInvalidValue;
+    return dispatch(fp32, form, ty, idx32 != 0, LaunchBatch{dev_args, items, nitems, grid, tx, stream});
 }
 
 __global__ void k_batch_running(FireDev *const *states, int n, unsigned int *running) {

@@ -36,12 +36,14 @@ EXPORTS = [
     "lq_force", "lq_energy", "lq_order_field", "lq_fire_reset", "lq_step", "lq_minimize",
     "lq_fire_result", "lq_get_state", "lq_set_state", "lq_set_zchunk", "lq_device_bytes",
     "lq_energy_noalloc", "lq_batch_create", "lq_batch_destroy", "lq_batch_last_error",
-    "lq_batch_set_tiling", "lq_batch_get_tiling", "lq_batch_autotune", "lq_batch_step",
+    "lq_batch_set_tiling", "lq_batch_get_tiling", "lq_batch_set_tile", "lq_batch_get_tile",
+    "lq_batch_autotune", "lq_batch_step",
     "lq_batch_minimize", "lq_server_create", "lq_server_destroy", "lq_server_submit",
     "lq_server_poll", "lq_server_wait", "lq_server_stats_get", "lq_boundary_check",
     "lq_add_boundary_text", "lq_load_boundary_file", "lq_object_count", "lq_move_object",
     "lq_clear_objects", "lq_set_material", "lq_clone", "lq_pmf_sweep", "lq_init_dipolar",
     "lq_frank_to_landau", "lq_set_index_width", "lq_inject_fault", "lq_bounds_check_hits",
+    "lq_fp64_fma_rate",
 ]
 
 
@@ -99,7 +101,8 @@ class Request(C.Structure):
 
 class ServerStats(C.Structure):
     _fields_ = [("queued", C.c_int64), ("active", C.c_int64), ("completed", C.c_int64),
-                ("bytes_in_use", C.c_size_t), ("budget", C.c_size_t), ("site_updates", C.c_double)]
+                ("bytes_in_use", C.c_size_t), ("budget", C.c_size_t), ("site_updates", C.c_double),
+                ("site_updates_issued", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -156,6 +159,8 @@ def load(path: str = LIB_PATH):
         "lq_batch_last_error": (C.c_char_p, [p]),
         "lq_batch_set_tiling": (C.c_int, [p, C.c_int, C.c_int]),
         "lq_batch_get_tiling": (C.c_int, [p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "lq_batch_set_tile": (C.c_int, [p, C.c_int, C.c_int, C.c_int]),
+        "lq_batch_get_tile": (C.c_int, [p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "lq_batch_autotune": (C.c_int, [p, C.POINTER(FireParams), C.c_int, C.POINTER(d)]),
         "lq_batch_step": (C.c_int, [p, C.POINTER(FireParams), i64, p]),
         "lq_batch_minimize": (C.c_int, [p, C.POINTER(FireParams), p]),
@@ -180,6 +185,7 @@ def load(path: str = LIB_PATH):
         "lq_set_index_width": (C.c_int, [S, C.c_int]),
         "lq_inject_fault": (C.c_int, [C.c_int, i64]),
         "lq_bounds_check_hits": (C.c_int, [C.POINTER(C.c_uint32)]),
+        "lq_fp64_fma_rate": (C.c_int, [i64, C.POINTER(d)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -232,6 +238,17 @@ def frank_to_landau(K1, K2, K3, K24, q0, S):
 LQ_FAULT_NONE, LQ_FAULT_DEVICE_ALLOC, LQ_FAULT_STEP_LAUNCH = 0, 1, 2
 
 
+def fp64_fma_rate(iters: int = 1 << 16) -> float:
+    """Measured FP64 fused multiply-adds per second of the current device
+    (lq_fp64_fma_rate): the ceiling of the FP64 form of the step."""
+    lib = load()
+    out = C.c_double()
+    st = lib.lq_fp64_fma_rate(int(iters), C.byref(out))
+    if st != LQ_OK:
+        raise LqError(st, "lq_fp64_fma_rate")
+    return out.value
+
+
 def inject_fault(kind, after=0):
     """Host-side fault injection for tests (see ``lq_inject_fault``)."""
     st = load().lq_inject_fault(int(kind), int(after))
@@ -254,6 +271,22 @@ def boundary_check(text):
 
 def anchoring(kind, W, dir=(0.0, 0.0, 1.0)) -> Anchoring:
     return Anchoring(int(kind), float(W), (C.c_double * 3)(*[float(v) for v in dir]))
+
+
+# lq_anchoring as a numpy record (int kind, 4 bytes of padding, double W,
+# double dir[3]: 40 bytes), for per-site arrays marshalled without a Python loop
+_ANCHOR_DTYPE = np.dtype([("kind", "<i4"), ("pad", "<i4"), ("W", "<f8"), ("dir", "<f8", (3,))])
+assert _ANCHOR_DTYPE.itemsize == C.sizeof(Anchoring)
+
+
+def anchoring_array(n, kinds, W, dirs) -> np.ndarray:
+    """n lq_anchoring records in one contiguous array (kinds, W, dirs
+    broadcast to n sites)."""
+    arr = np.zeros(max(1, n), dtype=_ANCHOR_DTYPE)
+    arr["kind"][:n] = np.broadcast_to(np.asarray(kinds), (n,))
+    arr["W"][:n] = np.broadcast_to(np.asarray(W, dtype=float), (n,))
+    arr["dir"][:n] = np.broadcast_to(np.asarray(dirs, dtype=float), (n, 3))
+    return arr
 
 
 class Solver:
@@ -340,13 +373,8 @@ class Solver:
     def add_anchored_sites(self, xyz, kinds, W, dirs):
         xyz = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
         n = xyz.shape[0]
-        arr = (Anchoring * max(1, n))()
-        kinds = np.broadcast_to(np.asarray(kinds), (n,))
-        W = np.broadcast_to(np.asarray(W, dtype=float), (n,))
-        dirs = np.broadcast_to(np.asarray(dirs, dtype=float), (n, 3))
-        for t in range(n):
-            arr[t] = anchoring(kinds[t], W[t], dirs[t])
-        self._ck(self.lib.lq_add_anchored_sites(self.h, n, _ptr(xyz), C.cast(arr, C.c_void_p)))
+        arr = anchoring_array(n, kinds, W, dirs)
+        self._ck(self.lib.lq_add_anchored_sites(self.h, n, _ptr(xyz), _ptr(arr)))
 
     def add_objects(self, objects):
         """Objects in the dict format of ``synth`` (same as the oracle's)."""
@@ -547,10 +575,21 @@ class Batch:
     def set_tiling(self, tile_y, zchunk):
         self._ck(self.lib.lq_batch_set_tiling(self.h, int(tile_y), int(zchunk)))
 
-    def autotune(self, params: FireParams, launches=5):
+    def tile(self):
+        """(tile width, tile height, z chunk) of the current tiling."""
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        self._ck(self.lib.lq_batch_get_tile(self.h, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
+
+    def set_tile(self, tile_x, tile_y, zchunk):
+        self._ck(self.lib.lq_batch_set_tile(self.h, int(tile_x), int(tile_y), int(zchunk)))
+
+    def autotune(self, params: FireParams, launches=12):
+        """Time every tiling (lq_batch_autotune); returns ((tile width,
+        tile height, z chunk), milliseconds per launch of the fastest)."""
         ms = C.c_double()
         self._ck(self.lib.lq_batch_autotune(self.h, C.byref(params), int(launches), C.byref(ms)))
-        return self.tiling(), ms.value
+        return self.tile(), ms.value
 
     def step(self, params: FireParams, n: int):
         out = (Result * len(self.solvers))()
@@ -621,15 +660,9 @@ class Server:
                 o.n = xyz.shape[0]
                 o.xyz = xyz.ctypes.data
                 if spec["type"] == "anchored":
-                    n = xyz.shape[0]
-                    per = (Anchoring * max(1, n))()
-                    kinds = np.broadcast_to(np.asarray(spec["kinds"]), (n,))
-                    Ws = np.broadcast_to(np.asarray(spec["W"], dtype=float), (n,))
-                    dirs = np.broadcast_to(np.asarray(spec["dirs"], dtype=float), (n, 3))
-                    for t in range(n):
-                        per[t] = anchoring(kinds[t], Ws[t], dirs[t])
+                    per = anchoring_array(xyz.shape[0], spec["kinds"], spec["W"], spec["dirs"])
                     keep.append(per)
-                    o.per_site = C.cast(per, C.c_void_p).value
+                    o.per_site = per.ctypes.data
         rq = Request(lat, mat, len(cfg.get("objects", [])), C.cast(objs, C.c_void_p).value, None,
                      int(seed), float(S), params, int(bool(want_S)))
         if q0 is not None:

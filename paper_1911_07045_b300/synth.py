@@ -253,9 +253,14 @@ def serving_requests(seed: int = 5, count: int = 2000, rate: float = 20.0):
     (alternating +-1 surface defects, period drawn from [16, 48] among values
     with L divisible by 2d) and a homeotropic top wall, half with 1-2
     homeotropic colloids."""
+    return list(iter_serving_requests(seed, count, rate))
+
+
+def iter_serving_requests(seed: int = 5, count: int = 2000, rate: float = 20.0):
+    """The requests of ``serving_requests`` one at a time (the same stream),
+    so that a long stream never sits in memory at once."""
     u = _rng_stream(seed)
     t = 0.0
-    out = []
     edges = list(range(48, 193, 16))
     hom = (ND_HOMEOTROPIC, W_HOMEOTROPIC, (0.0, 0.0, 1.0))
     for r in range(count):
@@ -280,6 +285,5 @@ def serving_requests(seed: int = 5, count: int = 2000, rate: float = 20.0):
                     for c, R in place_spheres(L, nsph, 12.0, 24.0, seed * 100000 + r + 1,
                                               walls=False, r_clamp=math.floor(0.2 * L))]
             kind = "colloids"
-        out.append(dict(t_arrival=t, shape=(L, L, L), L1=L1_5CB, L2=0.0, L3=0.0,
-                        objects=objs, seed=seed * 100000 + 50000 + r, kind=kind, tol=1e-6))
-    return out
+        yield dict(t_arrival=t, shape=(L, L, L), L1=L1_5CB, L2=0.0, L3=0.0,
+                   objects=objs, seed=seed * 100000 + 50000 + r, kind=kind, tol=1e-6)

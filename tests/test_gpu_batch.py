@@ -113,8 +113,8 @@ def test_autotune_leaves_state_and_tuned_run_agrees():
     batch = lqmin.Batch(mixed)
     p = lqmin.fire_params(**dict(FP, max_iter=10 ** 6, force_tol=1e-14))
     before = [m.get_q() for m in mixed]
-    (ty, zc), ms = batch.autotune(p, launches=3)
-    assert ty in (4, 8) and zc in (8, 16, 32, 64, 128) and ms > 0
+    (tx, ty, zc), ms = batch.autotune(p, launches=10)
+    assert tx in (32, 64) and ty in (4, 8) and zc in (8, 16, 32, 64, 128) and ms > 0
     for m, q in zip(mixed, before):
         assert np.array_equal(m.get_q(), q)
         assert m.fire_result().iterations == 0
@@ -143,3 +143,36 @@ def test_converged_lattice_stays_put():
     assert np.array_equal(ss[1].get_q(), uniform)
     assert res[0].iterations == 15 and res[2].iterations == 15
     batch.close()
+
+
+def test_wide_tiles_match_alone_bit_for_bit():
+    """64-wide batch tiles on one-constant FP32-form lattices at least 256
+    sites wide, which run 64-wide tiles alone too: bit-identical trajectories;
+    the wide tiles are refused for three-constant batches."""
+    cfgs = [dict(shape=(256, 12, 10), L=(2.32, 0.0, 0.0),
+                 objects=[dict(type="sphere", c=(100.0, 6.0, 5.0), R=3.5, anchor=HOM())]),
+            dict(shape=(320, 8, 12), L=(2.32, 0.0, 0.0), objects=[])]
+    alone = [make(c, 1) for c in cfgs]
+    mixed = [make(c, 1) for c in cfgs]
+    for k, (a, m, c) in enumerate(zip(alone, mixed, cfgs)):
+        q = synth.random_uniaxial_q(c["shape"], 500 + k)
+        a.set_q(q)
+        m.set_q(q)
+    batch = lqmin.Batch(mixed)
+    batch.set_tile(64, 4, 0)
+    assert batch.tile() == (64, 4, 0)
+    assert batch.tiling() == (4, 0)
+    p = lqmin.fire_params(**dict(FP, max_iter=10 ** 6, force_tol=1e-14))
+    res = batch.step(p, 17)
+    for a, m, r in zip(alone, mixed, res):
+        ra = a.step(p, 17)
+        assert ra.iterations == r.iterations == 17
+        assert np.array_equal(a.get_q(), m.get_q())
+        assert np.array_equal(a.get_force(), m.get_force())
+    batch.close()
+    three = [make(dict(shape=(256, 8, 8), L=(2.32, 0.5, 0.3), objects=[]), 1)]
+    b3 = lqmin.Batch(three)
+    lib = lqmin.load()
+    assert lib.lq_batch_set_tile(b3.h, 64, 4, 0) == lqmin.LQ_EINVAL
+    assert b3.tile()[0] == 32
+    b3.close()
