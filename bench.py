@@ -272,57 +272,153 @@ def run_batch(steps: int):
     sites = sum(int(np.prod(c["shape"])) for c in cfgs)
     batch = lqmin.Batch(solvers)
     p = lqmin.fire_params(**dict(synth.FIRE_DEFAULTS, max_iter=10 ** 12, force_tol=0.0))
-    (ty, zc), tuned_ms = batch.autotune(p, launches=3)
+    (tx, ty, zc), tuned_ms = batch.autotune(p, launches=12)
     batch.step(p, 3)                                  # warm-up
     t0 = time.perf_counter(); batch.step(p, steps); t1 = time.perf_counter()
     batch.step(p, 2 * steps); t2 = time.perf_counter()
     sec = (t2 - t1) - (t1 - t0)                       # host overhead of a call cancels
+    peak, peak_kind = measured_peaks()
+    ach = ALG_BYTES["fp32"] * sites / (sec / steps) / 1e9
     out = {"workload": f"{len(cfgs)} cubic lattices, edges {{32,48,64,96,128}}, 0-3 colloids "
                        f"R~U[6,16] (W=5.3), one constant, FP32 form",
            "sites": sites, "steps": steps, "value": sites * steps / sec, "unit": UNIT,
-           "ms_per_step": sec / steps * 1e3, "tiling": {"tile": f"32x{ty}", "zchunk": zc},
-           "autotune_ms_per_step": tuned_ms, "launches_per_step": 1}
+           "ms_per_step": sec / steps * 1e3, "tiling": {"tile": f"{tx}x{ty}", "zchunk": zc},
+           "autotune_ms_per_step": tuned_ms, "autotune_launches_per_candidate": 12,
+           "launches_per_step": 1,
+           # algorithmic bytes (q, v read + written, mask) of every lattice
+           # per launch over the time per launch (host-timed graph launches)
+           "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(ach / peak, 4), "traffic": None,
+                        "alg_bytes_per_site": ALG_BYTES["fp32"],
+                        "peak_kind": peak_kind + " (HBM copy)"}}
     batch.close()
     for s in solvers:
         s.close()
     return out
 
 
-def run_serving(count: int, rate: float, budget_gb: float = 120.0):
-    """The seeded request stream of the serving workload (Poisson arrivals,
-    edges 48..192, half patterned substrate + homeotropic top wall, half 1-2
-    colloids, one constant, FP32 form, max|F| < 1e-6), submitted in real
-    time to a continuous-batching server with an HBM budget."""
+SERVING_FIRE = dict(synth.FIRE_DEFAULTS, max_iter=200000, force_tol=1e-6)
+
+
+def serve_stream(rate: float, window_s: float, extra_s: float, max_requests: int = 2000,
+                 max_active: int = 8, budget_gb: float = 120.0, seed: int = 5, sample_s: float = 5.0):
+    """Serve the seeded request stream of the serving workload (Poisson
+    arrivals, edges 48..192, half patterned substrate + homeotropic top wall,
+    half 1-2 colloids, one constant, FP32 form, max|F| < 1e-6) in real time
+    on a continuous-batching server with an HBM budget: submit every request
+    that arrives within ``window_s`` seconds, keep serving ``extra_s`` seconds
+    more, then stop (the server drops what is left).  Reports the requests
+    completed, in flight and queued at the end, the queue over time, the
+    sustained site-updates/s (site updates the server issued to the GPU, and
+    those of completed solves alone), and p50/p99 time-to-converged of the
+    completed requests."""
     from paper_1911_07045_b300 import lqmin
-    reqs = synth.serving_requests(count=count, rate=rate)
-    p = lqmin.fire_params(**dict(synth.FIRE_DEFAULTS, max_iter=200000, force_tol=1e-6))
-    sv = lqmin.Server(int(budget_gb * (1 << 30)), max_active=64)
+    p = lqmin.fire_params(**SERVING_FIRE)
+    sv = lqmin.Server(int(budget_gb * (1 << 30)), max_active=max_active)
+    pending, done, timeline = {}, [], []
     t0 = time.perf_counter()
-    tickets = []
-    for r in reqs:
-        delay = r["t_arrival"] - (time.perf_counter() - t0)
-        if delay > 0:
-            time.sleep(delay)
-        tickets.append(sv.submit(r, p, seed=r["seed"]))
-    lat, its, conv = [], [], 0
-    for t in tickets:
-        got = sv.wait(t, timeout=900.0)
-        if got is None:
-            raise RuntimeError("served request did not finish within 900 s")
-        code, res, _ = got
-        conv += int(code == lqmin.LQ_OK and res.fire_status == lqmin.FIRE_CONVERGED)
-        lat.append(res.seconds)
-        its.append(res.iterations)
-    wall = time.perf_counter() - t0
+    nxt = [0.0]
+
+    def collect():
+        for t in list(pending):
+            got = sv.poll(t)
+            if got is not None:
+                code, res, _ = got
+                L, kind = pending.pop(t)
+                done.append(dict(latency=res.seconds, iterations=int(res.iterations), L=L, kind=kind,
+                                 converged=bool(code == lqmin.LQ_OK and
+                                                res.fire_status == lqmin.FIRE_CONVERGED)))
+
+    def tick(force=False):
+        now = time.perf_counter() - t0
+        if force or now >= nxt[0]:
+            collect()
+            st = sv.stats()
+            timeline.append(dict(t=round(now, 1), queued=st["queued"], active=st["active"],
+                                 completed=st["completed"], issued=st["site_updates_issued"]))
+            nxt[0] = now + sample_s
+        return now
+
+    submitted = 0
+    for r in synth.iter_serving_requests(seed=seed, count=max_requests, rate=rate):
+        if r["t_arrival"] > window_s:
+            break
+        while True:
+            now = tick()
+            if now >= r["t_arrival"]:
+                break
+            time.sleep(min(r["t_arrival"] - now, 0.05))
+        t = sv.submit(r, p, seed=r["seed"])
+        pending[t] = (r["shape"][0], r["kind"])
+        submitted += 1
+    while pending and tick() < window_s + extra_s:
+        time.sleep(0.05)
+    wall = tick(force=True)
     st = sv.stats()
     sv.close()
-    lat = np.array(lat)
-    return {"workload": f"first {count} requests of the seeded serving stream (seed 5), Poisson "
-                        f"{rate}/s, edges 48..192, FP32 form, tol 1e-6, HBM budget {budget_gb} GB",
-            "requests": count, "converged": conv,
+    lat = np.array([d["latency"] for d in done]) if done else np.array([np.nan])
+    # sustained rate: issued site updates between the first sample with work
+    # on the GPU and the end
+    first = next((x for x in timeline if x["issued"] > 0), timeline[-1])
+    span = max(1e-9, timeline[-1]["t"] - first["t"])
+    by_edge = {}
+    for d in done:
+        if d["converged"]:
+            by_edge.setdefault(d["L"], []).append(d["iterations"])
+    return {"rate_per_s": rate, "arrival_window_s": window_s, "extra_s": extra_s,
+            "max_active": max_active, "hbm_budget_gb": budget_gb, "submitted": submitted,
+            "completed": len(done), "converged": sum(d["converged"] for d in done),
+            "in_flight_at_end": int(st["active"]), "queued_at_end": int(st["queued"]),
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "mean_iterations": float(np.mean(its)),
-            "site_updates_per_s": st["site_updates"] / wall, "wall_s": wall}
+            "mean_iterations_completed": float(np.mean([d["iterations"] for d in done])) if done else None,
+            "iterations_by_edge": {str(k): float(np.median(v)) for k, v in sorted(by_edge.items())},
+            "site_updates_per_s": (timeline[-1]["issued"] - first["issued"]) / span,
+            "completed_site_updates_per_s": st["site_updates"] / wall, "wall_s": round(wall, 1),
+            "queue_over_time": [[x["t"], x["queued"], x["active"], x["completed"]]
+                                for x in timeline[:: max(1, len(timeline) // 24)] + [timeline[-1]]]}
+
+
+# FIRE iterations to max|F| < 1e-6 of the serving stream's requests by cubic
+# edge: the first request of each edge in the seeded stream minimised alone
+# on a B300 (FP32 form, `bench.py --serving-calibrate`); the scaled-rate
+# stream takes its arrival rate from these and the measured throughput
+SERVING_ITERS_BY_EDGE = {"48": 33530, "64": 13881, "80": 60508, "96": 64341, "112": 100200, "128": 32747, "144": 32364, "160": 43518, "176": 36239, "192": 55247}
+
+
+def serving_capacity(rate_site_updates: float, iters_by_edge: dict) -> float:
+    """Requests per second one GPU finishes at ``rate_site_updates``: the
+    stream's edges are uniform over {48, 64, ..., 192}, so the mean work per
+    request is the mean over edges of L^3 x iterations(L)."""
+    edges = list(range(48, 193, 16))
+    known = sorted((int(k), v) for k, v in iters_by_edge.items())
+    if not known:
+        return float("nan")
+    xs = np.array([k for k, _ in known], dtype=float)
+    ys = np.array([v for _, v in known], dtype=float)
+    work = np.mean([L ** 3 * float(np.interp(L, xs, ys)) for L in edges])
+    return rate_site_updates / work
+
+
+def serving_calibrate(count: int = 1):
+    """Minimise the first request of each edge of the seeded stream alone
+    (FP32 form, the serving FIRE parameters): iterations and seconds."""
+    from paper_1911_07045_b300 import lqmin
+    p = lqmin.fire_params(**SERVING_FIRE)
+    seen, out = {}, {}
+    for r in synth.iter_serving_requests(count=2000):
+        L = r["shape"][0]
+        if seen.get(L, 0) >= count:
+            continue
+        seen[L] = seen.get(L, 0) + 1
+        s = lqmin.solver_for(r, precision=lqmin.LQ_FP32_BULK_FP64_RED)
+        s.init_random_uniaxial(r["seed"])
+        st, res = s.minimize(p)
+        out.setdefault(str(L), []).append(dict(iterations=int(res.iterations), seconds=round(res.seconds, 2),
+                                               kind=r["kind"], converged=bool(res.fire_status == 1)))
+        s.close()
+        if len(seen) == 10 and all(v >= count for v in seen.values()):
+            break
+    return out
 
 
 def _trace(s, p, seconds, thresholds=(1e-2, 1e-3, 1e-4)):
@@ -490,12 +586,13 @@ def run_minimizers(L: int, seconds: float):
     return out
 
 
-def cpu_baseline(L_sample=128, steps=16):
-    """The oracle as it stands, on the host cores: FIRE iterations on a
-    L_sample^3 lattice with the same structure (colloids scaled by L/512,
-    planar walls, three constants)."""
+def _oracle_fire_rate(L_sample, steps, threads=None):
+    """FIRE iterations of the FP64 oracle on an L_sample^3 lattice with the
+    bench workload's structure; site-updates/s and the threads it used."""
     import oracle
     oracle.build()
+    if threads is not None:
+        oracle.set_num_threads(threads)
     cfg = synth.config_large(L_sample)
     o = oracle.Oracle(cfg["shape"], synth.A_5CB, synth.B_5CB, synth.C_5CB, cfg["L1"], cfg["L2"],
                       cfg["L3"], objects=cfg["objects"])
@@ -505,10 +602,117 @@ def cpu_baseline(L_sample=128, steps=16):
     t0 = time.perf_counter()
     q, v, F, st = o.fire(q, params, steps, state=st, v=v, F=F)
     dt = time.perf_counter() - t0
-    return {"value": o.N * steps / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    return o.N * steps / dt, oracle.num_threads(), dt
+
+
+def cpu_baseline(L_sample=128, steps=16):
+    """The oracle as it stands, on the host cores: FIRE iterations on a
+    L_sample^3 lattice with the same structure (colloids scaled by L/512,
+    planar walls, three constants), on every host core; then on one thread
+    (a 64^3 sample of 3 iterations)."""
+    import oracle
+    all_cores = os.cpu_count() or 1
+    val, cores, dt = _oracle_fire_rate(L_sample, steps, threads=all_cores)
+    v1, _, dt1 = _oracle_fire_rate(64, 3, threads=1)
+    oracle.set_num_threads(all_cores)
+    return {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{steps} FIRE iterations of the FP64 oracle on a {L_sample}^3 lattice with the "
                       f"same structure (4 colloids scaled by {L_sample}/512, planar walls, 3 constants)",
-            "seconds": dt}
+            "seconds": dt, "cpu_model": _cpu_model(),
+            "single_thread": {"value": v1, "unit": UNIT, "cores": 1, "seconds": dt1,
+                              "sample": "3 FIRE iterations of the FP64 oracle on a 64^3 lattice with the "
+                                        "same structure"}}
+
+
+def _cpu_model() -> str:
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def run_baselines():
+    """The CPU-baseline plan next to the GPU forms, on the workloads the
+    oracle can finish: config 1 (32^3 periodic bulk, one constant, random
+    start seed 1, FIRE to max site |F| < 1e-9) minimised in full by the
+    oracle on every host core, by the FP64 form and by the FP32 form (to
+    1e-6, the FP32 form's tolerance); config 2 (128^3 colloid slab, three
+    constants, seed 2, tol 1e-8) minimised in full by the FP64 form and the
+    FP32 form (1e-6), with the oracle's rate on it from 4 iterations on
+    every core and 1 on one thread (a full oracle minimisation of config 2
+    takes hours)."""
+    import oracle
+    from paper_1911_07045_b300 import lqmin
+    oracle.build()
+    all_cores = os.cpu_count() or 1
+    out = {"host": {"cpu_model": _cpu_model(), "cores": all_cores}}
+    # config 1
+    c1 = synth.config_small_periodic()
+    q0 = synth.random_uniaxial_q(c1["shape"], c1["seed"])
+    N1 = int(np.prod(c1["shape"]))
+    oracle.set_num_threads(all_cores)
+    o = oracle.Oracle(c1["shape"], synth.A_5CB, synth.B_5CB, synth.C_5CB, c1["L1"], 0.0, 0.0)
+    params = dict(synth.FIRE_DEFAULTS, max_iter=10 ** 6, force_tol=c1["tol"])
+    t0 = time.perf_counter()
+    q, v, F, st = o.fire(q0, params, 10 ** 6)
+    dt = time.perf_counter() - t0
+    e_orc = o.energy(q)[0]
+    res = {"oracle_fp64": dict(iterations=int(st["iter"]), seconds=round(dt, 2),
+                               converged=bool(st["status"] == 1), energy=e_orc,
+                               site_updates_per_s=N1 * st["iter"] / dt, cores=oracle.num_threads())}
+    for form, prec, tol in (("gpu_fp64", lqmin.LQ_FP64, c1["tol"]),
+                            ("gpu_fp32", lqmin.LQ_FP32_BULK_FP64_RED, 1e-6)):
+        s = lqmin.solver_for(c1, precision=prec)
+        s.set_q(q0)
+        code, r = s.minimize(lqmin.fire_params(**dict(synth.FIRE_DEFAULTS, max_iter=10 ** 6,
+                                                       force_tol=tol)))
+        res[form] = dict(iterations=int(r.iterations), seconds=round(r.seconds, 3), tol=tol,
+                         converged=bool(r.fire_status == 1), energy=r.energy,
+                         energy_rel_diff_vs_oracle=abs(r.energy - e_orc) / abs(e_orc),
+                         site_updates_per_s=N1 * r.iterations / r.seconds)
+        s.close()
+    out["config1_32cube"] = res
+    # config 2
+    c2 = synth.config_colloid_slab()
+    N2 = int(np.prod(c2["shape"]))
+    q0 = synth.random_uniaxial_q(c2["shape"], c2["seed"])
+    res = {}
+    for form, prec, tol in (("gpu_fp64", lqmin.LQ_FP64, c2["tol"]),
+                            ("gpu_fp32", lqmin.LQ_FP32_BULK_FP64_RED, 1e-6)):
+        s = lqmin.solver_for(c2, precision=prec)
+        s.set_q(q0)
+        code, r = s.minimize(lqmin.fire_params(**dict(synth.FIRE_DEFAULTS, max_iter=400000,
+                                                       force_tol=tol)))
+        res[form] = dict(iterations=int(r.iterations), seconds=round(r.seconds, 3), tol=tol,
+                         converged=bool(r.fire_status == 1), energy=r.energy,
+                         site_updates_per_s=N2 * r.iterations / r.seconds)
+        s.close()
+    o2 = oracle.Oracle(c2["shape"], synth.A_5CB, synth.B_5CB, synth.C_5CB, c2["L1"], c2["L2"], c2["L3"],
+                       objects=c2["objects"])
+    p2 = dict(synth.FIRE_DEFAULTS, max_iter=10 ** 9, force_tol=0.0)
+    for key, threads, steps in (("oracle_fp64_all_cores", all_cores, 4), ("oracle_fp64_1_thread", 1, 1)):
+        oracle.set_num_threads(threads)
+        q, v, F, st = o2.fire(q0, p2, 0)
+        t0 = time.perf_counter()
+        o2.fire(q, p2, steps, state=st, v=v, F=F)
+        dt = time.perf_counter() - t0
+        res[key] = dict(iterations=steps, seconds=round(dt, 2), cores=threads,
+                        site_updates_per_s=N2 * steps / dt)
+    oracle.set_num_threads(all_cores)
+    out["config2_128cube"] = res
+    # the oracle on one thread on config 1's lattice too
+    oracle.set_num_threads(1)
+    q, v, F, st = o.fire(synth.random_uniaxial_q(c1["shape"], c1["seed"]), params, 0)
+    t0 = time.perf_counter()
+    o.fire(q, dict(params, force_tol=0.0), 20, state=st, v=v, F=F)
+    dt = time.perf_counter() - t0
+    out["config1_32cube"]["oracle_fp64_1_thread_rate"] = dict(iterations=20, seconds=round(dt, 2),
+                                                             site_updates_per_s=N1 * 20 / dt)
+    oracle.set_num_threads(all_cores)
+    return out
 
 
 def main_ours(args, dist: Dist):
@@ -517,10 +721,14 @@ def main_ours(args, dist: Dist):
     peak, peak_kind = measured_peaks()
     forms = {}
     for prec in args.precision.split(","):
-        # the FP64 form is ~13x slower: a tenth of the steps keeps its timed
-        # region about as long as the FP32 form's
-        k = args.steps if prec.startswith("fp32") else max(3, args.steps // 10)
+        # the FP64 form is ~13x slower: a tenth of the steps, but at least 10
+        # (half a second at 512^3), keeps its timed region long enough to time
+        k = args.steps if prec.startswith("fp32") else max(10, args.steps // 10)
         forms[prec] = run_form(prec, args.size, k, args.warmup, dist, dist.local)
+    fp64_rate = None
+    if any(not k.startswith("fp32") for k in forms):
+        from paper_1911_07045_b300 import lqmin
+        fp64_rate = lqmin.fp64_fma_rate() / 1e9      # measured, G FP64 op/s
     head = "fp32" if "fp32" in forms else next(iter(forms))
     h = forms[head]
     # roofline of the step kernel: algorithmic bytes per launch over the
@@ -540,15 +748,19 @@ def main_ours(args, dist: Dist):
             if k not in DRAM_BYTES_PER_SITE:
                 rl[k]["traffic_from"] = "three-constant capture (same state bytes)"
         else:
-            # FP64 pipe: derived peak = SMs x ops/clock x maximum SM clock
-            fp64_peak = N_SM * FP64_OPS_PER_CLK_SM * (f["clocks"].get("sm_max_mhz") or 2032.0) * 1e6 / 1e9
+            # FP64 pipe: the measured fused multiply-add rate (lq_fp64_fma_rate);
+            # the figure derived from 148 SMs x 2 FP64 ops/clock x max SM clock
+            # is kept beside it
+            derived = N_SM * FP64_OPS_PER_CLK_SM * (f["clocks"].get("sm_max_mhz") or 2032.0) * 1e6 / 1e9
             ops = FP64_OPS_PER_SITE if k == base else FP64_OPS_PER_SITE_1C
             ach = ops * f["N"] / f["per_launch_s"] / 1e9
-            rl[k] = {"bound": "alu", "achieved": round(ach, 1), "peak": round(fp64_peak, 1),
-                     "unit": "G FP64 op/s", "frac": round(ach / fp64_peak, 4),
+            rl[k] = {"bound": "alu", "achieved": round(ach, 1), "peak": round(fp64_rate, 1),
+                     "unit": "G FP64 op/s", "frac": round(ach / fp64_rate, 4),
                      "traffic": round(traffic), "ops_per_site": ops,
                      "hbm_frac": round(traffic / f["per_launch_s"] / 1e9 / peak, 4),
-                     "peak_kind": "derived: 148 SMs x 2 FP64 ops/clock x max SM clock"}
+                     "peak_kind": "measured: FP64 fused multiply-add chains on every SM "
+                                  "(lq_fp64_fma_rate), CUDA events",
+                     "derived_peak": round(derived, 1)}
             if k not in DRAM_BYTES_PER_SITE:
                 rl[k]["traffic_from"] = "three-constant capture (same state bytes)"
     line = {
@@ -570,8 +782,8 @@ def main_ours(args, dist: Dist):
     }
     if dist.world == 1 and args.batch_steps > 0:
         line["batched"] = run_batch(args.batch_steps)
-    if dist.world == 1 and args.serving_requests > 0:
-        line["served"] = run_serving(args.serving_requests, args.serving_rate)
+    if dist.world == 1 and args.serving_window > 0:
+        line["served"] = run_served(args)
     if dist.world == 1 and not args.no_precision_check:
         line["precision_check"] = run_precision_check()
     if dist.world == 1 and args.minimizers > 0:
@@ -586,6 +798,36 @@ def main_ours(args, dist: Dist):
     if not all(f["ok"] for f in forms.values()):
         line["invalid"] = "FIRE stopped before all timed steps ran"
     return line
+
+
+def run_served(args):
+    """The serving workload: (1) the seeded stream at its own rate (20/s) for
+    ``--serving-window`` seconds of arrivals -- far above what one GPU serves,
+    so the queue grows and the latencies are those of the requests that
+    finished; (2) the scaled-rate deviation: ``--serving-scaled`` requests of
+    the same stream at about 0.8 of the measured capacity (arrival rate from
+    the per-edge steps-to-converge and the throughput of stream 1)."""
+    out = {"workload": "seeded serving stream (seed 5): Poisson arrivals, cubic edges 48..192 step 16, "
+                       "half patterned substrate + homeotropic top wall, half 1-2 colloids, one constant, "
+                       "FP32 form, FIRE to max|F| < 1e-6, HBM budget 120 GB"}
+    a = serve_stream(args.serving_rate, args.serving_window, args.serving_extra,
+                     max_active=args.serving_max_active)
+    out["stream"] = a
+    if args.serving_scaled > 0:
+        table = SERVING_ITERS_BY_EDGE or a["iterations_by_edge"]
+        cap = serving_capacity(a["site_updates_per_s"], table)
+        if np.isfinite(cap) and cap > 0:
+            rate = args.serving_utilisation * cap
+            window = args.serving_scaled / rate
+            b = serve_stream(rate, window, args.serving_scaled_extra * window,
+                             max_requests=args.serving_scaled, max_active=args.serving_max_active)
+            b["capacity_req_per_s"] = cap
+            b["target_utilisation"] = args.serving_utilisation
+            b["iterations_table"] = "committed calibration" if SERVING_ITERS_BY_EDGE else "stream 1 completions"
+            out["scaled_rate"] = b
+    p50, p99 = out.get("scaled_rate", a)["p50_s"], out.get("scaled_rate", a)["p99_s"]
+    out.update(p50_s=p50, p99_s=p99, site_updates_per_s=a["site_updates_per_s"])
+    return out
 
 
 def workload_name(size: int) -> str:
@@ -636,8 +878,22 @@ def main(argv=None):
     ap.add_argument("--precision", default="fp32,fp64,fp32_1c,fp64_1c")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=50)
-    ap.add_argument("--serving-requests", type=int, default=8)
+    ap.add_argument("--serving-window", type=float, default=100.0,
+                    help="seconds of arrivals of the served stream (0: skip serving)")
+    ap.add_argument("--serving-extra", type=float, default=10.0,
+                    help="seconds of serving after the last arrival before stopping")
     ap.add_argument("--serving-rate", type=float, default=20.0)
+    ap.add_argument("--serving-max-active", type=int, default=8)
+    ap.add_argument("--serving-scaled", type=int, default=64,
+                    help="requests of the scaled-rate stream (0: skip)")
+    ap.add_argument("--serving-utilisation", type=float, default=0.8)
+    ap.add_argument("--serving-scaled-extra", type=float, default=0.25,
+                    help="drain time of the scaled-rate stream as a fraction of its arrival window")
+    ap.add_argument("--baselines", action="store_true",
+                    help="only run the CPU-baseline plan: full minimisations of the 32^3 and 128^3 "
+                         "workloads next to the oracle, and print them")
+    ap.add_argument("--serving-calibrate", action="store_true",
+                    help="only minimise one request per edge of the served stream alone and print them")
     ap.add_argument("--minimizers", type=float, default=0.0,
                     help="seconds per method of the FIRE / GD / Nesterov comparison (0: skip)")
     ap.add_argument("--minimizer-size", type=int, default=250)
@@ -651,6 +907,16 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
+    if args.baselines:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"baselines": run_baselines()}), flush=True)
+        return
+    if args.serving_calibrate:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"serving_calibration": serving_calibrate()}), flush=True)
+        return
     dist = Dist(backend="gloo" if args.impl == "reference" else None)
     try:
         line = main_reference(args, dist) if args.impl == "reference" else main_ours(args, dist)

@@ -144,6 +144,8 @@ def lib():
         _lib.orc_eig_sym3.argtypes = [p, p, p]
         _lib.orc_order_field.argtypes = [C.POINTER(_Geometry), p, i64, p]
         _lib.orc_num_threads.restype = C.c_int
+        _lib.orc_set_num_threads.restype = C.c_int
+        _lib.orc_set_num_threads.argtypes = [C.c_int]
         _lib.orc_distortion_density.restype = d
         _lib.orc_distortion_density.argtypes = [C.POINTER(_Model), p, p]
     return _lib
@@ -156,6 +158,12 @@ def uniaxial_s0(A: float, B: float, C_: float) -> float:
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def set_num_threads(n: int) -> int:
+    """Threads of the oracle's parallel loops from now on; returns the count
+    in effect."""
+    return lib().orc_set_num_threads(int(n))
 
 
 def _ptr(a: np.ndarray):

@@ -34,6 +34,18 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* threads of the parallel loops from now on (n >= 1); returns the count in
+   effect, so that a timing can name the cores it used */
+int orc_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 /* ---- lattice helpers -------------------------------------------------- */
 
 static int64_t idx3(const orc_model *m, int x, int y, int z) {

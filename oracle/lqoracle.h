@@ -150,6 +150,7 @@ void orc_order_field(const orc_geometry *g, const double *q, int64_t N,
                      double *S);
 
 int orc_num_threads(void);
+int orc_set_num_threads(int n);
 
 #ifdef __cplusplus
 }
