@@ -133,8 +133,12 @@ typedef struct {
     double momentum;   /* LQ_MIN_NESTEROV: mu */
 } lq_fire_params;
 
+/* LQ_FIRE_STALLED: a tensor copy of the FP32 form's step did not complete
+   within its time limit (about a second; copies take microseconds); the step
+   kernel stopped and the entry point returned LQ_ECUDA.  lq_fire_reset (or a
+   new lq_minimize) starts again. */
 typedef enum { LQ_FIRE_RUNNING = 0, LQ_FIRE_CONVERGED = 1, LQ_FIRE_MAXITER = 2,
-               LQ_FIRE_DIVERGED = 3 } lq_fire_status;
+               LQ_FIRE_DIVERGED = 3, LQ_FIRE_STALLED = 4 } lq_fire_status;
 
 /* State after the last completed FIRE iteration.  max_force is the largest
    site force norm, rms_force = |F| / sqrt(N simulated sites), power = F.v
@@ -502,6 +506,18 @@ lq_status lq_set_zchunk(lq_solver *s, int zchunk);
    lattices, for testing it on small ones; results are identical).
    LQ_EINVAL for other values. */
 lq_status lq_set_index_width(lq_solver *s, int bits);
+/* Plane staging of the FP32 form's step kernel (three constants, no chiral
+   or cubic term): 0 = automatic (the faster staging measured on B300:
+   per-thread loads), 1 = per-thread loads, 2 = tensor copies, LQ_EINVAL
+   where they cannot serve (they need the lattice's x extent a multiple of
+   32 and a driver that encodes tensor maps).  In the tensor-copy staging the rows of each z plane that a
+   32 x 4 tile and its ring need arrive in shared memory as bulk tensor
+   copies completing on a barrier, instead of one load per thread and value;
+   the arithmetic is the same and so are the results, bit for bit. */
+lq_status lq_set_staging(lq_solver *s, int mode);
+/* *uses_tensor_copies = 1 when the solver's next FIRE step runs the
+   tensor-copy staging, else 0. */
+lq_status lq_get_staging(lq_solver *s, int *uses_tensor_copies);
 /* Bytes of device memory held by the solver. */
 size_t lq_device_bytes(const lq_solver *s);
 

@@ -23,7 +23,9 @@ constexpr uint8_t M_ANCH = 1u << 1;  // carries an anchoring record
 __host__ __device__ constexpr uint8_t m_fwd(int k) { return (uint8_t)(1u << (2 + 2 * k)); }
 __host__ __device__ constexpr uint8_t m_bwd(int k) { return (uint8_t)(1u << (3 + 2 * k)); }
 
-enum : int { FIRE_RUNNING = 0, FIRE_CONVERGED = 1, FIRE_MAXITER = 2, FIRE_DIVERGED = 3 };
+// FIRE_STALLED: a tensor copy of the step did not complete within its time
+// limit; the step kernel stopped (the entry point returns LQ_ECUDA)
+enum : int { FIRE_RUNNING = 0, FIRE_CONVERGED = 1, FIRE_MAXITER = 2, FIRE_DIVERGED = 3, FIRE_STALLED = 4 };
 
 // Anchoring record of one boundary site.  kind 1: Nobili-Durand, a = q0 (5
 // components of Q0), qi = the same in the fixed-point Q format of the FP32

@@ -22,6 +22,7 @@ struct StepLaunch {
     int zchunk, force_only, fp32, three;
     int idx64;                // 64-bit element indices even where 32 bits would do
     int wide;                 // 64-wide tiles (wide_tiles)
+    int tma;                  // FP32 form: plane rows staged by tensor copies
 };
 
 // one block's share of a batched step: lattice, tile, z range, and its
@@ -32,6 +33,10 @@ struct WorkItem {
 
 dim3 step_grid(const LatticeDev &L, int zchunk, int tx, int ty);
 bool wide_tiles(int fp32, int three, int nx);
+// tensor-copy staging of the FP32 form: the driver offers the tensor-map
+// encoder; the lattice's x extent is a multiple of 32
+bool tma_staging_available();
+bool tma_staging_fits(const LatticeDev &L);
 void step_tile(int fp32, int three, int nx, int *tx, int *ty);
 cudaError_t prepare_fire_step(int fp32, int three);
 cudaError_t launch_fire_step(const StepLaunch &sl, cudaStream_t stream);

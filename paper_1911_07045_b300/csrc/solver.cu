@@ -116,6 +116,8 @@ StepLaunch make_launch(lq_solver *s, int force_only) {
     sl.ext = s->ext;
     sl.idx64 = s->idx64;
     sl.wide = wide_tiles(s->fp32, s->three, s->L.nx);
+    sl.tma = s->staging == 2 && s->fp32 && s->three && !s->ext && tma_staging_fits(s->L) &&
+             tma_staging_available();
     return sl;
 }
 
@@ -768,6 +770,8 @@ lq_status lq_step(lq_solver *s, const lq_fire_params *p, int64_t n, lq_result *o
     r = sync_state(s);
     if (r != LQ_OK) return r;
     fill_result(s, out, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+    if (s->st_host->status == FIRE_STALLED)
+        return fail(s, LQ_ECUDA, "a tensor copy of the step did not complete (FIRE stopped)");
     return LQ_OK;
 }
 
@@ -826,6 +830,7 @@ lq_status lq_minimize(lq_solver *s, const lq_fire_params *p, lq_result *out) {
     if (timed_out && s->st_host->status == FIRE_RUNNING) ret = LQ_ETIMEOUT;
     else if (s->st_host->status == FIRE_MAXITER) ret = LQ_ENOTCONVERGED;
     else if (s->st_host->status == FIRE_DIVERGED) ret = LQ_EDIVERGED;
+    else if (s->st_host->status == FIRE_STALLED) ret = LQ_ECUDA;
     double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     fill_result(s, out, secs);
     if (out) {
@@ -835,6 +840,7 @@ lq_status lq_minimize(lq_solver *s, const lq_fire_params *p, lq_result *out) {
     if (ret == LQ_ETIMEOUT) fail(s, ret, "wall-clock limit reached");
     if (ret == LQ_ENOTCONVERGED) fail(s, ret, "max_iter reached");
     if (ret == LQ_EDIVERGED) fail(s, ret, "FIRE diverged (non-finite reduction)");
+    if (ret == LQ_ECUDA) fail(s, ret, "a tensor copy of the step did not complete (FIRE stopped)");
     return ret;
 }
 
@@ -918,6 +924,26 @@ lq_status lq_set_index_width(lq_solver *s, int bits) {
     s->idx64 = bits == 64;
     ++s->gen;          // batches pick their kernel instantiation again
     drop_graph(s);
+    return LQ_OK;
+}
+
+lq_status lq_set_staging(lq_solver *s, int mode) {
+    if (check_solver(s)) return LQ_EINVAL;
+    if (mode < 0 || mode > 2) return fail(s, LQ_EINVAL, "staging mode must be 0, 1 or 2");
+    if (mode == 2 && !(s->fp32 && s->three && !s->ext && tma_staging_fits(s->L) && tma_staging_available()))
+        return fail(s, LQ_EINVAL,
+                    "tensor-copy staging needs the FP32 form, three constants without the chiral or cubic "
+                    "terms, an x extent that is a multiple of 32 and a driver with the tensor-map encoder");
+    if (mode != s->staging) {
+        s->staging = mode;
+        drop_graph(s);       // captured launches name the kernel of the old mode
+    }
+    return LQ_OK;
+}
+
+lq_status lq_get_staging(lq_solver *s, int *uses_tensor_copies) {
+    if (check_solver(s) || !uses_tensor_copies) return LQ_EINVAL;
+    *uses_tensor_copies = make_launch(s, 0).tma;
     return LQ_OK;
 }
 

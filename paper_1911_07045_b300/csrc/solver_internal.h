@@ -59,6 +59,7 @@ struct lq_solver {
     bool fire_ready = false;
     int zchunk = 0;                 // 0 = automatic
     int idx64 = 0;                  // 64-bit element indices forced (lq_set_index_width)
+    int staging = 0;                // lq_set_staging: 0 automatic, 1 loads, 2 tensor copies
 
     cudaGraphExec_t gexec = nullptr;
     int graph_k = 0;

@@ -38,6 +38,8 @@
 // NEXT kernel: v_mix = cv v + cF F with (cv, cF, dt) written by the last
 // block of the previous kernel.  The first kernel after a reset (dt = 0,
 // cv = cF = 0) only evaluates F(q0).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cfloat>
 #include <cstdio>
 
@@ -1117,15 +1119,110 @@ __device__ __forceinline__ void regular_force(Smem<T, TX, TY> &S, int lx, int ly
     (void)L2q; (void)L3q;
 }
 
+// ---- tensor-memory-access (TMA) staging of the FP32 form --------------------
+// The rows of a plane that a tile needs -- its own TY rows and the ring rows
+// above and below, TX sites each -- arrive in shared memory by bulk tensor
+// copies (one per row and state array, all five components at once),
+// completing on an mbarrier per buffer; only the 2 TY + 4 ring sites left and
+// right of the tile (whose x offset is not 16-byte aligned) use per-thread
+// loads.  The copies name only this GPU's own arrays and are never multicast.
+
+// tensor maps of one lattice's state: q, v, F of both ping-pong buffers as
+// 4-D (x, y, z, component) tensors with a (TX, 1, 1, 5) box, the mask as a
+// 3-D (x, y, z) tensor with a (TX, 1, 1) box
+struct TmaMaps {
+    CUtensorMap q[2], v[2], f[2];
+    CUtensorMap m;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// make the initialised barriers visible to the copy engine
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// wait for the phase of the given parity; gives up after about one second
+// (a copy takes microseconds) and returns false
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > 1000000000ull) return false;
+    }
+}
+// order this thread's earlier shared-memory accesses before later copies
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int x, int y, int z, int c,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(c), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// shared-memory layout of the raw plane buffers: RB buffers, each with the
+// TY + 2 rows of q, v, F (five components of TX sites: a multiple of 128 bytes)
+// and the TY + 2 mask rows (TX bytes each, in 128-byte slots)
+template <int TX, int TY>
+struct RawLayout {
+    static constexpr int RB = 3;                                    // buffers
+    static constexpr int ROWS = TY + 2;
+    static constexpr int ROWB = 5 * TX * 4;                         // one row of one array
+    static constexpr int MROWB = 128;
+    static constexpr int BYTES = 3 * ROWS * ROWB + ROWS * MROWB;    // one buffer
+    static constexpr unsigned TX_BYTES = 3 * ROWS * ROWB + ROWS * TX;   // delivered per plane
+    static constexpr int TOTAL = 128 + RB * BYTES + RB * 8;         // with alignment slack and barriers
+    static_assert(ROWB % 128 == 0, "row boxes on 128-byte boundaries");
+};
+
 // One block's work for one lattice: the tile with origin (bx*TX, by*TY),
 // planes [z0, z1), block number bid of the nblk blocks of that lattice's
 // step (its partial-sum slot).  Shared memory is the caller's.
 // FORM: 0 one-constant, 1 three-constant (L1, L2, L3), 2 three-constant
 // with the chiral L4 and cubic L6 terms
-template <typename T, int FORM, int TX, int TY, typename I>
+// TMA: the plane rows arrive by tensor copies (FP32 form, lattices whose x
+// extent is a multiple of TX; tm holds the tensor maps) instead of per-thread
+// loads; the arithmetic of every site is the same, so are the results.
+template <typename T, int FORM, int TX, int TY, typename I, bool TMA = false>
 __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int by, int z0, int z1,
                                           int nblk, int bid, unsigned char *smem_raw, double *red,
-                                          int *am_last_p) {
+                                          int *am_last_p, const TmaMaps *tm = nullptr) {
     constexpr int NT = TX * TY;
     constexpr int NSLOT = 5;
     constexpr bool THREE = FORM >= 1;
@@ -1138,9 +1235,20 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
     S.X = reinterpret_cast<T *>(smem_raw + NSLOT * SM::SLOT_BYTES);
     S.D = S.X + (THREE ? 2 * 5 * SM::PL : 0);
     constexpr bool DIFFS = sizeof(T) == 8 && THREE;
-    constexpr bool WCACHE = keeps_w<T, FORM>();
+    // the TMA form has the registers to keep the kick's old-state part in
+    // every distortion form (no prefetch registers)
+    constexpr bool WCACHE = keeps_w<T, FORM>() || TMA;
     S.W = S.D + (DIFFS ? 2 * 2 * 5 * SM::PL : 0);
     S.M = reinterpret_cast<uint8_t *>(S.W + (WCACHE ? 3 * 5 * NT : 0));
+    using RL = RawLayout<TX, TY>;
+    unsigned char *raw_base = nullptr;
+    uint64_t *bars = nullptr;
+    if constexpr (TMA) {
+        static_assert(sizeof(T) == 4, "tensor-copy staging serves the FP32 form");
+        const uintptr_t a = reinterpret_cast<uintptr_t>(S.M + NSLOT * SM::PL);
+        raw_base = reinterpret_cast<unsigned char *>((a + 127) & ~uintptr_t(127));
+        bars = reinterpret_cast<uint64_t *>(raw_base + RL::RB * RL::BYTES);
+    }
     const LatticeDev L = args.L;
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const int x0 = bx * TX, y0 = by * TY;
@@ -1181,16 +1289,27 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
     // the old force's weight in the kick, cF + dt/2, rounded once
     const T cFh = fo_mode ? T(0) : T(args.st->cF + args.st->c_kick);
 
-    // ring sites of a staged plane: top row, bottom row, left/right columns
+    // ring sites of a staged plane: top row, bottom row, left/right columns.
+    // TMA: threads [0, 2 TX) take the row sites above and below the tile
+    // (from the copied rows), threads [2 TX, 2 TX + 2 (TY + 2)) the columns
+    // left and right of it, corners included (per-thread loads)
     constexpr int NRING = 2 * SM::SX + 2 * TY;
     static_assert(NRING <= NT, "one ring site per thread");
     int rx = -1, ry = -1;
-    if ((int)threadIdx.x < NRING) {
+    if constexpr (TMA) {
+        const int r = threadIdx.x;
+        if (r < TX) { rx = r + 1; ry = 0; }
+        else if (r < 2 * TX) { rx = r - TX + 1; ry = SM::SY - 1; }
+        else if (r < 2 * TX + 2 * SM::SY) { const int q = r - 2 * TX; rx = (q & 1) ? SM::SX - 1 : 0; ry = q >> 1; }
+    } else if ((int)threadIdx.x < NRING) {
         int r = threadIdx.x;
         if (r < SM::SX) { rx = r; ry = 0; }
         else if (r < 2 * SM::SX) { rx = r - SM::SX; ry = SM::SY - 1; }
         else { r -= 2 * SM::SX; rx = (r & 1) ? SM::SX - 1 : 0; ry = 1 + (r >> 1); }
     }
+    // TMA: row sites come from shared memory, column sites by loads
+    const bool ring_row = TMA && (int)threadIdx.x < 2 * TX;
+    const bool ring_col = rx >= 0 && !ring_row;
     // in-plane offsets of the own and ring sites (-1: outside the lattice)
     auto xy_of = [&](int sx, int sy) -> long long {
         int X = wrap_coord(x0 + sx - 1, L.nx, L.px);
@@ -1260,7 +1379,111 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
     auto slot_of = [&](int z) { return ((z % NSLOT) + NSLOT) % NSLOT; };
 
     Raw pf_own, pf_ring;
-    {
+    // TMA: plane p (z0 - 1 <= p <= z1) is the k-th of the block, k = p - z0 + 1,
+    // delivered into buffer k mod RB; its barrier phase has parity (k / RB) & 1
+    __shared__ int s_stall;
+    int issued = z0 - 2;          // last plane whose copies were issued
+    auto issue = [&](int p) {     // warp 0: the copies of plane p
+        if constexpr (TMA) {
+            if (threadIdx.x >= 32 || p > z1) return;
+            const int k = p - (z0 - 1), b = k % RL::RB;
+            const int lane = threadIdx.x;
+            if (lane == 0) {
+                fence_proxy_async();
+                mbar_arrive_expect_tx(&bars[b], RL::TX_BYTES);
+            }
+            __syncwarp();
+            if (lane < 4 * RL::ROWS) {
+                const int r = lane % RL::ROWS, a = lane / RL::ROWS;   // a: q, v, F, mask
+                // coordinates outside the lattice (open axes, rows past a
+                // ragged edge) read zeros: mask 0, a site that is not there
+                int Y = wrap_coord(y0 - 1 + r, L.ny, L.py);
+                int Z = wrap_coord(p, L.nz, L.pz);
+                if (Y < 0) Y = -1;
+                if (Z < 0) Z = -1;
+                unsigned char *dst = raw_base + b * RL::BYTES;
+                const int cur = args.st->cur;
+                if (a < 3) {
+                    const CUtensorMap *map = a == 0 ? &tm->q[cur] : (a == 1 ? &tm->v[cur] : &tm->f[cur]);
+                    tma_load_4d(dst + (a * RL::ROWS + r) * RL::ROWB, map, x0, Y, Z, 0, &bars[b]);
+                } else {
+                    tma_load_3d(dst + 3 * RL::ROWS * RL::ROWB + r * RL::MROWB, &tm->m, x0, Y, Z, &bars[b]);
+                }
+            }
+        }
+        (void)p;
+    };
+    // TMA: the site at (row, x) of the copied rows of plane p
+    auto raw_site = [&](int p, int row, int x, Raw &r) {
+        if constexpr (TMA) {
+            const int k = p - (z0 - 1);
+            const unsigned char *b = raw_base + (k % RL::RB) * RL::BYTES;
+            const QS *q = reinterpret_cast<const QS *>(b + row * RL::ROWB);
+            const T *v = reinterpret_cast<const T *>(b + (RL::ROWS + row) * RL::ROWB);
+            const T *f = reinterpret_cast<const T *>(b + (2 * RL::ROWS + row) * RL::ROWB);
+#pragma unroll
+            for (int c = 0; c < 5; ++c) { r.q[c] = q[c * TX + x]; r.v[c] = v[c * TX + x]; r.f[c] = f[c * TX + x]; }
+            r.m = b[3 * RL::ROWS * RL::ROWB + row * RL::MROWB + x];
+        }
+        (void)p; (void)row; (void)x; (void)r;
+    };
+    // TMA: wait for plane p; a wait that gives up marks the block stalled
+    auto wait_plane = [&](int p) {
+        if constexpr (TMA) {
+            const int k = p - (z0 - 1);
+            if (!mbar_wait_bounded(&bars[k % RL::RB], (k / RL::RB) & 1)) s_stall = 1;
+        }
+        (void)p;
+    };
+    // TMA: stage plane p into its slot from the copied rows (own site and the
+    // row ring sites) and, for the column ring sites, from registers
+    auto stage_plane = [&](int p, const Raw &col, bool own_w) {
+        Raw r;
+        raw_site(p, ly, tx, r);
+        commit(slot_of(p), lx, ly, r, true);
+        if (own_w) keep_w(p, r);
+        if (ring_row) {
+            raw_site(p, ry, rx - 1, r);
+            commit(slot_of(p), rx, ry, r, false);
+        } else if (ring_col) {
+            commit(slot_of(p), rx, ry, col, false);
+        }
+    };
+    // after a barrier: give up the whole block if any wait gave up; the
+    // copies in flight are awaited (bounded) before the block leaves
+    auto stalled = [&]() -> bool {
+        if constexpr (TMA) {
+            if (!s_stall) return false;
+            for (int p = issued; p > issued - RL::RB && p >= z0 - 1; --p) {
+                const int k = p - (z0 - 1);
+                mbar_wait_bounded(&bars[k % RL::RB], (k / RL::RB) & 1);
+            }
+            if (threadIdx.x == 0 && !fo_mode) args.st->status = FIRE_STALLED;
+            return true;
+        }
+        return false;
+    };
+
+    if constexpr (TMA) {
+        if (threadIdx.x == 0) {
+            s_stall = 0;
+            for (int b = 0; b < RL::RB; ++b) mbar_init(&bars[b], 1);
+            mbar_init_fence();
+        }
+        __syncthreads();
+        for (int p = z0 - 1; p < z0 - 1 + RL::RB; ++p) issue(p);
+        issued = min(z0 - 2 + RL::RB, z1);
+        for (int p = z0 - 1; p <= z0 + 1; ++p) {
+            Raw col;
+            if (ring_col) fetch(in_ring, xy_ring, p, col);
+            wait_plane(p);
+            stage_plane(p, col, p >= z0);
+            __syncthreads();     // every thread is done with the buffer of plane p
+            if (stalled()) return;
+            if (p + RL::RB <= z1) { issue(p + RL::RB); issued = p + RL::RB; }
+        }
+        if (ring_col) fetch(in_ring, xy_ring, z0 + 2, pf_ring);
+    } else {
         Raw r;
         for (int p = -1; p <= 1; ++p) {
             fetch(in_own, xy_own, z0 + p, r);
@@ -1273,8 +1496,8 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
         }
         fetch(in_own, xy_own, z0 + 2, pf_own);
         if (rx >= 0) fetch(in_ring, xy_ring, z0 + 2, pf_ring);
+        __syncthreads();   // the first regularity check reads neighbours' masks
     }
-    __syncthreads();   // the first regularity check reads neighbours' masks
 
     // central differences of plane `pz` (slot s_pl, the planes below and
     // above in s_dn, s_up) into the difference slot pz & 1: D_z at the tile,
@@ -1318,14 +1541,22 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
     int sm = slot_of(z0 - 1), sc = slot_of(z0), sp = slot_of(z0 + 1), s2 = slot_of(z0 + 2);
     for (int z = z0; z < z1; ++z) {
         // pipeline: plane z+2 into its slot, plane z+3 in flight
-        if (z + 2 <= z1) {
-            commit(s2, lx, ly, pf_own, true);
-            if (z + 2 < z1) keep_w(z + 2, pf_own);
-            if (rx >= 0) commit(s2, rx, ry, pf_ring, false);
-        }
-        if (z + 3 <= z1) {
-            fetch(in_own, xy_own, z + 3, pf_own);
-            if (rx >= 0) fetch(in_ring, xy_ring, z + 3, pf_ring);
+        if constexpr (TMA) {
+            if (z + 2 <= z1) {
+                wait_plane(z + 2);
+                stage_plane(z + 2, pf_ring, z + 2 < z1);
+            }
+            if (z + 3 <= z1 && ring_col) fetch(in_ring, xy_ring, z + 3, pf_ring);
+        } else {
+            if (z + 2 <= z1) {
+                commit(s2, lx, ly, pf_own, true);
+                if (z + 2 < z1) keep_w(z + 2, pf_own);
+                if (rx >= 0) commit(s2, rx, ry, pf_ring, false);
+            }
+            if (z + 3 <= z1) {
+                fetch(in_own, xy_own, z + 3, pf_own);
+                if (rx >= 0) fetch(in_ring, xy_ring, z + 3, pf_ring);
+            }
         }
         const uint8_t m0 = S.m(sc, lx, ly);
         const bool own = valid && (m0 & M_SIM);
@@ -1351,6 +1582,11 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
         }
         // the barrier publishes plane z+2 and decides the path of this plane
         const bool all_reg = __syncthreads_and(reg) != 0;
+        if constexpr (TMA) {
+            // every thread is done with the buffer of plane z+2: refill it
+            if (stalled()) return;
+            if (z + 2 + RL::RB <= z1) { issue(z + 2 + RL::RB); issued = z + 2 + RL::RB; }
+        }
         // the next plane's central differences: planes z .. z+2 are published,
         // and the slot (z+1) & 1 was last read by the previous plane's force
         if constexpr (shared_diffs<T, FORM>()) {
@@ -1668,6 +1904,23 @@ fire_step_kernel(StepArgs<T> args) {
                                   &am_last);
 }
 
+// one FIRE iteration of one lattice with the plane rows staged by tensor
+// copies (FP32 form); three blocks per SM (the raw plane buffers take shared
+// memory; the registers that prefetched planes in the other kernel are free)
+template <typename T, int FORM, int TX, int TY, typename I>
+__global__ void __launch_bounds__(TX * TY, 3)
+fire_step_tma_kernel(const __grid_constant__ StepArgs<T> args, const __grid_constant__ TmaMaps maps) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[4 * (TX * TY / 32)];
+    __shared__ int am_last;
+    const int z0 = blockIdx.z * args.zchunk;
+    const int z1 = min(z0 + args.zchunk, args.L.nz);
+    const int nblk = gridDim.x * gridDim.y * gridDim.z;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    step_tile<T, FORM, TX, TY, I, true>(args, blockIdx.x, blockIdx.y, z0, z1, nblk, bid, smem_raw, red,
+                                        &am_last, &maps);
+}
+
 // one FIRE iteration of every lattice of a batch: a persistent grid strides
 // over the work items (lattice, tile, z chunk); each lattice keeps its own
 // partial sums, last-block ticket and FIRE state, so a lattice advances
@@ -1689,7 +1942,7 @@ fire_batch_kernel(const StepArgs<T> *__restrict__ args, const WorkItem *__restri
 
 // ---- host launchers ---------------------------------------------------------
 
-template <typename T, int FORM, int TX, int TY>
+template <typename T, int FORM, int TX, int TY, bool TMA = false>
 static size_t step_smem_bytes() {
     constexpr bool THREE = FORM >= 1;
     using SM = Smem<T, TX, TY>;
@@ -1697,8 +1950,63 @@ static size_t step_smem_bytes() {
     constexpr bool DIFFS = sizeof(T) == 8 && THREE;   // shared_diffs (form 1; unused by form 2)
     size_t b = 5 * (size_t)SM::SLOT_BYTES + sizeof(T) * (THREE ? 2 * 5 * PL : 0) +
                sizeof(T) * (DIFFS ? 2 * 2 * 5 * PL : 0) + 5 * PL +
-               (keeps_w<T, FORM>() ? sizeof(T) * 3 * 5 * TX * TY : 0);
+               (keeps_w<T, FORM>() || TMA ? sizeof(T) * 3 * 5 * TX * TY : 0);
+    if (TMA) b += RawLayout<TX, TY>::TOTAL;
     return (b + 15) & ~size_t(15);
+}
+
+// ---- tensor maps (host) ---------------------------------------------------------
+
+// the driver's tensor-map encoder, found through the runtime (no link to the
+// driver library); null where the driver has none
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+bool tma_staging_available() { return tensor_map_encoder() != nullptr; }
+
+// lattices the tensor-copy staging serves: FP32 form, x extent a multiple of
+// the 32-site tile (row boxes start on 16-byte boundaries and never cross the
+// x edge; 16-byte mask rows)
+bool tma_staging_fits(const LatticeDev &L) { return L.nx % 32 == 0 && L.nx >= 32; }
+
+template <typename T, int TX>
+static bool encode_maps(const StepLaunch &sl, TmaMaps &m) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const LatticeDev &L = sl.L;
+    const cuuint64_t nx = L.nx, ny = L.ny, nz = L.nz;
+    const cuuint64_t dims4[4] = {nx, ny, nz, 5};
+    const cuuint64_t str4[3] = {nx * sizeof(T), nx * ny * sizeof(T), nx * ny * nz * sizeof(T)};
+    const cuuint32_t box4[4] = {TX, 1, 1, 5};
+    const cuuint32_t one[4] = {1, 1, 1, 1};
+    auto state = [&](CUtensorMap *out, void *base, CUtensorMapDataType dt) {
+        return enc(out, dt, 4, base, dims4, str4, box4, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    for (int b = 0; b < 2; ++b) {
+        if (!state(&m.q[b], sl.q[b], CU_TENSOR_MAP_DATA_TYPE_INT32)) return false;
+        if (!state(&m.v[b], sl.v[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32)) return false;
+        if (!state(&m.f[b], sl.F[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32)) return false;
+    }
+    const cuuint64_t dims3[3] = {nx, ny, nz};
+    const cuuint64_t str3[2] = {nx, nx * ny};
+    const cuuint32_t box3[3] = {TX, 1, 1};
+    return enc(&m.m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t *>(sl.g.mask), dims3, str3, box3, one,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <typename T>
@@ -1734,9 +2042,18 @@ template <typename T, int FORM, int TX, int TY, typename I>
 static cudaError_t launch_impl(const StepLaunch &sl, cudaStream_t stream) {
     StepArgs<T> a;
     pack_args<T>(sl, a);
+    dim3 grid = step_grid(sl.L, sl.zchunk, TX, TY);
+    if constexpr (sizeof(T) == 4 && TX == 32) {
+        if (sl.tma && !sl.force_only) {
+            TmaMaps maps;
+            if (!encode_maps<T, TX>(sl, maps)) return cudaErrorInvalidValue;
+            fire_step_tma_kernel<T, FORM, TX, TY, I>
+                <<<grid, TX * TY, step_smem_bytes<T, FORM, TX, TY, true>(), stream>>>(a, maps);
+            return cudaGetLastError();
+        }
+    }
     size_t smem = step_smem_bytes<T, FORM, TX, TY>();
     auto kern = fire_step_kernel<T, FORM, TX, TY, I>;
-    dim3 grid = step_grid(sl.L, sl.zchunk, TX, TY);
     kern<<<grid, TX * TY, smem, stream>>>(a);
     return cudaGetLastError();
 }
@@ -1788,6 +2105,12 @@ struct PrepareStep {
         cudaError_t e = cudaFuncSetAttribute(fire_step_kernel<T, FORM, 32, TY, I>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)step_smem_bytes<T, FORM, 32, TY>());
+        if constexpr (sizeof(T) == 4) {
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(fire_step_tma_kernel<T, FORM, 32, TY, I>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)step_smem_bytes<T, FORM, 32, TY, true>());
+        }
         if constexpr (sizeof(T) == 4 && FORM == 0) {
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(fire_step_kernel<T, FORM, 64, TY, I>,

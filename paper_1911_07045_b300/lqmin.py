@@ -24,7 +24,7 @@ STATUS_NAMES = ["LQ_OK", "LQ_EINVAL", "LQ_ENOMEM", "LQ_ECUDA", "LQ_ENOTCONVERGED
                 "LQ_EDIVERGED", "LQ_EBUSY"]
 LQ_FP64, LQ_FP32_BULK_FP64_RED = 0, 1
 ND_HOMEOTROPIC, ND_ORIENTED, FG_PLANAR = 0, 1, 2
-FIRE_RUNNING, FIRE_CONVERGED, FIRE_MAXITER, FIRE_DIVERGED = 0, 1, 2, 3
+FIRE_RUNNING, FIRE_CONVERGED, FIRE_MAXITER, FIRE_DIVERGED, FIRE_STALLED = 0, 1, 2, 3, 4
 LQ_MIN_FIRE, LQ_MIN_GD, LQ_MIN_NESTEROV = 0, 1, 2
 
 # every symbol include/lqmin.h declares
@@ -43,7 +43,7 @@ EXPORTS = [
     "lq_add_boundary_text", "lq_load_boundary_file", "lq_object_count", "lq_move_object",
     "lq_clear_objects", "lq_set_material", "lq_clone", "lq_pmf_sweep", "lq_init_dipolar",
     "lq_frank_to_landau", "lq_set_index_width", "lq_inject_fault", "lq_bounds_check_hits",
-    "lq_fp64_fma_rate",
+    "lq_fp64_fma_rate", "lq_set_staging", "lq_get_staging",
 ]
 
 
@@ -186,6 +186,8 @@ def load(path: str = LIB_PATH):
         "lq_inject_fault": (C.c_int, [C.c_int, i64]),
         "lq_bounds_check_hits": (C.c_int, [C.POINTER(C.c_uint32)]),
         "lq_fp64_fma_rate": (C.c_int, [i64, C.POINTER(d)]),
+        "lq_set_staging": (C.c_int, [S, C.c_int]),
+        "lq_get_staging": (C.c_int, [S, C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -529,6 +531,15 @@ class Solver:
 
     def set_zchunk(self, z):
         self._ck(self.lib.lq_set_zchunk(self.h, int(z)))
+
+    def set_staging(self, mode):
+        """0 automatic, 1 per-thread loads, 2 tensor copies (lq_set_staging)."""
+        self._ck(self.lib.lq_set_staging(self.h, int(mode)))
+
+    def uses_tensor_copies(self) -> bool:
+        out = C.c_int()
+        self._ck(self.lib.lq_get_staging(self.h, C.byref(out)))
+        return bool(out.value)
 
     def set_index_width(self, bits):
         self._ck(self.lib.lq_set_index_width(self.h, int(bits)))
