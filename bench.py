@@ -185,7 +185,8 @@ class ClockSampler:
 
 # ---- our arm ------------------------------------------------------------------------
 
-def run_form(precision: str, L: int, steps: int, warmup: int, dist: Dist, sampler_gpu: int):
+def run_form(precision: str, L: int, steps: int, warmup: int, dist: Dist, sampler_gpu: int,
+             staging: int = 0):
     """One precision form on the L^3 workload; a "_1c" suffix runs the same
     geometry with one-constant elasticity (L2 = L3 = 0), a "_chiral" suffix
     adds the chiral term L4 = 0.05 and "_cubic" also the cubic term L6 = 0.3
@@ -204,6 +205,9 @@ def run_form(precision: str, L: int, steps: int, warmup: int, dist: Dist, sample
         s.add_objects(cfg["objects"])
     else:
         s = lqmin.solver_for(cfg, precision=prec, stream=stream.cuda_stream)
+    if staging and prec == lqmin.LQ_FP32_BULK_FP64_RED and cfg.get("L2", 0.0) != 0.0 \
+            and not (precision.endswith("_chiral") or precision.endswith("_cubic")):
+        s.set_staging(staging)
     nsim, nrec = s.geometry_info()
     s.init_random_uniaxial(cfg["seed"])
     # fixed-step run: a tolerance of 0 never converges, so every step is done
@@ -724,7 +728,7 @@ def main_ours(args, dist: Dist):
         # the FP64 form is ~13x slower: a tenth of the steps, but at least 10
         # (half a second at 512^3), keeps its timed region long enough to time
         k = args.steps if prec.startswith("fp32") else max(10, args.steps // 10)
-        forms[prec] = run_form(prec, args.size, k, args.warmup, dist, dist.local)
+        forms[prec] = run_form(prec, args.size, k, args.warmup, dist, dist.local, args.staging)
     fp64_rate = None
     if any(not k.startswith("fp32") for k in forms):
         from paper_1911_07045_b300 import lqmin
@@ -877,6 +881,9 @@ def main(argv=None):
     ap.add_argument("--size", type=int, default=512)
     ap.add_argument("--precision", default="fp32,fp64,fp32_1c,fp64_1c")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--staging", type=int, default=0, choices=[0, 1, 2],
+                    help="plane staging of the FP32 three-constant step: 0 automatic, 1 per-thread "
+                         "loads, 2 tensor copies (lq_set_staging)")
     ap.add_argument("--batch-steps", type=int, default=50)
     ap.add_argument("--serving-window", type=float, default=100.0,
                     help="seconds of arrivals of the served stream (0: skip serving)")
