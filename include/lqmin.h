@@ -445,6 +445,45 @@ lq_status lq_server_wait(lq_server *sv, uint64_t ticket, double timeout_s, lq_re
                          double *S_out);
 lq_status lq_server_stats_get(lq_server *sv, lq_server_stats *out);
 
+/* ---- one lattice over several GPUs: z slabs ----------------------------------------- */
+
+/* Section III.B decomposes the lattice into sub-domains with halos, and
+   FIRE's power and norms (Algorithm 1) become sums over every sub-domain.
+   Here the sub-domains are slabs of z planes, one per GPU (one rank each).
+   lq_slab_create cuts planes [z_lo, z_hi) of a solver of the whole lattice
+   (built on each rank; only its geometry is used -- its masks and anchoring
+   records, so that every neighbour bit is the whole lattice's) into a new
+   solver on the current device with one halo plane below and one above:
+   its lattice is nx x ny x (z_hi - z_lo + 2), open in z, its own planes
+   1 .. z_hi - z_lo.  Its Q is set with lq_set_q / lq_set_q_device on all
+   its planes (halos included, taken from the whole lattice with its
+   periodicity) and read with lq_get_q.  A slab refuses lq_step,
+   lq_minimize, lq_fire_reset, objects, materials, clones and batches.
+   LQ_EINVAL for planes outside [0, nz), an empty slab, or a slab of a slab.
+   One FIRE iteration of the decomposed lattice, on every slab:
+     lq_slab_step(s, local)       the fused step over the own planes; local =
+                                  the slab's (P, |F|^2, |v|^2, largest site |F|^2);
+     total = (sum, sum, sum, max) of local over every slab, in FP64;
+     lq_slab_finish(s, total, out) the FIRE scalar update from total, the same
+                                  on every slab; out as lq_step's (may be NULL;
+                                  its rms_force uses the slab's own site count);
+     lq_slab_get_planes / lq_slab_set_halos  the first and last own planes go to
+                                  the neighbouring slabs' upper and lower halos.
+   lq_slab_start(s, p, local) starts FIRE (v = 0, F = F(q0)) the same way, to be
+   followed by lq_slab_finish and the halo exchange.  Plane buffers are host
+   memory of lq_slab_plane_bytes bytes: q, v, F, each five components of the
+   nx*ny sites of the plane, x fastest, in the solver's storage format (FP64
+   form: doubles; FP32 form: q as 32-bit fixed point, q = n * 2^-28, v and F
+   as floats).  NULL skips a plane (a halo beyond an open z edge, which holds
+   no sites). */
+lq_status lq_slab_create(lq_solver *whole, int z_lo, int z_hi, lq_solver **out);
+lq_status lq_slab_start(lq_solver *s, const lq_fire_params *p, double local[4]);
+lq_status lq_slab_step(lq_solver *s, double local[4]);
+lq_status lq_slab_finish(lq_solver *s, const double total[4], lq_result *out);
+lq_status lq_slab_plane_bytes(const lq_solver *s, size_t *bytes);
+lq_status lq_slab_get_planes(lq_solver *s, void *lower_own, void *upper_own);
+lq_status lq_slab_set_halos(lq_solver *s, const void *below, const void *above);
+
 /* ---- without allocation ------------------------------------------------------------ */
 
 /* The paper has no counterpart to this call; it exists for callers that cannot

@@ -264,6 +264,8 @@ lq_status batch_set_members(lq_batch *b, lq_solver *const *solvers, int n) {
         if (!solvers[l] || solvers[l]->device != b->device || solvers[l]->fp32 != b->fp32 ||
             solvers[l]->three != b->three)
             return bfail(b, LQ_EINVAL, "one device, one precision, one distortion form per batch");
+    for (int l = 0; l < n; ++l)
+        if (solvers[l]->slab) return bfail(b, LQ_EINVAL, "a slab of a decomposed lattice cannot join a batch");
     cudaSetDevice(b->device);
     drop_batch_graph(b);
     b->tables_ok = false;

@@ -23,6 +23,8 @@ struct StepLaunch {
     int idx64;                // 64-bit element indices even where 32 bits would do
     int wide;                 // 64-wide tiles (wide_tiles)
     int tma;                  // FP32 form: plane rows staged by tensor copies
+    int zbeg = 0, zend = 0;   // planes updated (zend 0: all); a slab owns [zbeg, zend)
+    int reduce_only = 0;      // slab: the sums stay in the FIRE state (fire_apply)
 };
 
 // one block's share of a batched step: lattice, tile, z range, and its
@@ -40,6 +42,8 @@ bool tma_staging_fits(const LatticeDev &L);
 void step_tile(int fp32, int three, int nx, int *tx, int *ty);
 cudaError_t prepare_fire_step(int fp32, int three);
 cudaError_t launch_fire_step(const StepLaunch &sl, cudaStream_t stream);
+// the FIRE scalar update with sums taken over every slab of a lattice
+cudaError_t fire_apply(FireDev *st, const double sums[4], cudaStream_t stream);
 
 // true when the state arrays of a lattice of N sites are indexed in 32 bits
 bool step_index32(long long N);

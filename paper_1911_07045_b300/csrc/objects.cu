@@ -213,6 +213,7 @@ lq_status lq_frank_to_landau(double K1, double K2, double K3, double K24, double
 
 lq_status lq_set_material(lq_solver *s, const lq_material *mat) {
     if (check_solver(s)) return LQ_EINVAL;
+    if (s->slab) return fail(s, LQ_EINVAL, "a slab takes its geometry and material from the whole lattice");
     if (!mat) return fail(s, LQ_EINVAL, "null material");
     double S0 = 0;
     if (const char *why = validate_material(mat, &S0)) return fail(s, LQ_EINVAL, "%s", why);
@@ -246,6 +247,7 @@ lq_status lq_object_count(lq_solver *s, int *n) {
 
 lq_status lq_move_object(lq_solver *s, int index, const double shift[3]) {
     if (check_solver(s)) return LQ_EINVAL;
+    if (s->slab) return fail(s, LQ_EINVAL, "a slab takes its geometry and material from the whole lattice");
     if (!shift || index < 0 || index >= (int)s->objects.size()) return fail(s, LQ_EINVAL, "no object %d", index);
     for (int k = 0; k < 3; ++k)
         if (!std::isfinite(shift[k])) return fail(s, LQ_EINVAL, "shift must be finite");
@@ -279,6 +281,7 @@ lq_status lq_move_object(lq_solver *s, int index, const double shift[3]) {
 
 lq_status lq_clear_objects(lq_solver *s) {
     if (check_solver(s)) return LQ_EINVAL;
+    if (s->slab) return fail(s, LQ_EINVAL, "a slab takes its geometry and material from the whole lattice");
     s->objects.clear();
     s->geom_dirty = true;
     s->fire_ready = false;
@@ -288,6 +291,7 @@ lq_status lq_clear_objects(lq_solver *s) {
 lq_status lq_clone(lq_solver *src, void *cuda_stream, lq_solver **out) {
     if (check_solver(src) || !out) return LQ_EINVAL;
     *out = nullptr;
+    if (src->slab) return fail(src, LQ_EINVAL, "a slab is cut from the whole lattice (lq_slab_create)");
     lq_status r = build_geometry(src);
     if (r != LQ_OK) return r;
     if (src->fire_ready) {

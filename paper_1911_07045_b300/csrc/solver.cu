@@ -118,6 +118,11 @@ StepLaunch make_launch(lq_solver *s, int force_only) {
     sl.wide = wide_tiles(s->fp32, s->three, s->L.nx);
     sl.tma = s->staging == 2 && s->fp32 && s->three && !s->ext && tma_staging_fits(s->L) &&
              tma_staging_available();
+    if (s->slab) {            // own planes only; the FIRE update waits for every slab's sums
+        sl.zbeg = 1;
+        sl.zend = s->L.nz - 1;
+        sl.reduce_only = 1;
+    }
     return sl;
 }
 
@@ -421,6 +426,7 @@ const char *validate_material(const lq_material *m, double *S0) {
 }
 
 lq_status add_object(lq_solver *s, HostObject &&o) {
+    if (s->slab) return fail(s, LQ_EINVAL, "a slab takes its geometry from the whole lattice");
     if (o.type != 3) {
         const lq_anchoring &a = o.anch;
         if (a.kind < 0 || a.kind > 2 || !(a.W >= 0)) return fail(s, LQ_EINVAL, "bad anchoring");
@@ -749,12 +755,14 @@ lq_status lq_order_field(lq_solver *s, double *S_out) {
 
 lq_status lq_fire_reset(lq_solver *s, const lq_fire_params *p) {
     if (check_solver(s)) return LQ_EINVAL;
+    if (s->slab) return fail(s, LQ_EINVAL, "a slab starts FIRE through lq_slab_start");
     if (s->fire_ready) { lq_status r = sync_state(s); if (r != LQ_OK) return r; }
     return fire_reset(s, p);
 }
 
 lq_status lq_step(lq_solver *s, const lq_fire_params *p, int64_t n, lq_result *out) {
     if (check_solver(s)) return LQ_EINVAL;
+    if (s->slab) return fail(s, LQ_EINVAL, "a slab steps through lq_slab_step and lq_slab_finish");
     if (n < 0) return fail(s, LQ_EINVAL, "negative step count");
     auto t0 = std::chrono::steady_clock::now();
     lq_status r = check_params(s, p);
@@ -786,6 +794,7 @@ lq_status lq_fire_result(lq_solver *s, lq_result *out) {
 
 lq_status lq_minimize(lq_solver *s, const lq_fire_params *p, lq_result *out) {
     if (check_solver(s)) return LQ_EINVAL;
+    if (s->slab) return fail(s, LQ_EINVAL, "a slab steps through lq_slab_step and lq_slab_finish");
     auto t0 = std::chrono::steady_clock::now();
     if (s->fire_ready) { lq_status r = sync_state(s); if (r != LQ_OK) return r; }
     lq_status r = fire_reset(s, p);

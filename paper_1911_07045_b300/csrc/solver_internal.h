@@ -60,6 +60,8 @@ struct lq_solver {
     int zchunk = 0;                 // 0 = automatic
     int idx64 = 0;                  // 64-bit element indices forced (lq_set_index_width)
     int staging = 0;                // lq_set_staging: 0 automatic, 1 loads, 2 tensor copies
+    int slab = 0;                   // a z slab of a decomposed lattice (lq_slab_create): its own
+                                    // planes are 1 .. nz-2, planes 0 and nz-1 are halos
 
     cudaGraphExec_t gexec = nullptr;
     int graph_k = 0;

@@ -106,6 +106,10 @@ struct StepArgs {
     double *partials;         // 4 doubles per block
     int zchunk;
     int force_only;
+    int zbeg, zend;           // the planes the step updates (a slab owns [zbeg, zend))
+    int reduce_only;          // slab of a decomposed lattice: the last block leaves the
+                              // slab's sums (P, |F|^2, |v|^2, max) in the FIRE state and
+                              // the scalar update waits for the sums of every slab
 };
 
 __device__ __forceinline__ int wrap_coord(int g, int n, int periodic) {
@@ -1883,9 +1887,25 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
     }
     block_reduce4<NT>(P2, F2, V2, R2, red);
     if (threadIdx.x == 0) {
-        fire_update(args.st, P2, F2, V2, R2);
+        if (args.reduce_only) {
+            FireDev *st = args.st;
+            st->P = P2; st->F2 = F2; st->v2 = V2; st->r2 = R2;
+        } else {
+            fire_update(args.st, P2, F2, V2, R2);
+        }
         args.st->counter = 0;
     }
+}
+
+// the FIRE scalar update of a slab of a decomposed lattice from the sums over
+// every slab (one thread; the same update on every slab)
+__global__ void k_fire_apply(FireDev *st, double P, double F2, double v2, double r2) {
+    if (st->status == FIRE_RUNNING) fire_update(st, P, F2, v2, r2);
+}
+
+cudaError_t fire_apply(FireDev *st, const double sums[4], cudaStream_t stream) {
+    k_fire_apply<<<1, 1, 0, stream>>>(st, sums[0], sums[1], sums[2], sums[3]);
+    return cudaGetLastError();
 }
 
 
@@ -1896,8 +1916,8 @@ fire_step_kernel(StepArgs<T> args) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[4 * (TX * TY / 32)];
     __shared__ int am_last;
-    const int z0 = blockIdx.z * args.zchunk;
-    const int z1 = min(z0 + args.zchunk, args.L.nz);
+    const int z0 = args.zbeg + blockIdx.z * args.zchunk;
+    const int z1 = min(z0 + args.zchunk, args.zend);
     const int nblk = gridDim.x * gridDim.y * gridDim.z;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     step_tile<T, FORM, TX, TY, I>(args, blockIdx.x, blockIdx.y, z0, z1, nblk, bid, smem_raw, red,
@@ -1913,8 +1933,8 @@ fire_step_tma_kernel(const __grid_constant__ StepArgs<T> args, const __grid_cons
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[4 * (TX * TY / 32)];
     __shared__ int am_last;
-    const int z0 = blockIdx.z * args.zchunk;
-    const int z1 = min(z0 + args.zchunk, args.L.nz);
+    const int z0 = args.zbeg + blockIdx.z * args.zchunk;
+    const int z1 = min(z0 + args.zchunk, args.zend);
     const int nblk = gridDim.x * gridDim.y * gridDim.z;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     step_tile<T, FORM, TX, TY, I, true>(args, blockIdx.x, blockIdx.y, z0, z1, nblk, bid, smem_raw, red,
@@ -2032,6 +2052,9 @@ static void pack_args(const StepLaunch &sl, StepArgs<T> &a) {
     a.partials = sl.partials;
     a.zchunk = sl.zchunk;
     a.force_only = sl.force_only;
+    a.zbeg = sl.zbeg;
+    a.zend = sl.zend > 0 ? sl.zend : sl.L.nz;
+    a.reduce_only = sl.reduce_only;
 }
 
 // 32-bit element indices serve every lattice whose state arrays hold fewer
@@ -2043,6 +2066,7 @@ static cudaError_t launch_impl(const StepLaunch &sl, cudaStream_t stream) {
     StepArgs<T> a;
     pack_args<T>(sl, a);
     dim3 grid = step_grid(sl.L, sl.zchunk, TX, TY);
+    grid.z = (a.zend - a.zbeg + sl.zchunk - 1) / sl.zchunk;
     if constexpr (sizeof(T) == 4 && TX == 32) {
         if (sl.tma && !sl.force_only) {
             TmaMaps maps;

@@ -44,6 +44,8 @@ EXPORTS = [
     "lq_clear_objects", "lq_set_material", "lq_clone", "lq_pmf_sweep", "lq_init_dipolar",
     "lq_frank_to_landau", "lq_set_index_width", "lq_inject_fault", "lq_bounds_check_hits",
     "lq_fp64_fma_rate", "lq_set_staging", "lq_get_staging",
+    "lq_slab_create", "lq_slab_start", "lq_slab_step", "lq_slab_finish", "lq_slab_plane_bytes",
+    "lq_slab_get_planes", "lq_slab_set_halos",
 ]
 
 
@@ -188,6 +190,13 @@ def load(path: str = LIB_PATH):
         "lq_fp64_fma_rate": (C.c_int, [i64, C.POINTER(d)]),
         "lq_set_staging": (C.c_int, [S, C.c_int]),
         "lq_get_staging": (C.c_int, [S, C.POINTER(C.c_int)]),
+        "lq_slab_create": (C.c_int, [S, C.c_int, C.c_int, C.POINTER(p)]),
+        "lq_slab_start": (C.c_int, [S, C.POINTER(FireParams), p]),
+        "lq_slab_step": (C.c_int, [S, p]),
+        "lq_slab_finish": (C.c_int, [S, p, C.POINTER(Result)]),
+        "lq_slab_plane_bytes": (C.c_int, [S, C.POINTER(C.c_size_t)]),
+        "lq_slab_get_planes": (C.c_int, [S, p, p]),
+        "lq_slab_set_halos": (C.c_int, [S, p, p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
