@@ -304,14 +304,15 @@ def run_batch(steps: int):
 SERVING_FIRE = dict(synth.FIRE_DEFAULTS, max_iter=200000, force_tol=1e-6)
 
 
-def serve_stream(rate: float, window_s: float, extra_s: float, max_requests: int = 2000,
+def serve_stream(rate: float, window_s, extra_s: float, max_requests: int = 2000,
                  max_active: int = 8, budget_gb: float = 120.0, seed: int = 5, sample_s: float = 5.0):
     """Serve the seeded request stream of the serving workload (Poisson
     arrivals, edges 48..192, half patterned substrate + homeotropic top wall,
     half 1-2 colloids, one constant, FP32 form, max|F| < 1e-6) in real time
     on a continuous-batching server with an HBM budget: submit every request
-    that arrives within ``window_s`` seconds, keep serving ``extra_s`` seconds
-    more, then stop (the server drops what is left).  Reports the requests
+    that arrives within ``window_s`` seconds (None: the first
+    ``max_requests``), keep serving ``extra_s`` seconds after the last
+    arrival, then stop (the server drops what is left).  Reports the requests
     completed, in flight and queued at the end, the queue over time, the
     sustained site-updates/s (site updates the server issued to the GPU, and
     those of completed solves alone), and p50/p99 time-to-converged of the
@@ -344,8 +345,9 @@ def serve_stream(rate: float, window_s: float, extra_s: float, max_requests: int
         return now
 
     submitted = 0
+    last_arrival = 0.0
     for r in synth.iter_serving_requests(seed=seed, count=max_requests, rate=rate):
-        if r["t_arrival"] > window_s:
+        if window_s is not None and r["t_arrival"] > window_s:
             break
         while True:
             now = tick()
@@ -355,7 +357,9 @@ def serve_stream(rate: float, window_s: float, extra_s: float, max_requests: int
         t = sv.submit(r, p, seed=r["seed"])
         pending[t] = (r["shape"][0], r["kind"])
         submitted += 1
-    while pending and tick() < window_s + extra_s:
+        last_arrival = r["t_arrival"]
+    end = (window_s if window_s is not None else last_arrival) + extra_s
+    while pending and tick() < end:
         time.sleep(0.05)
     wall = tick(force=True)
     st = sv.stats()
@@ -369,7 +373,8 @@ def serve_stream(rate: float, window_s: float, extra_s: float, max_requests: int
     for d in done:
         if d["converged"]:
             by_edge.setdefault(d["L"], []).append(d["iterations"])
-    return {"rate_per_s": rate, "arrival_window_s": window_s, "extra_s": extra_s,
+    return {"rate_per_s": rate, "arrival_window_s": window_s if window_s is not None else last_arrival,
+            "extra_s": extra_s,
             "max_active": max_active, "hbm_budget_gb": budget_gb, "submitted": submitted,
             "completed": len(done), "converged": sum(d["converged"] for d in done),
             "in_flight_at_end": int(st["active"]), "queued_at_end": int(st["queued"]),
@@ -822,8 +827,9 @@ def run_served(args):
         cap = serving_capacity(a["site_updates_per_s"], table)
         if np.isfinite(cap) and cap > 0:
             rate = args.serving_utilisation * cap
-            window = args.serving_scaled / rate
-            b = serve_stream(rate, window, args.serving_scaled_extra * window,
+            # the first --serving-scaled requests of the stream at this rate,
+            # then a drain of a fraction of their expected arrival span
+            b = serve_stream(rate, None, args.serving_scaled_extra * args.serving_scaled / rate,
                              max_requests=args.serving_scaled, max_active=args.serving_max_active)
             b["capacity_req_per_s"] = cap
             b["target_utilisation"] = args.serving_utilisation

@@ -523,9 +523,15 @@ lq_status lq_energy_noalloc(const lq_lattice *lattice, const lq_material *materi
    a CUDA graph is captured) that the library makes fails as if CUDA had
    returned out-of-memory or a launch failure: nothing is allocated or
    launched for it, and the calling entry point returns LQ_ENOMEM or
-   LQ_ECUDA.  No device fault is ever made.  One-shot and process-wide;
-   LQ_FAULT_NONE cancels.  LQ_EINVAL for an unknown kind or after < 0. */
-enum { LQ_FAULT_NONE = 0, LQ_FAULT_DEVICE_ALLOC = 1, LQ_FAULT_STEP_LAUNCH = 2 };
+   LQ_ECUDA.  LQ_FAULT_COPY_WAIT: the (after + 1)-th launch of the
+   tensor-copy staging (lq_set_staging) makes its barriers expect more bytes
+   than its copies deliver, so that every wait for a plane runs out (about a
+   second each; copies take microseconds): the kernel stops with FIRE
+   status LQ_FIRE_STALLED and the entry point returns LQ_ECUDA -- the path a
+   copy that never completed would take.  No device fault is ever made.
+   One-shot and process-wide; LQ_FAULT_NONE cancels.  LQ_EINVAL for an
+   unknown kind or after < 0. */
+enum { LQ_FAULT_NONE = 0, LQ_FAULT_DEVICE_ALLOC = 1, LQ_FAULT_STEP_LAUNCH = 2, LQ_FAULT_COPY_WAIT = 3 };
 lq_status lq_inject_fault(int kind, int64_t after);
 /* The bounds-checked build of the library (compiled with LQ_BOUNDS_CHECK)
    checks every shared-memory slot, tile and ring index and every global

@@ -190,7 +190,7 @@ lq_status lq_bounds_check_hits(uint32_t *hits) {
 }
 
 lq_status lq_inject_fault(int kind, int64_t after) {
-    if (kind < LQ_FAULT_NONE || kind > LQ_FAULT_STEP_LAUNCH || after < 0) return LQ_EINVAL;
+    if (kind < LQ_FAULT_NONE || kind > LQ_FAULT_COPY_WAIT || after < 0) return LQ_EINVAL;
     g_fault_kind.store(LQ_FAULT_NONE, std::memory_order_release);
     g_fault_after.store(after, std::memory_order_release);
     g_fault_kind.store(kind, std::memory_order_release);

@@ -106,6 +106,8 @@ struct StepArgs {
     double *partials;         // 4 doubles per block
     int zchunk;
     int force_only;
+    unsigned tma_extra;       // testing: bytes a plane's barrier expects beyond its copies
+                              // (lq_inject_fault LQ_FAULT_COPY_WAIT); 0 otherwise
     int zbeg, zend;           // the planes the step updates (a slab owns [zbeg, zend))
     int reduce_only;          // slab of a decomposed lattice: the last block leaves the
                               // slab's sums (P, |F|^2, |v|^2, max) in the FIRE state and
@@ -1394,7 +1396,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
             const int lane = threadIdx.x;
             if (lane == 0) {
                 fence_proxy_async();
-                mbar_arrive_expect_tx(&bars[b], RL::TX_BYTES);
+                mbar_arrive_expect_tx(&bars[b], RL::TX_BYTES + args.tma_extra);
             }
             __syncwarp();
             if (lane < 4 * RL::ROWS) {
@@ -2052,6 +2054,7 @@ static void pack_args(const StepLaunch &sl, StepArgs<T> &a) {
     a.partials = sl.partials;
     a.zchunk = sl.zchunk;
     a.force_only = sl.force_only;
+    a.tma_extra = 0;
     a.zbeg = sl.zbeg;
     a.zend = sl.zend > 0 ? sl.zend : sl.L.nz;
     a.reduce_only = sl.reduce_only;
@@ -2071,6 +2074,11 @@ static cudaError_t launch_impl(const StepLaunch &sl, cudaStream_t stream) {
         if (sl.tma && !sl.force_only) {
             TmaMaps maps;
             if (!encode_maps<T, TX>(sl, maps)) return cudaErrorInvalidValue;
+            // injected (direct launches only, never baked into a captured
+            // graph): every plane's wait runs out
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            cudaStreamIsCapturing(stream, &cs);
+            if (cs == cudaStreamCaptureStatusNone && fault_due(3)) a.tma_extra = 16;
             fire_step_tma_kernel<T, FORM, TX, TY, I>
                 <<<grid, TX * TY, step_smem_bytes<T, FORM, TX, TY, true>(), stream>>>(a, maps);
             return cudaGetLastError();

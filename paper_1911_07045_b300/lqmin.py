@@ -246,7 +246,7 @@ def frank_to_landau(K1, K2, K3, K24, q0, S):
     return dict(zip(("L1", "L2", "L3", "L4", "L6"), list(out)))
 
 
-LQ_FAULT_NONE, LQ_FAULT_DEVICE_ALLOC, LQ_FAULT_STEP_LAUNCH = 0, 1, 2
+LQ_FAULT_NONE, LQ_FAULT_DEVICE_ALLOC, LQ_FAULT_STEP_LAUNCH, LQ_FAULT_COPY_WAIT = 0, 1, 2, 3
 
 
 def fp64_fma_rate(iters: int = 1 << 16) -> float:

@@ -154,3 +154,34 @@ def test_staging_modes_and_refusals():
         assert lib.lq_set_staging(s.h, 2) == lqmin.LQ_EINVAL
         assert not s.uses_tensor_copies()
         s.close()
+
+
+def test_copy_wait_that_runs_out_stops_fire_and_reports_it():
+    """A plane whose copies never satisfy its barrier (injected on the host:
+    the barrier expects more bytes than the copies deliver) must not hang
+    the GPU: every wait gives up after about a second, the kernel stops with
+    the stalled status, the entry point returns LQ_ECUDA, the context stays
+    usable, and a FIRE restart runs exactly like a fresh solver."""
+    import ctypes as C
+    c = CASES["open_axes"]
+    a, fresh = make(c, 2), make(c, 2)
+    q0 = synth.random_uniaxial_q(c["shape"], 24)
+    a.set_q(q0)
+    p = lqmin.fire_params(**FP)
+    a.step(p, 2)
+    lib = lqmin.load()
+    assert lib.lq_inject_fault(lqmin.LQ_FAULT_COPY_WAIT, 0) == lqmin.LQ_OK
+    r = lqmin.Result()
+    st = lib.lq_step(a.h, C.byref(p), 1, C.byref(r))        # one direct launch
+    assert st == lqmin.LQ_ECUDA
+    assert r.fire_status == lqmin.FIRE_STALLED
+    assert b"tensor copy" in lib.lq_last_error(a.h)
+    assert lib.lq_step(a.h, C.byref(p), 1, C.byref(r)) == lqmin.LQ_ECUDA   # stays stopped
+    # restart from a fresh start state: the same trajectory as a fresh solver
+    a.set_q(q0)
+    fresh.set_q(q0)
+    ra, rf = a.step(p, 5), fresh.step(p, 5)
+    assert ra.fire_status == rf.fire_status == lqmin.FIRE_RUNNING
+    assert np.array_equal(a.get_q(), fresh.get_q())
+    a.close()
+    fresh.close()
