@@ -43,9 +43,9 @@ DESIGN_BYTES = {"fp32": 6 * 5 * 4 + 1, "fp64": 6 * 5 * 8 + 1}
 # launch grows with the sites it updates); the bench scales it to its lattice.
 # The FP64 one-constant form moves the same state bytes as the three-constant
 # one and takes its figure.
-DRAM_BYTES_PER_SITE = {"fp32": (1.075125e9 + 0.961110e9) / 256 ** 3,
-                       "fp64": (2.258716e9 + 1.955101e9) / 256 ** 3,
-                       "fp32_1c": (1.060582e9 + 0.956583e9) / 256 ** 3}
+DRAM_BYTES_PER_SITE = {"fp32": (1.074887e9 + 0.961360128e9) / 256 ** 3,
+                       "fp64": (2.260472e9 + 1.955142e9) / 256 ** 3,
+                       "fp32_1c": (1.060716e9 + 0.956969984e9) / 256 ** 3}
 # FP64 form: bound by the FP64 pipe (2 FP64 operations per clock per SM).
 # FP64 arithmetic operations per site-update of the regular three-constant
 # site, counted from the kernel's arithmetic: stencil 94 (second
