@@ -128,16 +128,50 @@ def aggregate(dist: Dist, units: float, seconds: float):
 # ---- clocks during the timed region ---------------------------------------------
 
 class ClockSampler:
+    """SM clocks and throttle reasons of one GPU, sampled while a timed
+    region runs: through NVML every 2 ms where the NVML bindings load (a
+    20-step region of the 512^3 workload lasts under 100 ms), else through
+    ``nvidia-smi -lms 200``.  Only reads the GPU's state."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, interval_s: float = 0.002):
         self.gpu = gpu_index
+        self.interval = interval_s
         self.proc = None
+        self.nvml = None
         self.lines = []
+        self.samples = []          # NVML: (sm MHz, max sm MHz, reason names)
+        self.stop = threading.Event()
 
     def __enter__(self):
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            h = pynvml.nvmlDeviceGetHandleByIndex(self.gpu)
+            bits = [pynvml.nvmlClocksEventReasonHwSlowdown, pynvml.nvmlClocksEventReasonHwThermalSlowdown,
+                    pynvml.nvmlClocksEventReasonSwThermalSlowdown, pynvml.nvmlClocksEventReasonSwPowerCap]
+            mx = pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM)
+
+            def poll():
+                while True:
+                    try:
+                        sm = pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM)
+                        r = pynvml.nvmlDeviceGetCurrentClocksEventReasons(h)
+                        self.samples.append((float(sm), float(mx),
+                                             [n for n, b in zip(self.NAMES, bits) if r & b]))
+                    except Exception:
+                        pass
+                    if self.stop.wait(self.interval):
+                        break
+            self.nvml = pynvml
+            self.t = threading.Thread(target=poll, daemon=True)
+            self.t.start()
+            return self
+        except Exception:
+            self.nvml = None
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
@@ -154,6 +188,13 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def __exit__(self, *a):
+        if self.nvml is not None:
+            self.stop.set()
+            self.t.join(timeout=2)
+            try:
+                self.nvml.nvmlShutdown()
+            except Exception:
+                pass
         if self.proc:
             self.proc.terminate()
             try:
@@ -164,7 +205,10 @@ class ClockSampler:
 
     def summary(self):
         sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for f_sm, f_mx, names in self.samples:
+            sm.append(f_sm)
+            mx = f_mx
+            reasons.update(names)
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
@@ -174,13 +218,13 @@ class ClockSampler:
                 mx = float(f[2])
             except ValueError:
                 continue
-            for nm, val in zip(names, f[5:9]):
+            for nm, val in zip(self.NAMES, f[5:9]):
                 if val.lower().startswith("active"):
                     reasons.add(nm)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvml 2 ms" if self.samples else "nvidia-smi 200 ms"}
 
 
 # ---- our arm ------------------------------------------------------------------------

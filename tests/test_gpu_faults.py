@@ -118,9 +118,12 @@ def test_served_request_whose_allocation_fails():
 
 def test_injection_arguments_are_checked():
     with pytest.raises(lqmin.LqError):
-        lqmin.inject_fault(3)
+        lqmin.inject_fault(lqmin.LQ_FAULT_COPY_WAIT + 1)     # no such kind
+    with pytest.raises(lqmin.LqError):
+        lqmin.inject_fault(-1)
     with pytest.raises(lqmin.LqError):
         lqmin.inject_fault(lqmin.LQ_FAULT_DEVICE_ALLOC, -1)
+    lqmin.inject_fault(lqmin.LQ_FAULT_NONE)                   # nothing stays armed
 
 
 def test_served_round_with_a_failed_launch_is_retried():
