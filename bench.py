@@ -129,13 +129,15 @@ def aggregate(dist: Dist, units: float, seconds: float):
 
 class ClockSampler:
     """SM clocks and throttle reasons of one GPU, sampled while a timed
-    region runs: through NVML every 2 ms where the NVML bindings load (a
-    20-step region of the 512^3 workload lasts under 100 ms), else through
-    ``nvidia-smi -lms 200``.  Only reads the GPU's state."""
+    region runs: through the driver's NVML library (ctypes) every 2 ms where
+    it loads (a 20-step region of the 512^3 workload lasts under 100 ms),
+    else through ``nvidia-smi -lms 200``.  Only reads the GPU's state."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
     NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    BITS = [0x8, 0x40, 0x20, 0x4]      # nvmlClocksEventReason* of nvml.h, in NAMES order
+    NVML_CLOCK_SM = 1
 
     def __init__(self, gpu_index: int, interval_s: float = 0.002):
         self.gpu = gpu_index
@@ -146,27 +148,55 @@ class ClockSampler:
         self.samples = []          # NVML: (sm MHz, max sm MHz, reason names)
         self.stop = threading.Event()
 
+    def _nvml_open(self):
+        import ctypes as C
+        lib = C.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit")
+        dev = C.c_void_p()
+        # the CUDA device's PCI address names the same GPU in NVML whatever
+        # CUDA_VISIBLE_DEVICES hides; the index is the fallback
+        rc = -1
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(self.gpu)
+            bus = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0".encode()
+            rc = lib.nvmlDeviceGetHandleByPciBusId_v2(C.c_char_p(bus), C.byref(dev))
+        except Exception:
+            rc = -1
+        if rc != 0 and lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(self.gpu), C.byref(dev)) != 0:
+            lib.nvmlShutdown()
+            raise RuntimeError("nvmlDeviceGetHandleByIndex")
+        reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = C.c_uint()
+        lib.nvmlDeviceGetMaxClockInfo(dev, self.NVML_CLOCK_SM, C.byref(mx))
+        clk, rs = C.c_uint(), C.c_ulonglong()
+
+        def read():
+            if lib.nvmlDeviceGetClockInfo(dev, self.NVML_CLOCK_SM, C.byref(clk)) != 0:
+                return None
+            if reasons_fn(dev, C.byref(rs)) != 0:
+                return None
+            return (float(clk.value), float(mx.value),
+                    [n for n, b in zip(self.NAMES, self.BITS) if rs.value & b])
+        if read() is None:
+            lib.nvmlShutdown()
+            raise RuntimeError("nvml clock query")
+        return lib, read
+
     def __enter__(self):
         try:
-            import pynvml
-            pynvml.nvmlInit()
-            h = pynvml.nvmlDeviceGetHandleByIndex(self.gpu)
-            bits = [pynvml.nvmlClocksEventReasonHwSlowdown, pynvml.nvmlClocksEventReasonHwThermalSlowdown,
-                    pynvml.nvmlClocksEventReasonSwThermalSlowdown, pynvml.nvmlClocksEventReasonSwPowerCap]
-            mx = pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM)
+            lib, read = self._nvml_open()
 
             def poll():
                 while True:
-                    try:
-                        sm = pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM)
-                        r = pynvml.nvmlDeviceGetCurrentClocksEventReasons(h)
-                        self.samples.append((float(sm), float(mx),
-                                             [n for n, b in zip(self.NAMES, bits) if r & b]))
-                    except Exception:
-                        pass
+                    smp = read()
+                    if smp is not None:
+                        self.samples.append(smp)
                     if self.stop.wait(self.interval):
                         break
-            self.nvml = pynvml
+            self.nvml = lib
             self.t = threading.Thread(target=poll, daemon=True)
             self.t.start()
             return self
@@ -191,10 +221,7 @@ class ClockSampler:
         if self.nvml is not None:
             self.stop.set()
             self.t.join(timeout=2)
-            try:
-                self.nvml.nvmlShutdown()
-            except Exception:
-                pass
+            self.nvml.nvmlShutdown()
         if self.proc:
             self.proc.terminate()
             try:
