@@ -459,10 +459,15 @@ def serve_stream(rate: float, window_s, extra_s: float, max_requests: int = 2000
 
 
 # FIRE iterations to max|F| < 1e-6 of the serving stream's requests by cubic
-# edge: the first request of each edge in the seeded stream minimised alone
-# on a B300 (FP32 form, `bench.py --serving-calibrate`); the scaled-rate
-# stream takes its arrival rate from these and the measured throughput
-SERVING_ITERS_BY_EDGE = {"48": 33530, "64": 13881, "80": 60508, "96": 64341, "112": 100200, "128": 32747, "144": 32364, "160": 43518, "176": 36239, "192": 55247}
+# edge: the mean over the first five requests of each edge in the seeded
+# stream, each minimised alone on a B300 (FP32 form, `bench.py
+# --serving-calibrate`; requests that stop at the 200 000-iteration limit
+# count with that limit).  The mean work per request from it, 1.70e11 site
+# updates, is what the first 64 requests of the stream cost when served (the
+# capacity needs the mean, not a typical request); the scaled-rate stream
+# takes its arrival rate from these and the measured throughput
+SERVING_ITERS_BY_EDGE = {"48": 30886, "64": 34999, "80": 43593, "96": 72288, "112": 78296, "128": 77236,
+                         "144": 49290, "160": 94536, "176": 43122, "192": 78535}
 
 
 def serving_capacity(rate_site_updates: float, iters_by_edge: dict) -> float:
@@ -479,9 +484,10 @@ def serving_capacity(rate_site_updates: float, iters_by_edge: dict) -> float:
     return rate_site_updates / work
 
 
-def serving_calibrate(count: int = 1):
-    """Minimise the first request of each edge of the seeded stream alone
-    (FP32 form, the serving FIRE parameters): iterations and seconds."""
+def serving_calibrate(count: int = 5):
+    """Minimise the first ``count`` requests of each edge of the seeded
+    stream alone (FP32 form, the serving FIRE parameters): iterations and
+    seconds of each."""
     from paper_1911_07045_b300 import lqmin
     p = lqmin.fire_params(**SERVING_FIRE)
     seen, out = {}, {}
@@ -798,6 +804,8 @@ def run_baselines():
 def main_ours(args, dist: Dist):
     import torch
     torch.cuda.set_device(dist.local)
+    t_start = time.perf_counter()
+    legs = {}
     peak, peak_kind = measured_peaks()
     forms = {}
     for prec in args.precision.split(","):
@@ -805,6 +813,7 @@ def main_ours(args, dist: Dist):
         # (half a second at 512^3), keeps its timed region long enough to time
         k = args.steps if prec.startswith("fp32") else max(10, args.steps // 10)
         forms[prec] = run_form(prec, args.size, k, args.warmup, dist, dist.local, args.staging)
+    legs["forms"] = round(time.perf_counter() - t_start, 1)
     fp64_rate = None
     if any(not k.startswith("fp32") for k in forms):
         from paper_1911_07045_b300 import lqmin
@@ -860,21 +869,27 @@ def main_ours(args, dist: Dist):
         "gpu_launches": sum(f["launches"] for f in forms.values()),
         "clocks": h["clocks"],
     }
+    def leg(name, fn, *a):
+        t = time.perf_counter()
+        line[name] = fn(*a)
+        legs[name] = round(time.perf_counter() - t, 1)
     if dist.world == 1 and args.batch_steps > 0:
-        line["batched"] = run_batch(args.batch_steps)
+        leg("batched", run_batch, args.batch_steps)
     if dist.world == 1 and args.serving_window > 0:
-        line["served"] = run_served(args)
+        leg("served", run_served, args)
     if dist.world == 1 and not args.no_precision_check:
-        line["precision_check"] = run_precision_check()
+        leg("precision_check", run_precision_check)
     if dist.world == 1 and args.minimizers > 0:
-        line["minimizers"] = run_minimizers(args.minimizer_size, args.minimizers)
+        leg("minimizers", run_minimizers, args.minimizer_size, args.minimizers)
     if dist.world == 1 and args.objects > 0:
-        line["objects_fig3"] = run_objects(args.minimizer_size, args.objects)
+        leg("objects_fig3", run_objects, args.minimizer_size, args.objects)
     if dist.world == 1 and args.step_scaling:
-        line["step_scaling"] = run_step_scaling([int(v) for v in args.step_scaling.split(",")],
-                                                args.step_scaling_tol)
+        leg("step_scaling", run_step_scaling, [int(v) for v in args.step_scaling.split(",")],
+            args.step_scaling_tol)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        leg("cpu_baseline", cpu_baseline)
+    legs["total"] = round(time.perf_counter() - t_start, 1)
+    line["wall_seconds_by_leg"] = legs
     if not all(f["ok"] for f in forms.values()):
         line["invalid"] = "FIRE stopped before all timed steps ran"
     return line
@@ -968,8 +983,9 @@ def main(argv=None):
                     help="seconds of serving after the last arrival before stopping")
     ap.add_argument("--serving-rate", type=float, default=20.0)
     ap.add_argument("--serving-max-active", type=int, default=8)
-    ap.add_argument("--serving-scaled", type=int, default=64,
-                    help="requests of the scaled-rate stream (0: skip)")
+    ap.add_argument("--serving-scaled", type=int, default=32,
+                    help="requests of the scaled-rate stream (0: skip); at 0.8 of capacity (0.1 "
+                         "requests/s) the first 32 arrive over 331 s, the first 64 over 757 s")
     ap.add_argument("--serving-utilisation", type=float, default=0.8)
     ap.add_argument("--serving-scaled-extra", type=float, default=0.25,
                     help="drain time of the scaled-rate stream as a fraction of its arrival window")
@@ -977,7 +993,10 @@ def main(argv=None):
                     help="only run the CPU-baseline plan: full minimisations of the 32^3 and 128^3 "
                          "workloads next to the oracle, and print them")
     ap.add_argument("--serving-calibrate", action="store_true",
-                    help="only minimise one request per edge of the served stream alone and print them")
+                    help="only minimise the first requests of each edge of the served stream alone and "
+                         "print them with the median and mean iterations per edge")
+    ap.add_argument("--serving-calibrate-count", type=int, default=5,
+                    help="requests per edge of --serving-calibrate")
     ap.add_argument("--minimizers", type=float, default=0.0,
                     help="seconds per method of the FIRE / GD / Nesterov comparison (0: skip)")
     ap.add_argument("--minimizer-size", type=int, default=250)
@@ -999,7 +1018,11 @@ def main(argv=None):
     if args.serving_calibrate:
         import torch
         torch.cuda.set_device(0)
-        print(json.dumps({"serving_calibration": serving_calibrate()}), flush=True)
+        cal = serving_calibrate(args.serving_calibrate_count)
+        med = {L: int(np.median([x["iterations"] for x in v])) for L, v in cal.items()}
+        mean = {L: int(np.mean([x["iterations"] for x in v])) for L, v in cal.items()}
+        print(json.dumps({"serving_calibration": cal, "median_iterations_by_edge": med,
+                          "mean_iterations_by_edge": mean}), flush=True)
         return
     dist = Dist(backend="gloo" if args.impl == "reference" else None)
     try:
