@@ -1947,8 +1947,13 @@ fire_step_tma_kernel(const __grid_constant__ StepArgs<T> args, const __grid_cons
 // over the work items (lattice, tile, z chunk); each lattice keeps its own
 // partial sums, last-block ticket and FIRE state, so a lattice advances
 // exactly as it would alone with the same tile and z chunk
+// FP32 form: three blocks of 128 threads per SM with three constants (168
+// registers: at 128 the three-constant item loop spills 144 bytes a thread
+// and runs 1.6 times slower), four with one constant
 template <typename T, int FORM, int TX, int TY, typename I>
-__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? (FORM == 2 ? 384 : 512) / (TX * TY) : 1)
+__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? (FORM == 2 || (FORM == 1 && TX * TY == 128) ? 384 : 512) /
+                                                               (TX * TY)
+                                                         : 1)
 fire_batch_kernel(const StepArgs<T> *__restrict__ args, const WorkItem *__restrict__ items,
                   int nitems) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
