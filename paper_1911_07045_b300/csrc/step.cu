@@ -1586,8 +1586,17 @@ __device__ __forceinline__ void step_tile(const StepArgs<T> &args, int bx, int b
                 for (int c = 0; c < 5; ++c) { vold[c] = __ldg(vin + c * N + i); fold[c] = __ldg(Fin + c * N + i); }
             }
         }
-        // the barrier publishes plane z+2 and decides the path of this plane
-        const bool all_reg = __syncthreads_and(reg) != 0;
+        // the barrier publishes plane z+2.  The path of this plane: with one
+        // constant the general path has no block-wide step, so each warp
+        // takes the regular path when its own sites allow it; with three
+        // constants the general path's cross terms need the whole block
+        bool all_reg;
+        if constexpr (THREE) {
+            all_reg = __syncthreads_and(reg) != 0;
+        } else {
+            __syncthreads();
+            all_reg = __all_sync(0xffffffffu, reg);
+        }
         if constexpr (TMA) {
             // every thread is done with the buffer of plane z+2: refill it
             if (stalled()) return;
