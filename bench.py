@@ -45,7 +45,7 @@ DESIGN_BYTES = {"fp32": 6 * 5 * 4 + 1, "fp64": 6 * 5 * 8 + 1}
 # one and takes its figure.
 DRAM_BYTES_PER_SITE = {"fp32": (1.074887e9 + 0.961360128e9) / 256 ** 3,
                        "fp64": (2.260472e9 + 1.955142e9) / 256 ** 3,
-                       "fp32_1c": (1.060716e9 + 0.956969984e9) / 256 ** 3}
+                       "fp32_1c": (1.060342e9 + 0.957613312e9) / 256 ** 3}
 # FP64 form: bound by the FP64 pipe (2 FP64 operations per clock per SM).
 # FP64 arithmetic operations per site-update of the regular three-constant
 # site, counted from the kernel's arithmetic: stencil 94 (second
@@ -334,9 +334,10 @@ def run_form(precision: str, L: int, steps: int, warmup: int, dist: Dist, sample
     return out
 
 
-def run_batch(steps: int):
+def run_batch(steps: int, tile=None):
     """64 uneven lattices (edges 32..128, 0-3 colloids, one constant, FP32
-    form) advanced by the persistent batch kernel; the tiling is autotuned."""
+    form) advanced by the persistent batch kernel; the tiling is autotuned,
+    or ``tile`` = (width, height, z chunk) when given (for profiling)."""
     from paper_1911_07045_b300 import lqmin
     cfgs = synth.config_batch()
     solvers = []
@@ -347,7 +348,11 @@ def run_batch(steps: int):
     sites = sum(int(np.prod(c["shape"])) for c in cfgs)
     batch = lqmin.Batch(solvers)
     p = lqmin.fire_params(**dict(synth.FIRE_DEFAULTS, max_iter=10 ** 12, force_tol=0.0))
-    (tx, ty, zc), tuned_ms = batch.autotune(p, launches=12)
+    if tile:
+        (tx, ty, zc), tuned_ms = tile, None
+        batch.set_tile(tx, ty, zc)
+    else:
+        (tx, ty, zc), tuned_ms = batch.autotune(p, launches=12)
     batch.step(p, 3)                                  # warm-up
     t0 = time.perf_counter(); batch.step(p, steps); t1 = time.perf_counter()
     batch.step(p, 2 * steps); t2 = time.perf_counter()
@@ -358,7 +363,7 @@ def run_batch(steps: int):
                        f"R~U[6,16] (W=5.3), one constant, FP32 form",
            "sites": sites, "steps": steps, "value": sites * steps / sec, "unit": UNIT,
            "ms_per_step": sec / steps * 1e3, "tiling": {"tile": f"{tx}x{ty}", "zchunk": zc},
-           "autotune_ms_per_step": tuned_ms, "autotune_launches_per_candidate": 12,
+           "autotune_ms_per_step": tuned_ms, "autotune_launches_per_candidate": 12 if not tile else 0,
            "launches_per_step": 1,
            # algorithmic bytes (q, v read + written, mask) of every lattice
            # per launch over the time per launch (host-timed graph launches)
@@ -874,7 +879,8 @@ def main_ours(args, dist: Dist):
         line[name] = fn(*a)
         legs[name] = round(time.perf_counter() - t, 1)
     if dist.world == 1 and args.batch_steps > 0:
-        leg("batched", run_batch, args.batch_steps)
+        leg("batched", run_batch, args.batch_steps,
+            tuple(int(v) for v in args.batch_tile.split("x")) if args.batch_tile else None)
     if dist.world == 1 and args.serving_window > 0:
         leg("served", run_served, args)
     if dist.world == 1 and not args.no_precision_check:
@@ -977,6 +983,8 @@ def main(argv=None):
                     help="plane staging of the FP32 three-constant step: 0 automatic, 1 per-thread "
                          "loads, 2 tensor copies (lq_set_staging)")
     ap.add_argument("--batch-steps", type=int, default=50)
+    ap.add_argument("--batch-tile", default="",
+                    help="WxHxZ: run the batched leg with this tiling instead of autotuning it")
     ap.add_argument("--serving-window", type=float, default=100.0,
                     help="seconds of arrivals of the served stream (0: skip serving)")
     ap.add_argument("--serving-extra", type=float, default=10.0,
