@@ -46,6 +46,10 @@ DESIGN_BYTES = {"fp32": 6 * 5 * 4 + 1, "fp64": 6 * 5 * 8 + 1}
 DRAM_BYTES_PER_SITE = {"fp32": (1.074887e9 + 0.961360128e9) / 256 ** 3,
                        "fp64": (2.260472e9 + 1.955142e9) / 256 ** 3,
                        "fp32_1c": (1.060342e9 + 0.957613312e9) / 256 ** 3}
+# DRAM bytes per site-update of the batched leg's launch (64 lattices, 32x4
+# tiles, z chunk 128; ncu, mean of three launches): re-reads around the
+# colloids lift it above the single-lattice figure
+DRAM_BYTES_PER_SITE_BATCH = (4.641573632e9 + 2.734156288e9) / 46252032
 # FP64 form: bound by the FP64 pipe (2 FP64 operations per clock per SM).
 # FP64 arithmetic operations per site-update of the regular three-constant
 # site, counted from the kernel's arithmetic: stencil 94 (second
@@ -368,7 +372,10 @@ def run_batch(steps: int, tile=None):
            # algorithmic bytes (q, v read + written, mask) of every lattice
            # per launch over the time per launch (host-timed graph launches)
            "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                        "frac": round(ach / peak, 4), "traffic": None,
+                        "frac": round(ach / peak, 4),
+                        "traffic": round(DRAM_BYTES_PER_SITE_BATCH * sites) if sites == 46252032 else None,
+                        "dram_frac": round(DRAM_BYTES_PER_SITE_BATCH * sites / (sec / steps) / 1e9 / peak, 4)
+                        if sites == 46252032 else None,
                         "alg_bytes_per_site": ALG_BYTES["fp32"],
                         "peak_kind": peak_kind + " (HBM copy)"}}
     batch.close()
