@@ -340,15 +340,18 @@ struct FireSums<float> {
     float2 vv_hi = make_float2(0.f, 0.f), vv_lo = vv_hi;   // |v|^2 in two lanes
     float r_hi = 0.f, r_lo = 0.f;                           // largest site |F|^2
     __device__ __forceinline__ void site(const float *fn, const float *vn) {
-        // the site's (F.v, |F|^2) as float-float pairs (s, lo)
-        float2 lo, e, t;
-        float2 s = two_prod2(make_float2(fn[0], fn[0]), make_float2(vn[0], fn[0]), lo);
+        // the site's (F.v, |F|^2) as float-float pairs (s, lo), summed as a
+        // tree ((0 + 1) + (2 + 3)) + 4 to shorten the dependent chain
+        float2 p[5], e[5], t0, t1, t2, t3, t;
 #pragma unroll
-        for (int c = 1; c < 5; ++c) {
-            const float2 pc = two_prod2(make_float2(fn[c], fn[c]), make_float2(vn[c], fn[c]), e);
-            s = two_sum2(s, pc, t);
-            lo = __fadd2_rn(lo, __fadd2_rn(t, e));
-        }
+        for (int c = 0; c < 5; ++c)
+            p[c] = two_prod2(make_float2(fn[c], fn[c]), make_float2(vn[c], fn[c]), e[c]);
+        const float2 s01 = two_sum2(p[0], p[1], t0);
+        const float2 s23 = two_sum2(p[2], p[3], t1);
+        const float2 s03 = two_sum2(s01, s23, t2);
+        const float2 s = two_sum2(s03, p[4], t3);
+        const float2 lo = __fadd2_rn(__fadd2_rn(__fadd2_rn(e[0], e[1]), __fadd2_rn(e[2], e[3])),
+                                     __fadd2_rn(__fadd2_rn(e[4], t0), __fadd2_rn(__fadd2_rn(t1, t2), t3)));
         // largest site |F|^2: normalise the pair (fast two-sum, |s| >= |lo|),
         // compare high parts first
         {
@@ -358,13 +361,17 @@ struct FireSums<float> {
         }
         pf_hi = two_sum2(pf_hi, s, t);
         pf_lo = __fadd2_rn(pf_lo, __fadd2_rn(t, lo));
-        // |v|^2 product by product: components (0, 1), (2, 3), (4, -)
-#pragma unroll
-        for (int c = 0; c < 5; c += 2) {
-            const float2 vc = make_float2(vn[c], c + 1 < 5 ? vn[c + 1] : 0.f);
-            const float2 pc = two_prod2(vc, vc, e);
-            vv_hi = two_sum2(vv_hi, pc, t);
-            vv_lo = __fadd2_rn(vv_lo, __fadd2_rn(t, e));
+        // |v|^2: components (0, 1), (2, 3), (4, -) summed within the site,
+        // then one two-sum into the thread's pair
+        {
+            float2 ea, eb, ec, ta, tb, tc;
+            const float2 va = make_float2(vn[0], vn[1]), vb = make_float2(vn[2], vn[3]),
+                         vc = make_float2(vn[4], 0.f);
+            const float2 pa = two_prod2(va, va, ea), pb = two_prod2(vb, vb, eb), pcc = two_prod2(vc, vc, ec);
+            const float2 sv = two_sum2(two_sum2(pa, pb, ta), pcc, tb);
+            vv_hi = two_sum2(vv_hi, sv, tc);
+            vv_lo = __fadd2_rn(vv_lo, __fadd2_rn(__fadd2_rn(__fadd2_rn(ea, eb), __fadd2_rn(ec, ta)),
+                                                 __fadd2_rn(tb, tc)));
         }
     }
     __device__ __forceinline__ void get(double &P, double &F2, double &V2, double &R2) const {
