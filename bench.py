@@ -43,13 +43,13 @@ DESIGN_BYTES = {"fp32": 6 * 5 * 4 + 1, "fp64": 6 * 5 * 8 + 1}
 # launch grows with the sites it updates); the bench scales it to its lattice.
 # The FP64 one-constant form moves the same state bytes as the three-constant
 # one and takes its figure.
-DRAM_BYTES_PER_SITE = {"fp32": (1.074887e9 + 0.961360128e9) / 256 ** 3,
+DRAM_BYTES_PER_SITE = {"fp32": (1.074094e9 + 0.961506304e9) / 256 ** 3,
                        "fp64": (2.260472e9 + 1.955142e9) / 256 ** 3,
-                       "fp32_1c": (1.060342e9 + 0.957613312e9) / 256 ** 3}
+                       "fp32_1c": (1.059682e9 + 0.95704064e9) / 256 ** 3}
 # DRAM bytes per site-update of the batched leg's launch (64 lattices, 32x4
 # tiles, z chunk 128; ncu, mean of three launches): re-reads around the
 # colloids lift it above the single-lattice figure
-DRAM_BYTES_PER_SITE_BATCH = (4.641573632e9 + 2.734156288e9) / 46252032
+DRAM_BYTES_PER_SITE_BATCH = (4.658075136e9 + 2.733903957e9) / 46252032
 # FP64 form: bound by the FP64 pipe (2 FP64 operations per clock per SM).
 # FP64 arithmetic operations per site-update of the regular three-constant
 # site, counted from the kernel's arithmetic: stencil 94 (second
