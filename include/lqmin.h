@@ -546,10 +546,11 @@ lq_status lq_bounds_check_hits(uint32_t *hits);
 /* Number of z planes one thread block marches through (0 = automatic). */
 lq_status lq_set_zchunk(lq_solver *s, int zchunk);
 /* Element-index width of the step kernels: 0 = automatic (32-bit indices
-   while 5 N < 2^32, i.e. below about 950^3 sites, 64-bit beyond), 64 = the
-   64-bit instantiation on any lattice (the code path of the largest
-   lattices, for testing it on small ones; results are identical).
-   LQ_EINVAL for other values. */
+   while 5 N < 2^32, i.e. below about 950^3 sites, 64-bit beyond; the FP32
+   form's three-constant step always runs its 64-bit instantiation, which is
+   faster), 64 = the 64-bit instantiation on any lattice (the code path of
+   the largest lattices, for testing it on small ones; results are
+   identical).  LQ_EINVAL for other values. */
 lq_status lq_set_index_width(lq_solver *s, int bits);
 /* Plane staging of the FP32 form's step kernel (three constants, no chiral
    or cubic term): 0 = automatic (the faster staging measured on B300:
