@@ -271,7 +271,10 @@ lq_status batch_set_members(lq_batch *b, lq_solver *const *solvers, int n) {
     b->tables_ok = false;
     b->solvers.assign(solvers, solvers + n);
     b->sites = 0;
-    b->idx32 = 1;
+    // FP32-form batches run the 64-bit-index instantiation, measured faster
+    // on 64 lattices (one constant 1.580 -> 1.570 ms, three constants 2.163
+    // -> 2.112 ms per launch); FP64 batches 32-bit indices where they fit
+    b->idx32 = b->fp32 ? 0 : 1;
     b->form = b->three ? 1 : 0;
     for (int l = 0; l < n; ++l) {
         if (!step_index32(solvers[l]->L.N) || solvers[l]->idx64) b->idx32 = 0;

@@ -134,7 +134,9 @@ def test_served_round_with_a_failed_launch_is_retried():
     p = lqmin.fire_params(**dict(synth.FIRE_DEFAULTS, max_iter=400000, force_tol=1e-6))
     t = sv.submit(dict(shape=(48, 48, 40), L1=2.32, objects=[]), p, seed=3)
     t0 = time.time()
-    while sv.stats()["active"] == 0 and time.time() - t0 < 60:
+    # inject once the solve runs its rounds (its admission, which also
+    # launches a step kernel, is over): the failed launch is a round's
+    while sv.stats()["site_updates_issued"] == 0 and time.time() - t0 < 60:
         time.sleep(0.005)
     lqmin.inject_fault(lqmin.LQ_FAULT_STEP_LAUNCH, 0)
     code, r, _ = sv.wait(t, timeout=300)
