@@ -49,7 +49,7 @@ DRAM_BYTES_PER_SITE = {"fp32": (1.073290e9 + 0.960306176e9) / 256 ** 3,
 # DRAM bytes per site-update of the batched leg's launch (64 lattices, 32x4
 # tiles, z chunk 128; ncu, mean of three launches): re-reads around the
 # colloids lift it above the single-lattice figure
-DRAM_BYTES_PER_SITE_BATCH = (4.658075136e9 + 2.733903957e9) / 46252032
+DRAM_BYTES_PER_SITE_BATCH = (4.677079040e9 + 2.734580736e9) / 46252032
 # FP64 form: bound by the FP64 pipe (2 FP64 operations per clock per SM).
 # FP64 arithmetic operations per site-update of the regular three-constant
 # site, counted from the kernel's arithmetic: stencil 94 (second
